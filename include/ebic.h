@@ -1,0 +1,236 @@
+/* ebic.h -- C ABI of the GB300 (sm_103a) EBIC library.
+ *
+ * EBIC (arXiv 1801.03039) searches for order-preserving biclusters: a
+ * bicluster is a series of column indices, and a row supports the series when
+ * its values strictly rise along it (section "Motivation").  This library runs
+ * the data-parallel core of the method on one GPU:
+ *   - support counting and Eq. (1) fitness for a population of series
+ *     (Step 4 of the "EBIC Algorithm" section), and
+ *   - the whole generation loop of Steps 1-5 (elitism, tournament with the
+ *     crowding penalty, mutation, crossover, tabu list, top-rank list),
+ *     kept on the device between calls.
+ *
+ * Conventions shared by every entry point:
+ *   - Matrices are row-major float32 [rows][cols] on the caller's side.
+ *   - A population is given in CBF (Fig. 3): offsets[P + 1] (int32, offsets[0]
+ *     = 0, non-decreasing, offsets[P] = total length) and cols[offsets[P]]
+ *     (int32, 0-based column indices).  Fig. 3 stores only the P start
+ *     offsets; this ABI adds offsets[P] so that every length is explicit.
+ *   - Series lengths are 1 .. EBIC_MAX_EVAL_LEN for evaluation.  A column may
+ *     repeat inside a series; such a series is supported by no row (the strict
+ *     chain cannot pass the same value twice).  A length-1 series is supported
+ *     by every row.
+ *   - Every buffer the caller passes stays owned by the caller.  Inputs are
+ *     only read, during the call (host variants) or until the work queued on
+ *     the given stream has run (device variants).
+ *   - Every call returns an ebic_status.  On EBIC_ERR_ARG nothing was written
+ *     and no GPU work was queued.  ebic_last_error() gives a message for the
+ *     last failing call on the calling thread.
+ *   - A handle is bound to the CUDA device that was current when it was
+ *     created.  A handle must not be used from two threads at once.
+ *   - `void* stream` parameters take a cudaStream_t (NULL = legacy default).
+ */
+#ifndef EBIC_H_
+#define EBIC_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define EBIC_ABI_VERSION 1
+#define EBIC_MAX_EVAL_LEN 1024 /* longest series accepted by evaluation */
+#define EBIC_MAX_EA_LEN 64     /* longest series the EA builds (len_max) */
+#define EBIC_MAX_TOURNAMENT 4  /* largest tournament_k */
+
+typedef struct ebic_ctx* ebic_handle;
+
+typedef enum {
+  EBIC_OK = 0,
+  EBIC_ERR_ARG = 1,       /* invalid argument; nothing written */
+  EBIC_ERR_CUDA = 2,      /* a CUDA call failed; see ebic_last_error() */
+  EBIC_ERR_OOM = 3,       /* device allocation failed */
+  EBIC_ERR_TIMEOUT = 4,   /* a bounded device wait gave up */
+  EBIC_ERR_STATE = 5,     /* call out of order (e.g. step before init) */
+  EBIC_ERR_CANCELLED = 6, /* reserved: run cancelled by the caller */
+  EBIC_ERR_DEVICE = 7     /* a kernel flagged invalid device-side input */
+} ebic_status;
+
+/* Support path of the evaluation kernel. */
+typedef enum {
+  EBIC_PATH_AUTO = 0,    /* pick by the built-in cost model / autotuner */
+  EBIC_PATH_GATHER = 1,  /* compare fp32 values read from the column-major matrix */
+  EBIC_PATH_BITMASK = 2  /* AND precomputed pair bitmasks (needs the pair table) */
+} ebic_path;
+
+/* Which support enters |I| of Eq. (1). */
+typedef enum {
+  EBIC_SUPPORT_INC = 0,         /* rows rising along the series (the paper's search) */
+  EBIC_SUPPORT_INC_PLUS_DEC = 1 /* rising plus falling rows */
+} ebic_support_mode;
+
+const char* ebic_last_error(void);
+int32_t ebic_abi_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Matrix.  Step 1 of the "EBIC Algorithm" section: the data is placed on the
+ * GPU once.  The library keeps it column-major (each column padded to a
+ * multiple of 128 rows with NaN, which no comparison passes), so that warps
+ * walking rows read consecutive addresses, plus the table LN[m] = log(m)
+ * (binary64, host libm) used by Eq. (1).
+ *
+ * ebic_load_matrix: host_rowmajor = rows x cols float32, row-major, host
+ *   memory (pageable or pinned).  rows in [1, 2^26], cols in [1, 65535].  The
+ *   data is copied; the caller keeps its buffer.  *out receives a new handle.
+ * ebic_load_matrix_dev: the same from device memory, queued on `stream`.
+ * ebic_free: releases the handle and all its device memory (NULL is ignored).
+ * ------------------------------------------------------------------------- */
+ebic_status ebic_load_matrix(const float* host_rowmajor, int32_t rows, int32_t cols,
+                             ebic_handle* out);
+ebic_status ebic_load_matrix_dev(const float* dev_rowmajor, int32_t rows, int32_t cols,
+                                 void* stream, ebic_handle* out);
+void ebic_free(ebic_handle h);
+
+/* Shape queries. */
+ebic_status ebic_matrix_shape(ebic_handle h, int32_t* rows, int32_t* cols);
+
+/* ---------------------------------------------------------------------------
+ * Pair bitmask table (derived from the pairwise count #{k : a_kp < a_kq} of
+ * the "Motivation" section).  Word w of entry (p, q) holds bit r set iff
+ * a[32w + r][p] < a[32w + r][q] (IEEE; NaN and ties give 0; rows past the end
+ * give 0).  Layout: uint32 [cols][cols][words], words = padded rows / 32.
+ * Size cols^2 * words * 4 bytes; the call fails with EBIC_ERR_OOM if that does
+ * not fit.  Built on `stream`.  ebic_pair_table_bytes reports the size the
+ * table would take (0 if not built yet in *built).
+ * ------------------------------------------------------------------------- */
+ebic_status ebic_build_pair_table(ebic_handle h, void* stream);
+ebic_status ebic_pair_table_bytes(ebic_handle h, uint64_t* bytes, int32_t* built);
+/* Copy words [w0, w0 + n) of entry (p, q) of the built table to host memory. */
+ebic_status ebic_read_pair_words(ebic_handle h, int32_t p, int32_t q, int32_t w0, int32_t n,
+                                 uint32_t* host_out);
+
+/* Force a support path for later evaluations (EBIC_PATH_AUTO restores the
+ * automatic choice).  EBIC_PATH_BITMASK builds the table if needed. */
+ebic_status ebic_set_path(ebic_handle h, int32_t path);
+
+/* Launch shape of later evaluations (used by the autotuner; 0 = automatic).
+ * group_lanes: 32 gives every series (part) a whole warp on the bitmask path;
+ * 1..16 (a power of two) gives one lane per 16-byte vector of a table entry,
+ * allowed when an entry has at most 32 vectors (up to 4096 rows).
+ * vecs_bitmask / vecs_gather: 16-byte vectors of one table entry / one column
+ * that one warp walks before handing the rest of the series to another warp
+ * (rounded to a multiple of 32).  Results do not depend on these. */
+ebic_status ebic_set_eval_tuning(ebic_handle h, int32_t group_lanes, int32_t vecs_bitmask,
+                                 int32_t vecs_gather);
+
+/* ---------------------------------------------------------------------------
+ * Population evaluation: Step 4 of the "EBIC Algorithm" section with Eq. (1).
+ * For each series s of the CBF population:
+ *   inc[s] = #rows k with a[k][s0] < a[k][s1] < ... (strict, IEEE)
+ *   dec[s] = #rows k with a[k][s0] > a[k][s1] > ...
+ *   n      = inc (EBIC_SUPPORT_INC) or inc + dec (EBIC_SUPPORT_INC_PLUS_DEC)
+ *   fitness[s] = 0 if n <= 1, else ldexp(LN[n - 1], min(n - sigma, 0)) * |s|
+ *               (binary64; LN[m] = log(m) from the host libm)
+ * Results are exact: counts are integers and the fitness is the same binary64
+ * value a CPU evaluating the formula with that libm produces.
+ *
+ * ebic_eval_population: all buffers in host memory; synchronous.  offsets has
+ *   P + 1 entries; cols offsets[P] entries; out_inc and out_fitness P entries;
+ *   out_dec P entries or NULL.  P in [0, 2^24].  Invalid CBF (a column outside
+ *   [0, cols), a length outside [1, EBIC_MAX_EVAL_LEN], offsets[0] != 0) gives
+ *   EBIC_ERR_ARG with nothing written.
+ * ebic_eval_population_dev: the same with device buffers, queued on `stream`
+ *   (asynchronous).  total_cols must equal offsets[P].  The CBF is validated on
+ *   the device: an invalid series gets inc = dec = 0 and fitness = 0, and sets
+ *   the handle's device error flag, which ebic_check_device_error() reports
+ *   (EBIC_ERR_DEVICE) and clears.
+ * ------------------------------------------------------------------------- */
+ebic_status ebic_eval_population(ebic_handle h, const int32_t* offsets, const int32_t* cols,
+                                 int32_t P, int32_t sigma, int32_t support_mode,
+                                 uint32_t* out_inc, uint32_t* out_dec, double* out_fitness);
+ebic_status ebic_eval_population_dev(ebic_handle h, const int32_t* d_offsets,
+                                     const int32_t* d_cols, int32_t P, int32_t total_cols,
+                                     int32_t sigma, int32_t support_mode, uint32_t* d_inc,
+                                     uint32_t* d_dec, double* d_fitness, void* stream);
+/* Synchronises the handle's work and reports/clears the device error flag. */
+ebic_status ebic_check_device_error(ebic_handle h);
+
+/* ---------------------------------------------------------------------------
+ * Generation loop: Steps 1-5 of the "EBIC Algorithm" section, run entirely on
+ * the device.  Semantics (identical to the library's reference reading):
+ *   Step 1: distinct random series (length uniform in [len_min, len_max],
+ *     distinct columns) until P are accepted; evaluate; build the top-rank list.
+ *   Step 2: the best ceil(elite_frac * |list|) records start the new
+ *     population; every column use raises that column's penalty count.
+ *   Step 3: attempts until P individuals: tournament of tournament_k entrants
+ *     from the previous population by f / penalty_base^theta (theta = mean
+ *     penalty count of the entrant's columns; ties to the lower index); with
+ *     probability p_crossover a second tournament and one-point crossover;
+ *     then one of the four mutations (Fig. 1).  A child already evaluated in
+ *     this run (tabu list) is a hit; more than P hits in one generation stops
+ *     the run.
+ *   Step 4: support and Eq. (1).
+ *   Step 5: top-rank update by decreasing fitness: add unless an overlapping
+ *     record of higher or equal fitness is listed (overlap = |a & b| /
+ *     min(|a|, |b|) > overlap_tau); evict overlapping records of lower
+ *     fitness; keep the toprank_size best.
+ * Random numbers: Philox-4x32-10 (Salmon et al., SC'11), draw d of attempt j in
+ * generation g = word d % 4 of Philox(counter (j, g, d / 4, 0), key = seed).
+ * ------------------------------------------------------------------------- */
+typedef struct {
+  int32_t pop_size;        /* P >= 2 */
+  int32_t len_min;         /* >= 1 */
+  int32_t len_max;         /* len_min .. min(cols, EBIC_MAX_EA_LEN) */
+  int32_t iterations;      /* Steps 2-5 passes run by ebic_run_generations */
+  int32_t sigma;           /* Eq. (1) */
+  int32_t toprank_size;    /* T >= 1 */
+  int32_t tournament_k;    /* 1 .. EBIC_MAX_TOURNAMENT */
+  int32_t support_mode;    /* ebic_support_mode */
+  double overlap_tau;      /* in [0, 1] */
+  double elite_frac;       /* in [0, 1]; the paper's value is 0.25 */
+  double penalty_base;     /* >= 1; the paper's value is 1.2 */
+  double p_crossover;      /* in [0, 1] */
+  uint64_t seed;
+} ebic_params_t;
+
+typedef struct {
+  int32_t generations_done;  /* Steps 2-5 passes completed */
+  int32_t stop_reason;       /* 0 iterations reached, 1 tabu hits > P, 2 Step 1 failed */
+  int64_t tabu_hits_total;
+  int64_t attempts_total;
+  int64_t evaluations_total;
+  int32_t last_gen_hits;
+  int32_t toprank_n;
+  int64_t exact_tournaments; /* tournaments decided by the exact binary64 path */
+} ebic_stats_t;
+
+/* Fill *p with the defaults (P 100, len 2..6, sigma 10, T 100, k 2, tau 0.5,
+ * elite 0.25, base 1.2, p_crossover 0.5, seed 0, 10 iterations). */
+void ebic_default_params(ebic_params_t* p);
+
+/* Step 1.  Allocates the run state on the device (population archive, tabu
+ * hash table sized for (iterations + 1) * P series, penalty table) and runs
+ * Step 1.  Replaces any earlier run of the handle. */
+ebic_status ebic_run_init(ebic_handle h, const ebic_params_t* p);
+/* Steps 2-5, `generations` times (fewer if the tabu rule stops the run, or if
+ * the archive is full: EBIC_ERR_STATE).  Synchronous. */
+ebic_status ebic_run_step(ebic_handle h, int32_t generations, ebic_stats_t* stats);
+/* The current top-rank list as CBF: *inout_n = capacity in records on entry,
+ * records written on return; offsets needs capacity + 1 entries and cols
+ * capacity * len_max.  fitness / inc may be NULL. */
+ebic_status ebic_get_toprank(ebic_handle h, int32_t* offsets, int32_t* cols, double* fitness,
+                             uint32_t* inc, int32_t* inout_n);
+/* The current population (P records) in the same form, with inc, dec and
+ * fitness (each nullable). */
+ebic_status ebic_get_population(ebic_handle h, int32_t* offsets, int32_t* cols, uint32_t* inc,
+                                uint32_t* dec, double* fitness, int32_t* inout_n);
+/* ebic_run_init + ebic_run_step(p->iterations) + ebic_get_toprank. */
+ebic_status ebic_run_generations(ebic_handle h, const ebic_params_t* p, int32_t* out_offsets,
+                                 int32_t* out_cols, double* out_fitness, int32_t* inout_n,
+                                 ebic_stats_t* stats);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* EBIC_H_ */

@@ -1,0 +1,296 @@
+"""GB300 (sm_103a) implementation of the EBIC hot path (arXiv 1801.03039).
+
+A thin ctypes binding over ``libebic.so``, whose C ABI is declared in
+``include/ebic.h``.  The functions below carry the C names and only marshal
+arguments: every step of support counting, Eq. (1) and the generation loop
+runs in the library's CUDA kernels.  There is no CPU fallback -- if the
+library is missing or no GPU is visible the calls raise.
+
+Device buffers may be given as torch CUDA tensors (or raw integer device
+pointers); host buffers as numpy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import _build
+
+__all__ = [
+    "EbicError", "build", "lib", "ebic_load_matrix", "ebic_load_matrix_dev", "ebic_free",
+    "ebic_matrix_shape", "ebic_build_pair_table", "ebic_pair_table_bytes",
+    "ebic_read_pair_words", "ebic_set_path", "ebic_set_eval_tuning", "ebic_eval_population",
+    "ebic_eval_population_dev", "ebic_check_device_error", "ebic_default_params",
+    "ebic_run_init", "ebic_run_step", "ebic_get_toprank", "ebic_get_population",
+    "ebic_run_generations", "Params", "Stats", "PATH_AUTO", "PATH_GATHER", "PATH_BITMASK",
+    "SUPPORT_INC", "SUPPORT_INC_PLUS_DEC",
+]
+
+PATH_AUTO, PATH_GATHER, PATH_BITMASK = 0, 1, 2
+SUPPORT_INC, SUPPORT_INC_PLUS_DEC = 0, 1
+STATUS = {0: "EBIC_OK", 1: "EBIC_ERR_ARG", 2: "EBIC_ERR_CUDA", 3: "EBIC_ERR_OOM",
+          4: "EBIC_ERR_TIMEOUT", 5: "EBIC_ERR_STATE", 6: "EBIC_ERR_CANCELLED",
+          7: "EBIC_ERR_DEVICE"}
+
+
+class EbicError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Params(ctypes.Structure):
+    _fields_ = [
+        ("pop_size", ctypes.c_int32), ("len_min", ctypes.c_int32),
+        ("len_max", ctypes.c_int32), ("iterations", ctypes.c_int32),
+        ("sigma", ctypes.c_int32), ("toprank_size", ctypes.c_int32),
+        ("tournament_k", ctypes.c_int32), ("support_mode", ctypes.c_int32),
+        ("overlap_tau", ctypes.c_double), ("elite_frac", ctypes.c_double),
+        ("penalty_base", ctypes.c_double), ("p_crossover", ctypes.c_double),
+        ("seed", ctypes.c_uint64),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("generations_done", ctypes.c_int32), ("stop_reason", ctypes.c_int32),
+        ("tabu_hits_total", ctypes.c_int64), ("attempts_total", ctypes.c_int64),
+        ("evaluations_total", ctypes.c_int64), ("last_gen_hits", ctypes.c_int32),
+        ("toprank_n", ctypes.c_int32), ("exact_tournaments", ctypes.c_int64),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+_P = ctypes.c_void_p
+_I32 = ctypes.c_int32
+_SIGS = {
+    "ebic_last_error": ([], ctypes.c_char_p),
+    "ebic_abi_version": ([], _I32),
+    "ebic_load_matrix": ([_P, _I32, _I32, _P], _I32),
+    "ebic_load_matrix_dev": ([_P, _I32, _I32, _P, _P], _I32),
+    "ebic_free": ([_P], None),
+    "ebic_matrix_shape": ([_P, _P, _P], _I32),
+    "ebic_build_pair_table": ([_P, _P], _I32),
+    "ebic_pair_table_bytes": ([_P, _P, _P], _I32),
+    "ebic_read_pair_words": ([_P, _I32, _I32, _I32, _I32, _P], _I32),
+    "ebic_set_path": ([_P, _I32], _I32),
+    "ebic_set_eval_tuning": ([_P, _I32, _I32, _I32], _I32),
+    "ebic_eval_population": ([_P, _P, _P, _I32, _I32, _I32, _P, _P, _P], _I32),
+    "ebic_eval_population_dev": ([_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P], _I32),
+    "ebic_check_device_error": ([_P], _I32),
+    "ebic_default_params": ([_P], None),
+    "ebic_run_init": ([_P, _P], _I32),
+    "ebic_run_step": ([_P, _I32, _P], _I32),
+    "ebic_get_toprank": ([_P, _P, _P, _P, _P, _P], _I32),
+    "ebic_get_population": ([_P, _P, _P, _P, _P, _P, _P], _I32),
+    "ebic_run_generations": ([_P, _P, _P, _P, _P, _P, _P], _I32),
+}
+
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the CUDA library for sm_103a (no-op when up to date)."""
+    return _build.build(force=force)
+
+
+def lib():
+    """The loaded ``libebic.so``.  Raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(_build.LIB):
+                raise RuntimeError(
+                    "libebic.so is missing: the CUDA library must be built (build()); "
+                    "there is no CPU fallback")
+            L = ctypes.CDLL(_build.LIB)
+            for name, (args, res) in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = res
+            _lib = L
+    return _lib
+
+
+def _check(status: int):
+    if status != 0:
+        raise EbicError(status, lib().ebic_last_error().decode(errors="replace"))
+
+
+def _host(a, dtype):
+    a = np.ascontiguousarray(a, dtype=dtype)
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _dev(x):
+    """Device pointer of a torch CUDA tensor (or an int / None)."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    if not getattr(x, "is_cuda", False):
+        raise TypeError("expected a CUDA tensor for a device buffer")
+    if not x.is_contiguous():
+        raise ValueError("device buffers must be contiguous")
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return ctypes.c_void_p(s)
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ---------------------------------------------------------------------------
+def ebic_load_matrix(A) -> ctypes.c_void_p:
+    A, p = _host(A, np.float32)
+    if A.ndim != 2:
+        raise ValueError("A must be 2-D (rows x cols)")
+    h = ctypes.c_void_p()
+    _check(lib().ebic_load_matrix(p, A.shape[0], A.shape[1], ctypes.byref(h)))
+    return h
+
+
+def ebic_load_matrix_dev(A, stream=None) -> ctypes.c_void_p:
+    h = ctypes.c_void_p()
+    _check(lib().ebic_load_matrix_dev(_dev(A), A.shape[0], A.shape[1], _stream(stream),
+                                      ctypes.byref(h)))
+    return h
+
+
+def ebic_free(h):
+    if h is not None and h.value:
+        lib().ebic_free(h)
+        h.value = None
+
+
+def ebic_matrix_shape(h):
+    r, c = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().ebic_matrix_shape(h, ctypes.byref(r), ctypes.byref(c)))
+    return r.value, c.value
+
+
+def ebic_build_pair_table(h, stream=None):
+    _check(lib().ebic_build_pair_table(h, _stream(stream)))
+
+
+def ebic_pair_table_bytes(h):
+    b, built = ctypes.c_uint64(), ctypes.c_int32()
+    _check(lib().ebic_pair_table_bytes(h, ctypes.byref(b), ctypes.byref(built)))
+    return b.value, bool(built.value)
+
+
+def ebic_read_pair_words(h, p, q, w0, n):
+    out = np.zeros(n, np.uint32)
+    _check(lib().ebic_read_pair_words(h, p, q, w0, n, out.ctypes.data_as(ctypes.c_void_p)))
+    return out
+
+
+def ebic_set_path(h, path: int):
+    _check(lib().ebic_set_path(h, path))
+
+
+def ebic_set_eval_tuning(h, group_lanes: int = 0, vecs_bitmask: int = 0,
+                         vecs_gather: int = 0):
+    _check(lib().ebic_set_eval_tuning(h, group_lanes, vecs_bitmask, vecs_gather))
+
+
+def ebic_eval_population(h, offsets, cols, sigma: int, support_mode: int = SUPPORT_INC,
+                         want_dec: bool = True):
+    """Host-buffer evaluation.  Returns (inc, dec or None, fitness)."""
+    off, po = _host(offsets, np.int32)
+    cl, pc = _host(cols, np.int32)
+    P = off.shape[0] - 1
+    inc = np.zeros(P, np.uint32)
+    dec = np.zeros(P, np.uint32) if want_dec else None
+    fit = np.zeros(P, np.float64)
+    _check(lib().ebic_eval_population(
+        h, po, pc, P, int(sigma), int(support_mode), inc.ctypes.data_as(_P),
+        dec.ctypes.data_as(_P) if dec is not None else None, fit.ctypes.data_as(_P)))
+    return inc, dec, fit
+
+
+def ebic_eval_population_dev(h, d_offsets, d_cols, P: int, total_cols: int, sigma: int,
+                             support_mode: int, d_inc, d_dec, d_fitness, stream=None):
+    """Device-buffer evaluation, queued on ``stream`` (torch stream or handle)."""
+    _check(lib().ebic_eval_population_dev(h, _dev(d_offsets), _dev(d_cols), int(P),
+                                          int(total_cols), int(sigma), int(support_mode),
+                                          _dev(d_inc), _dev(d_dec), _dev(d_fitness),
+                                          _stream(stream)))
+
+
+def ebic_check_device_error(h):
+    _check(lib().ebic_check_device_error(h))
+
+
+def ebic_default_params(**overrides) -> Params:
+    p = Params()
+    lib().ebic_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def ebic_run_init(h, params: Params):
+    _check(lib().ebic_run_init(h, ctypes.byref(params)))
+
+
+def ebic_run_step(h, generations: int) -> dict:
+    st = Stats()
+    _check(lib().ebic_run_step(h, int(generations), ctypes.byref(st)))
+    return st.as_dict()
+
+
+def _records(off, cols, n):
+    return [cols[off[i]:off[i + 1]].tolist() for i in range(n)]
+
+
+def ebic_get_toprank(h, capacity: int, len_max: int):
+    off = np.zeros(capacity + 1, np.int32)
+    cols = np.zeros(max(1, capacity * len_max), np.int32)
+    fit = np.zeros(max(1, capacity), np.float64)
+    inc = np.zeros(max(1, capacity), np.uint32)
+    n = ctypes.c_int32(capacity)
+    _check(lib().ebic_get_toprank(h, off.ctypes.data_as(_P), cols.ctypes.data_as(_P),
+                                  fit.ctypes.data_as(_P), inc.ctypes.data_as(_P),
+                                  ctypes.byref(n)))
+    k = n.value
+    return _records(off, cols, k), fit[:k].copy(), inc[:k].copy()
+
+
+def ebic_get_population(h, capacity: int, len_max: int):
+    off = np.zeros(capacity + 1, np.int32)
+    cols = np.zeros(max(1, capacity * len_max), np.int32)
+    inc = np.zeros(max(1, capacity), np.uint32)
+    dec = np.zeros(max(1, capacity), np.uint32)
+    fit = np.zeros(max(1, capacity), np.float64)
+    n = ctypes.c_int32(capacity)
+    _check(lib().ebic_get_population(h, off.ctypes.data_as(_P), cols.ctypes.data_as(_P),
+                                     inc.ctypes.data_as(_P), dec.ctypes.data_as(_P),
+                                     fit.ctypes.data_as(_P), ctypes.byref(n)))
+    k = n.value
+    return dict(seqs=_records(off, cols, k), inc=inc[:k].copy(), dec=dec[:k].copy(),
+                f=fit[:k].copy())
+
+
+def ebic_run_generations(h, params: Params, capacity: int | None = None):
+    """Steps 1-5 for params.iterations generations; returns (toprank, fitness, stats)."""
+    cap = params.toprank_size if capacity is None else capacity
+    off = np.zeros(cap + 1, np.int32)
+    cols = np.zeros(max(1, cap * params.len_max), np.int32)
+    fit = np.zeros(max(1, cap), np.float64)
+    n = ctypes.c_int32(cap)
+    st = Stats()
+    _check(lib().ebic_run_generations(h, ctypes.byref(params), off.ctypes.data_as(_P),
+                                      cols.ctypes.data_as(_P), fit.ctypes.data_as(_P),
+                                      ctypes.byref(n), ctypes.byref(st)))
+    k = n.value
+    return _records(off, cols, k), fit[:k].copy(), st.as_dict()

@@ -1,0 +1,133 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "ebic.h"
+
+namespace ebic {
+
+// Thread-local message of the last failing call.
+void set_error(const char* fmt, ...);
+ebic_status fail(ebic_status st, const char* fmt, ...);
+
+#define EBIC_CUDA_TRY(expr)                                                           \
+  do {                                                                                \
+    cudaError_t e_ = (expr);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      cudaGetLastError();                                                             \
+      return ::ebic::fail(e_ == cudaErrorMemoryAllocation ? EBIC_ERR_OOM : EBIC_ERR_CUDA, \
+                          "%s failed: %s (%s:%d)", #expr, cudaGetErrorString(e_),     \
+                          __FILE__, __LINE__);                                        \
+    }                                                                                 \
+  } while (0)
+
+#define EBIC_TRY(expr)                  \
+  do {                                  \
+    ebic_status s_ = (expr);            \
+    if (s_ != EBIC_OK) return s_;       \
+  } while (0)
+
+// A growable device buffer owned by a handle.
+struct DevBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  ebic_status reserve(size_t want);
+  ebic_status reserve_zeroed(size_t want, cudaStream_t s);  // new bytes are zero
+  void release();
+  template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+// A growable pinned host buffer.
+struct HostBuf {
+  void* ptr = nullptr;
+  size_t bytes = 0;
+  ebic_status reserve(size_t want);
+  void release();
+  template <class T> T* as() const { return static_cast<T*>(ptr); }
+};
+
+struct EaState;     // generation-loop state (ebic_ea.cu)
+
+}  // namespace ebic
+
+// The opaque handle.
+struct ebic_ctx {
+  int device = 0;
+  int32_t R = 0;          // rows
+  int32_t C = 0;          // columns
+  int32_t R_pad = 0;      // rows padded to a multiple of 128 (NaN padding)
+  int32_t W = 0;          // 32-row words per column pair = R_pad / 32 (multiple of 4)
+  float* A_c = nullptr;   // column-major [C][R_pad]
+  double* LN = nullptr;   // LN[m] = log(m), m = 0 .. 2R + 1 (LN[0] unused)
+  uint32_t* LT = nullptr; // pair bitmask table [C][C][W] (nullptr until built)
+  size_t LT_bytes = 0;
+  int32_t path = EBIC_PATH_AUTO;
+  int32_t tune_group = 0;          // bitmask lanes per series (0 = automatic)
+  int32_t tune_vecs_bitmask = 0;   // 16-byte vectors per part, bitmask path (0 = auto)
+  int32_t tune_vecs_gather = 0;    // 16-byte vectors per part, gather path (0 = auto)
+  cudaStream_t stream = nullptr;  // internal stream for the host-buffer calls
+  int* d_err = nullptr;           // device error flag (0 = none)
+  ebic::DevBuf tickets;           // per-series arrival counters (self-resetting)
+  ebic::DevBuf st_off, st_cols, st_inc, st_dec, st_fit;   // staging for host calls
+  ebic::HostBuf h_stage;          // pinned staging for host calls
+  ebic::EaState* ea = nullptr;
+};
+
+namespace ebic {
+
+// Population views used by the support kernels.
+struct CbfPop {          // caller CBF: offsets[P + 1], cols[total]
+  const int32_t* offsets;
+  const int32_t* cols;
+  int32_t total;
+  __device__ __forceinline__ bool range(int32_t i, int32_t* begin, int32_t* len) const {
+    int32_t b = offsets[i], e = offsets[i + 1];
+    *begin = b;
+    *len = e - b;
+    return b >= 0 && e <= total && e - b >= 1 && e - b <= EBIC_MAX_EVAL_LEN;
+  }
+  __device__ __forceinline__ int32_t col(int32_t begin, int32_t t) const { return cols[begin + t]; }
+};
+
+struct FixedPop {        // EA layout: seq[P][stride] (uint16), len[P]
+  const uint16_t* seq;
+  const int32_t* len;
+  int32_t stride;
+  __device__ __forceinline__ bool range(int32_t i, int32_t* begin, int32_t* L) const {
+    *begin = i * stride;
+    *L = len[i];
+    return *L >= 1 && *L <= stride;
+  }
+  __device__ __forceinline__ int32_t col(int32_t begin, int32_t t) const { return seq[begin + t]; }
+};
+
+// Arguments of one evaluation launch.
+struct EvalArgs {
+  int32_t P;
+  int32_t sigma;
+  int32_t mode;           // ebic_support_mode
+  int32_t want_dec;       // compute dec (needed when mode == INC_PLUS_DEC or dec requested)
+  uint32_t* inc;
+  uint32_t* dec;          // may be nullptr when only inc is returned
+  double* fit;
+  float* lnf;             // optional: log(fitness) as float (EA tournaments), -inf for 0
+};
+
+// Evaluate a population on the handle's matrix (Step 4 + Eq. (1)), queued on s.
+ebic_status eval_cbf(ebic_ctx* h, const int32_t* d_off, const int32_t* d_cols, int32_t total,
+                     const EvalArgs& a, cudaStream_t s);
+ebic_status eval_fixed(ebic_ctx* h, const uint16_t* d_seq, const int32_t* d_len, int32_t stride,
+                       const EvalArgs& a, cudaStream_t s);
+// Which path an evaluation of this handle would take now.
+int32_t resolve_path(ebic_ctx* h);
+ebic_status build_pair_table(ebic_ctx* h, cudaStream_t s);
+
+void ea_release(ebic_ctx* h);
+
+}  // namespace ebic

@@ -1,0 +1,846 @@
+// Matrix placement, pair bitmask table and population evaluation.
+//
+//   K1 k_load_colmajor  -- row-major fp32 -> column-major, NaN-padded to a
+//                          multiple of 128 rows (Step 1: data placed on the GPU)
+//   K2 k_pair_table     -- LT[p][q][w] = ballot over 32 rows of a[k][p] < a[k][q]
+//                          (the pairwise count #{k : a_kp < a_kq}, "Motivation")
+//   K3 k_support_bitmask / k_support_gather
+//                       -- support of every series (strict chain, "Motivation";
+//                          Step 4) reduced to exact counts, with Eq. (1) fused
+//                          into the epilogue of the last part of each series.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "ebic_internal.cuh"
+
+namespace ebic {
+
+// ---------------------------------------------------------------------------
+// errors and buffers
+// ---------------------------------------------------------------------------
+static thread_local char g_last_error[512] = "";
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+}
+
+ebic_status fail(ebic_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+ebic_status DevBuf::reserve(size_t want) {
+  if (want <= bytes) return EBIC_OK;
+  release();
+  if (want == 0) return EBIC_OK;
+  EBIC_CUDA_TRY(cudaMalloc(&ptr, want));
+  bytes = want;
+  return EBIC_OK;
+}
+
+ebic_status DevBuf::reserve_zeroed(size_t want, cudaStream_t s) {
+  if (want <= bytes) return EBIC_OK;
+  EBIC_TRY(reserve(want));
+  EBIC_CUDA_TRY(cudaMemsetAsync(ptr, 0, bytes, s));
+  return EBIC_OK;
+}
+
+void DevBuf::release() {
+  if (ptr) cudaFree(ptr);
+  ptr = nullptr;
+  bytes = 0;
+}
+
+ebic_status HostBuf::reserve(size_t want) {
+  if (want <= bytes) return EBIC_OK;
+  release();
+  if (want == 0) return EBIC_OK;
+  EBIC_CUDA_TRY(cudaMallocHost(&ptr, want));
+  bytes = want;
+  return EBIC_OK;
+}
+
+void HostBuf::release() {
+  if (ptr) cudaFreeHost(ptr);
+  ptr = nullptr;
+  bytes = 0;
+}
+
+// Makes the handle's device current for the lifetime of the object.
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+    else if (prev == dev) prev = -1;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// ---------------------------------------------------------------------------
+// K1: column-major placement
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_load_colmajor(const float* __restrict__ src, int32_t R, int32_t C, int32_t R_pad,
+                float* __restrict__ dst) {
+  __shared__ float tile[32][33];
+  const int r0 = blockIdx.x * 32;
+  const int c0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  const float qnan = __int_as_float(0x7fc00000);
+  for (int j = ty; j < 32; j += 8) {
+    int r = r0 + j, c = c0 + tx;
+    tile[j][tx] = (r < R && c < C) ? src[(size_t)r * C + c] : qnan;
+  }
+  __syncthreads();
+  for (int j = ty; j < 32; j += 8) {
+    int c = c0 + j, r = r0 + tx;
+    if (c < C && r < R_pad) dst[(size_t)c * R_pad + r] = tile[tx][j];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2: pair bitmask table.  One CTA = 8 columns p (one per warp) x 1024 rows
+// (32 words).  Each warp keeps its column's 1024 values in registers and walks
+// every q; the 8 warps read the same q values, which L1 serves after the first.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256)
+k_pair_table(const float* __restrict__ A_c, int32_t C, int32_t R_pad, int32_t W,
+             uint32_t* __restrict__ LT) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int p = blockIdx.y * 8 + warp;
+  const int w0 = blockIdx.x * 32;
+  if (p >= C) return;
+  const int nw = min(32, W - w0);
+  const float qnan = __int_as_float(0x7fc00000);
+  const float* colp = A_c + (size_t)p * R_pad + (size_t)w0 * 32;
+  float ap[32];
+#pragma unroll
+  for (int j = 0; j < 32; ++j) ap[j] = (j < nw) ? colp[j * 32 + lane] : qnan;
+  uint32_t* out = LT + (size_t)p * C * W + w0;
+  for (int q = 0; q < C; ++q) {
+    const float* colq = A_c + (size_t)q * R_pad + (size_t)w0 * 32;
+    uint32_t mine = 0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      float aq = (j < nw) ? colq[j * 32 + lane] : qnan;
+      uint32_t b = __ballot_sync(0xffffffffu, ap[j] < aq);
+      if (lane == j) mine = b;
+    }
+    if (lane < nw) out[(size_t)q * W + lane] = mine;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3 shared pieces
+// ---------------------------------------------------------------------------
+constexpr int kBatch = 4;          // AND steps issued together before an exit test
+constexpr unsigned kFull = 0xffffffffu;
+
+// Eq. (1) for one series and the write-out of its results.
+__device__ __forceinline__ void finish_series(const EvalArgs& a, const double* __restrict__ LN,
+                                              int32_t i, uint32_t inc, uint32_t dec, int32_t L) {
+  a.inc[i] = inc;
+  if (a.dec) a.dec[i] = dec;
+  int64_t n = (a.mode == EBIC_SUPPORT_INC_PLUS_DEC) ? (int64_t)inc + (int64_t)dec : (int64_t)inc;
+  double f = 0.0;
+  if (n > 1) {
+    int64_t e = n - (int64_t)a.sigma;
+    if (e > 0) e = 0;
+    if (e < -2000) e = -2000;
+    f = __dmul_rn(ldexp(LN[n - 1], (int)e), (double)L);
+  }
+  a.fit[i] = f;
+  if (a.lnf) a.lnf[i] = f > 0.0 ? (float)log(f) : -INFINITY;
+}
+
+// Adds one part's counts; the part that arrives last writes the results.
+__device__ __forceinline__ void add_part(const EvalArgs& a, const double* __restrict__ LN,
+                                         uint32_t* __restrict__ tickets, int32_t items_per,
+                                         int32_t i, uint32_t inc, uint32_t dec, int32_t L) {
+  if (items_per == 1) {
+    finish_series(a, LN, i, inc, dec, L);
+    return;
+  }
+  uint32_t* dec_acc = a.dec;
+  atomicAdd(&a.inc[i], inc);
+  if (dec_acc) atomicAdd(&dec_acc[i], dec);
+  __threadfence();
+  unsigned t = atomicAdd(&tickets[i], 1u);
+  if (t == (unsigned)items_per - 1) {
+    __threadfence();
+    uint32_t n_inc = atomicAdd(&a.inc[i], 0u);
+    uint32_t n_dec = dec_acc ? atomicAdd(&dec_acc[i], 0u) : 0u;
+    tickets[i] = 0;   // ready for the next launch
+    finish_series(a, LN, i, n_inc, n_dec, L);
+  }
+}
+
+__device__ __forceinline__ uint32_t popc4(const uint4& v) {
+  return __popc(v.x) + __popc(v.y) + __popc(v.z) + __popc(v.w);
+}
+
+__device__ __forceinline__ uint4 and4(const uint4& a, const uint4& b) {
+  return make_uint4(a.x & b.x, a.y & b.y, a.z & b.z, a.w & b.w);
+}
+
+__device__ __forceinline__ bool nz4(const uint4& v) { return (v.x | v.y | v.z | v.w) != 0u; }
+
+__device__ __forceinline__ uint4 ld_table(const uint4* p) { return __ldg(p); }
+
+// ---------------------------------------------------------------------------
+// K3 bitmask path, one warp per (series, part).  Lane l holds words
+// [4 v, 4 v + 4) of the running AND for the vectors v = vb + l of the part.
+// Steps are walked in windows of 32: lane t computes the pair index of step
+// w0 + t and the warp broadcasts it with shuffles.  Every loop condition is
+// warp-uniform; the warp leaves when its AND is zero in every lane.
+// ---------------------------------------------------------------------------
+template <bool DEC, bool CHECK, class Pop>
+__global__ void __launch_bounds__(256)
+k_support_bitmask_warp(const uint32_t* __restrict__ LT, int32_t C, int32_t W, int32_t R,
+                       Pop pop, EvalArgs a, int32_t vecs_per_item, int32_t items_per,
+                       uint32_t* __restrict__ tickets, const double* __restrict__ LN,
+                       int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_items = (int64_t)a.P * items_per;
+  if (item >= n_items) return;                           // warp-uniform
+  const int32_t sid = (int32_t)(item / items_per);
+  const int32_t part = (int32_t)(item % items_per);
+  int32_t begin = 0, L = 0;
+  bool ok = pop.range(sid, &begin, &L);
+  bool bad = !ok;
+  if (CHECK) {
+    bool lb = false;
+    if (ok)
+      for (int t = lane; t < L; t += 32) lb |= (uint32_t)pop.col(begin, t) >= (uint32_t)C;
+    if (__any_sync(kFull, lb)) bad = true;
+    ok = ok && !bad;
+  }
+  const int32_t nsteps = ok ? L - 1 : 0;                 // warp-uniform
+  const int32_t V = W >> 2;
+  const int32_t v_lo = part * vecs_per_item;
+  const int32_t v_hi = min(v_lo + vecs_per_item, V);
+  const uint4* LT4 = reinterpret_cast<const uint4*>(LT);
+  const size_t row4 = (size_t)V;
+  const uint4 ones = make_uint4(kFull, kFull, kFull, kFull);
+  uint32_t cnt_inc = 0, cnt_dec = 0;
+
+  for (int32_t vb = v_lo; vb < v_hi; vb += 32) {
+    const int32_t vec = vb + lane;
+    const bool lane_on = nsteps > 0 && vec < v_hi;
+    uint4 mi = lane_on ? ones : make_uint4(0u, 0u, 0u, 0u);
+    uint4 md = (DEC && lane_on) ? ones : make_uint4(0u, 0u, 0u, 0u);
+    bool alive = nsteps > 0;                               // warp-uniform
+    for (int32_t w0 = 0; alive && w0 < nsteps; w0 += 32) {
+      uint32_t pi = 0, pd = 0;                             // pair indices x * C + y
+      if (w0 + lane < nsteps) {
+        uint32_t x = (uint32_t)pop.col(begin, w0 + lane);
+        uint32_t y = (uint32_t)pop.col(begin, w0 + lane + 1);
+        pi = x * (uint32_t)C + y;
+        pd = y * (uint32_t)C + x;
+      }
+      const int32_t wn = min(32, nsteps - w0);             // warp-uniform
+      for (int32_t t = 0; alive && t < wn; t += kBatch) {
+        uint4 xi[kBatch], xd[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const uint32_t qi = __shfl_sync(kFull, pi, (t + u) & 31);
+          const uint32_t qd = DEC ? __shfl_sync(kFull, pd, (t + u) & 31) : 0u;
+          const bool use = lane_on && (t + u) < wn;
+          xi[u] = use ? ld_table(LT4 + (size_t)qi * row4 + vec) : ones;
+          if (DEC) xd[u] = use ? ld_table(LT4 + (size_t)qd * row4 + vec) : ones;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          mi = and4(mi, xi[u]);
+          if (DEC) md = and4(md, xd[u]);
+        }
+        alive = __any_sync(kFull, lane_on && (nz4(mi) || (DEC && nz4(md))));
+      }
+    }
+    if (lane_on) {
+      cnt_inc += popc4(mi);
+      if (DEC) cnt_dec += popc4(md);
+    }
+  }
+  if (ok && L == 1 && part == 0 && lane == 0) cnt_inc = cnt_dec = (uint32_t)R;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    cnt_inc += __shfl_xor_sync(kFull, cnt_inc, o);
+    cnt_dec += __shfl_xor_sync(kFull, cnt_dec, o);
+  }
+  if (lane == 0) {
+    if (bad) {
+      atomicOr(err, 1);
+      cnt_inc = cnt_dec = 0;
+    }
+    add_part(a, LN, tickets, items_per, sid, cnt_inc, DEC ? cnt_dec : 0u, bad ? 1 : L);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3 bitmask path for short tables (at most 32 16-byte vectors per entry, i.e.
+// up to 4096 rows): one lane per (series, vector).  The VP = 2^k lanes of a
+// series are consecutive and aligned, each walks the whole chain for its own
+// vector with its own early exit -- no warp-level vote inside the loops -- and
+// a butterfly over the VP lanes sums the counts at the end.
+// ---------------------------------------------------------------------------
+template <bool DEC, bool CHECK, class Pop>
+__global__ void __launch_bounds__(256)
+k_support_bitmask_lane(const uint32_t* __restrict__ LT, int32_t C, int32_t W, int32_t R,
+                       Pop pop, EvalArgs a, int32_t VP, const double* __restrict__ LN,
+                       int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t sid64 = tid / VP;
+  const int32_t v = (int32_t)(tid % VP);
+  const bool valid = sid64 < a.P;
+  const int32_t sid = valid ? (int32_t)sid64 : 0;
+  int32_t begin = 0, L = 0;
+  bool ok = valid && pop.range(sid, &begin, &L);
+  uint32_t bad = (valid && !ok) ? 1u : 0u;
+  if (CHECK && ok)
+    for (int t = v; t < L; t += VP) bad |= (uint32_t)pop.col(begin, t) >= (uint32_t)C ? 1u : 0u;
+  for (int o = 1; o < VP; o <<= 1) bad |= __shfl_xor_sync(kFull, bad, o);
+  ok = ok && !bad;
+  const int32_t V = W >> 2;
+  const int32_t nsteps = ok ? L - 1 : 0;
+  const bool lane_on = nsteps > 0 && v < V;
+  const uint4* LT4 = reinterpret_cast<const uint4*>(LT);
+  const size_t row4 = (size_t)V;
+  const uint4 ones = make_uint4(kFull, kFull, kFull, kFull);
+  uint4 mi = lane_on ? ones : make_uint4(0u, 0u, 0u, 0u);
+  uint4 md = (DEC && lane_on) ? ones : make_uint4(0u, 0u, 0u, 0u);
+  if (lane_on) {
+    uint32_t x = (uint32_t)pop.col(begin, 0);
+    for (int32_t i = 0; i < nsteps; i += kBatch) {
+      uint4 xi[kBatch], xd[kBatch];
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        if (i + u < nsteps) {
+          const uint32_t y = (uint32_t)pop.col(begin, i + u + 1);
+          xi[u] = ld_table(LT4 + (size_t)(x * (uint32_t)C + y) * row4 + v);
+          if (DEC) xd[u] = ld_table(LT4 + (size_t)(y * (uint32_t)C + x) * row4 + v);
+          x = y;
+        } else {
+          xi[u] = ones;
+          if (DEC) xd[u] = ones;
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kBatch; ++u) {
+        mi = and4(mi, xi[u]);
+        if (DEC) md = and4(md, xd[u]);
+      }
+      if (!(nz4(mi) || (DEC && nz4(md)))) break;
+    }
+  }
+  uint32_t cnt_inc = lane_on ? popc4(mi) : 0u;
+  uint32_t cnt_dec = (DEC && lane_on) ? popc4(md) : 0u;
+  if (ok && L == 1 && v == 0) cnt_inc = cnt_dec = (uint32_t)R;
+  for (int o = 1; o < VP; o <<= 1) {
+    cnt_inc += __shfl_xor_sync(kFull, cnt_inc, o);
+    cnt_dec += __shfl_xor_sync(kFull, cnt_dec, o);
+  }
+  (void)lane;
+  if (valid && v == 0) {
+    if (bad) {
+      atomicOr(err, 1);
+      cnt_inc = cnt_dec = 0;
+    }
+    finish_series(a, LN, sid, cnt_inc, DEC ? cnt_dec : 0u, bad ? 1 : L);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K3 gather path.  A warp owns one (series, part); lane l holds 4 consecutive
+// rows (one float4 of each column read) and a 4-bit mask per direction.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t lt4(const float4& a, const float4& b) {
+  return (uint32_t)(a.x < b.x) | ((uint32_t)(a.y < b.y) << 1) | ((uint32_t)(a.z < b.z) << 2) |
+         ((uint32_t)(a.w < b.w) << 3);
+}
+__device__ __forceinline__ uint32_t gt4(const float4& a, const float4& b) {
+  return (uint32_t)(a.x > b.x) | ((uint32_t)(a.y > b.y) << 1) | ((uint32_t)(a.z > b.z) << 2) |
+         ((uint32_t)(a.w > b.w) << 3);
+}
+
+template <bool DEC, bool CHECK, class Pop>
+__global__ void __launch_bounds__(256)
+k_support_gather(const float* __restrict__ A_c, int32_t C, int32_t R_pad, int32_t R, Pop pop,
+                 EvalArgs a, int32_t vecs_per_item, int32_t items_per,
+                 uint32_t* __restrict__ tickets, const double* __restrict__ LN,
+                 int* __restrict__ err) {
+  const int lane = threadIdx.x & 31;
+  const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_items = (int64_t)a.P * items_per;
+  if (item >= n_items) return;
+  const int32_t sid = (int32_t)(item / items_per);
+  const int32_t part = (int32_t)(item % items_per);
+  int32_t begin = 0, L = 0;
+  bool ok = pop.range(sid, &begin, &L);
+  bool bad = !ok;
+  if (CHECK) {
+    bool lb = false;
+    if (ok)
+      for (int t = lane; t < L; t += 32) lb |= (uint32_t)pop.col(begin, t) >= (uint32_t)C;
+    if (__any_sync(kFull, lb)) bad = true;
+    ok = ok && !bad;
+  }
+  const int32_t nsteps = ok ? L - 1 : 0;
+  const int32_t V = R_pad >> 2;
+  const int32_t v_lo = part * vecs_per_item;
+  const int32_t v_hi = min(v_lo + vecs_per_item, V);
+  const float4* A4 = reinterpret_cast<const float4*>(A_c);
+  const size_t col4 = (size_t)V;
+  uint32_t cnt_inc = 0, cnt_dec = 0;
+  const size_t first = nsteps > 0 ? (size_t)(uint32_t)pop.col(begin, 0) * col4 : 0;
+
+  for (int32_t vb = v_lo; vb < v_hi; vb += 32) {
+    const int32_t vec = vb + lane;
+    const bool lane_on = nsteps > 0 && vec < v_hi;
+    uint32_t mi = lane_on ? 0xFu : 0u;
+    uint32_t md = (DEC && lane_on) ? 0xFu : 0u;
+    float4 prev = lane_on ? __ldg(A4 + first + vec) : make_float4(0.f, 0.f, 0.f, 0.f);
+    bool alive = nsteps > 0;
+    for (int32_t w0 = 0; alive && w0 < nsteps; w0 += 32) {
+      uint32_t cl = 0;
+      if (w0 + lane < nsteps) cl = (uint32_t)pop.col(begin, w0 + lane + 1);
+      const int32_t wn = min(32, nsteps - w0);
+      for (int32_t t = 0; alive && t < wn; t += kBatch) {
+        float4 cur[kBatch];
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          const uint32_t c = __shfl_sync(kFull, cl, (t + u) & 31);
+          cur[u] = (lane_on && t + u < wn) ? __ldg(A4 + (size_t)c * col4 + vec) : prev;
+        }
+#pragma unroll
+        for (int u = 0; u < kBatch; ++u) {
+          if (t + u < wn) {
+            mi &= lt4(prev, cur[u]);
+            if (DEC) md &= gt4(prev, cur[u]);
+            prev = cur[u];
+          }
+        }
+        alive = __any_sync(kFull, (mi | md) != 0u);
+      }
+    }
+    cnt_inc += __popc(mi);
+    if (DEC) cnt_dec += __popc(md);
+  }
+  if (ok && L == 1 && part == 0 && lane == 0) cnt_inc = cnt_dec = (uint32_t)R;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    cnt_inc += __shfl_xor_sync(kFull, cnt_inc, o);
+    cnt_dec += __shfl_xor_sync(kFull, cnt_dec, o);
+  }
+  if (lane == 0) {
+    if (bad) {
+      atomicOr(err, 1);
+      cnt_inc = cnt_dec = 0;
+    }
+    add_part(a, LN, tickets, items_per, sid, cnt_inc, DEC ? cnt_dec : 0u, bad ? 1 : L);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+constexpr int kSMs = 152;          // GB300
+constexpr int kTargetWarps = kSMs * 48;
+
+// Split each series' vectors into parts so that the launch has enough warps.
+static void choose_split(int32_t P, int32_t V, int32_t forced_vpi, int32_t* vecs_per_item,
+                         int32_t* items_per) {
+  if (forced_vpi > 0) {
+    *vecs_per_item = std::max(forced_vpi / 32, 1) * 32;
+    *items_per = (V + *vecs_per_item - 1) / *vecs_per_item;
+    return;
+  }
+  int32_t chunks = (V + 31) / 32;
+  int64_t want = (kTargetWarps + (int64_t)P - 1) / std::max<int64_t>(P, 1);
+  int32_t parts = (int32_t)std::min<int64_t>(std::max<int64_t>(want, 1), chunks);
+  int32_t per = (chunks + parts - 1) / parts;
+  *vecs_per_item = per * 32;
+  *items_per = (V + *vecs_per_item - 1) / *vecs_per_item;
+}
+
+int32_t resolve_path(ebic_ctx* h) {
+  if (h->path == EBIC_PATH_GATHER) return EBIC_PATH_GATHER;
+  if (h->path == EBIC_PATH_BITMASK) return EBIC_PATH_BITMASK;
+  return h->LT ? EBIC_PATH_BITMASK : EBIC_PATH_GATHER;
+}
+
+template <bool CHECK, class Pop>
+static ebic_status eval_any(ebic_ctx* h, const Pop& pop, EvalArgs a, cudaStream_t s) {
+  if (a.P <= 0) return EBIC_OK;
+  const bool dec = a.want_dec != 0 || a.mode == EBIC_SUPPORT_INC_PLUS_DEC;
+  if (dec && !a.dec) return fail(EBIC_ERR_ARG, "internal: dec output required");
+  const int32_t path = resolve_path(h);
+  if (path == EBIC_PATH_BITMASK && !h->LT) EBIC_TRY(build_pair_table(h, s));
+  int32_t vpi = 0, ipc = 1;
+  bool lane_kernel = false;
+  int32_t VP = 1;
+  if (path == EBIC_PATH_BITMASK) {
+    const int32_t V = h->W >> 2;
+    lane_kernel = h->tune_group > 0 ? (h->tune_group < 32 && V <= 32) : V <= 16;
+    if (lane_kernel) {
+      while (VP < V) VP <<= 1;
+    } else {
+      choose_split(a.P, V, h->tune_vecs_bitmask, &vpi, &ipc);
+    }
+  } else {
+    choose_split(a.P, h->R_pad >> 2, h->tune_vecs_gather, &vpi, &ipc);
+  }
+  if (ipc > 1) {
+    EBIC_TRY(h->tickets.reserve_zeroed((size_t)a.P * sizeof(uint32_t), s));
+    EBIC_CUDA_TRY(cudaMemsetAsync(a.inc, 0, (size_t)a.P * sizeof(uint32_t), s));
+    if (a.dec) EBIC_CUDA_TRY(cudaMemsetAsync(a.dec, 0, (size_t)a.P * sizeof(uint32_t), s));
+  }
+  uint32_t* tk = h->tickets.as<uint32_t>();
+  if (path == EBIC_PATH_BITMASK && lane_kernel) {
+    const int64_t threads = (int64_t)a.P * VP;
+    const unsigned blocks = (unsigned)((threads + 255) / 256);
+    if (dec)
+      k_support_bitmask_lane<true, CHECK, Pop><<<blocks, 256, 0, s>>>(h->LT, h->C, h->W, h->R,
+                                                                      pop, a, VP, h->LN, h->d_err);
+    else
+      k_support_bitmask_lane<false, CHECK, Pop><<<blocks, 256, 0, s>>>(h->LT, h->C, h->W, h->R,
+                                                                       pop, a, VP, h->LN, h->d_err);
+  } else {
+    const unsigned blocks = (unsigned)(((int64_t)a.P * ipc + 7) / 8);
+    if (path == EBIC_PATH_BITMASK) {
+      if (dec)
+        k_support_bitmask_warp<true, CHECK, Pop><<<blocks, 256, 0, s>>>(
+            h->LT, h->C, h->W, h->R, pop, a, vpi, ipc, tk, h->LN, h->d_err);
+      else
+        k_support_bitmask_warp<false, CHECK, Pop><<<blocks, 256, 0, s>>>(
+            h->LT, h->C, h->W, h->R, pop, a, vpi, ipc, tk, h->LN, h->d_err);
+    } else {
+      if (dec)
+        k_support_gather<true, CHECK, Pop><<<blocks, 256, 0, s>>>(
+            h->A_c, h->C, h->R_pad, h->R, pop, a, vpi, ipc, tk, h->LN, h->d_err);
+      else
+        k_support_gather<false, CHECK, Pop><<<blocks, 256, 0, s>>>(
+            h->A_c, h->C, h->R_pad, h->R, pop, a, vpi, ipc, tk, h->LN, h->d_err);
+    }
+  }
+  EBIC_CUDA_TRY(cudaGetLastError());
+  return EBIC_OK;
+}
+
+ebic_status eval_cbf(ebic_ctx* h, const int32_t* d_off, const int32_t* d_cols, int32_t total,
+                     const EvalArgs& a, cudaStream_t s) {
+  CbfPop pop{d_off, d_cols, total};
+  return eval_any<true>(h, pop, a, s);
+}
+
+ebic_status eval_fixed(ebic_ctx* h, const uint16_t* d_seq, const int32_t* d_len, int32_t stride,
+                       const EvalArgs& a, cudaStream_t s) {
+  FixedPop pop{d_seq, d_len, stride};
+  return eval_any<false>(h, pop, a, s);
+}
+
+ebic_status build_pair_table(ebic_ctx* h, cudaStream_t s) {
+  if (h->LT) return EBIC_OK;
+  const size_t bytes = (size_t)h->C * (size_t)h->C * (size_t)h->W * sizeof(uint32_t);
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(EBIC_ERR_OOM, "pair table of %zu bytes does not fit: %s", bytes,
+                cudaGetErrorString(e));
+  }
+  h->LT = static_cast<uint32_t*>(p);
+  h->LT_bytes = bytes;
+  dim3 grid((unsigned)((h->W + 31) / 32), (unsigned)((h->C + 7) / 8));
+  k_pair_table<<<grid, 256, 0, s>>>(h->A_c, h->C, h->R_pad, h->W, h->LT);
+  EBIC_CUDA_TRY(cudaGetLastError());
+  return EBIC_OK;
+}
+
+static ebic_status create_handle(int32_t rows, int32_t cols, ebic_ctx** out) {
+  if (rows < 1 || rows > (1 << 26) || cols < 1 || cols > 65535)
+    return fail(EBIC_ERR_ARG, "matrix shape %d x %d outside [1, 2^26] x [1, 65535]", rows, cols);
+  ebic_ctx* h = new ebic_ctx();
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return fail(EBIC_ERR_CUDA, "no CUDA device");
+  }
+  h->R = rows;
+  h->C = cols;
+  h->R_pad = (rows + 127) / 128 * 128;
+  h->W = h->R_pad / 32;
+  *out = h;
+  return EBIC_OK;
+}
+
+static void destroy(ebic_ctx* h) {
+  if (!h) return;
+  DeviceGuard g(h->device);
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  ea_release(h);
+  if (h->A_c) cudaFree(h->A_c);
+  if (h->LN) cudaFree(h->LN);
+  if (h->LT) cudaFree(h->LT);
+  if (h->d_err) cudaFree(h->d_err);
+  h->tickets.release();
+  h->st_off.release();
+  h->st_cols.release();
+  h->st_inc.release();
+  h->st_dec.release();
+  h->st_fit.release();
+  h->h_stage.release();
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+// Allocates the per-matrix buffers and places the matrix (rowmajor_dev is a
+// device pointer); the caller's stream orders the work.
+static ebic_status place(ebic_ctx* h, const float* rowmajor_dev, cudaStream_t s) {
+  EBIC_CUDA_TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+  EBIC_CUDA_TRY(cudaMalloc(&h->A_c, (size_t)h->C * h->R_pad * sizeof(float)));
+  EBIC_CUDA_TRY(cudaMalloc(&h->d_err, sizeof(int)));
+  EBIC_CUDA_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+  // LN[m] = log(m) with the host C library, m = 0 .. 2R + 1.
+  const size_t nln = 2 * (size_t)h->R + 2;
+  EBIC_CUDA_TRY(cudaMalloc(&h->LN, nln * sizeof(double)));
+  EBIC_TRY(h->h_stage.reserve(nln * sizeof(double)));
+  double* ln = h->h_stage.as<double>();
+  ln[0] = -INFINITY;
+  for (size_t m = 1; m < nln; ++m) ln[m] = std::log((double)m);
+  EBIC_CUDA_TRY(cudaMemcpyAsync(h->LN, ln, nln * sizeof(double), cudaMemcpyHostToDevice, s));
+  dim3 grid((unsigned)(h->R_pad / 32), (unsigned)((h->C + 31) / 32));
+  k_load_colmajor<<<grid, 256, 0, s>>>(rowmajor_dev, h->R, h->C, h->R_pad, h->A_c);
+  EBIC_CUDA_TRY(cudaGetLastError());
+  // The pinned LN staging is reused by later calls: finish the copy first.
+  EBIC_CUDA_TRY(cudaStreamSynchronize(s));
+  return EBIC_OK;
+}
+
+}  // namespace ebic
+
+using namespace ebic;
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+const char* ebic_last_error(void) { return g_last_error; }
+int32_t ebic_abi_version(void) { return EBIC_ABI_VERSION; }
+
+ebic_status ebic_load_matrix(const float* host_rowmajor, int32_t rows, int32_t cols,
+                             ebic_handle* out) {
+  if (!host_rowmajor || !out) return fail(EBIC_ERR_ARG, "null pointer");
+  ebic_ctx* h = nullptr;
+  EBIC_TRY(create_handle(rows, cols, &h));
+  DeviceGuard g(h->device);
+  float* tmp = nullptr;
+  size_t bytes = (size_t)rows * cols * sizeof(float);
+  ebic_status st = EBIC_OK;
+  cudaError_t e = cudaMalloc(&tmp, bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    destroy(h);
+    return fail(EBIC_ERR_OOM, "matrix staging: %s", cudaGetErrorString(e));
+  }
+  st = [&]() -> ebic_status {
+    EBIC_CUDA_TRY(cudaMemcpy(tmp, host_rowmajor, bytes, cudaMemcpyHostToDevice));
+    return place(h, tmp, nullptr);
+  }();
+  cudaFree(tmp);
+  if (st != EBIC_OK) {
+    destroy(h);
+    return st;
+  }
+  *out = h;
+  return EBIC_OK;
+}
+
+ebic_status ebic_load_matrix_dev(const float* dev_rowmajor, int32_t rows, int32_t cols,
+                                 void* stream, ebic_handle* out) {
+  if (!dev_rowmajor || !out) return fail(EBIC_ERR_ARG, "null pointer");
+  ebic_ctx* h = nullptr;
+  EBIC_TRY(create_handle(rows, cols, &h));
+  DeviceGuard g(h->device);
+  ebic_status st = place(h, dev_rowmajor, static_cast<cudaStream_t>(stream));
+  if (st != EBIC_OK) {
+    destroy(h);
+    return st;
+  }
+  *out = h;
+  return EBIC_OK;
+}
+
+void ebic_free(ebic_handle h) { destroy(h); }
+
+ebic_status ebic_matrix_shape(ebic_handle h, int32_t* rows, int32_t* cols) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  if (rows) *rows = h->R;
+  if (cols) *cols = h->C;
+  return EBIC_OK;
+}
+
+ebic_status ebic_build_pair_table(ebic_handle h, void* stream) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  DeviceGuard g(h->device);
+  return build_pair_table(h, static_cast<cudaStream_t>(stream));
+}
+
+ebic_status ebic_pair_table_bytes(ebic_handle h, uint64_t* bytes, int32_t* built) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  if (bytes) *bytes = (uint64_t)h->C * (uint64_t)h->C * (uint64_t)h->W * 4u;
+  if (built) *built = h->LT != nullptr;
+  return EBIC_OK;
+}
+
+ebic_status ebic_read_pair_words(ebic_handle h, int32_t p, int32_t q, int32_t w0, int32_t n,
+                                 uint32_t* host_out) {
+  if (!h || !host_out) return fail(EBIC_ERR_ARG, "null pointer");
+  if (!h->LT) return fail(EBIC_ERR_STATE, "pair table not built");
+  if (p < 0 || p >= h->C || q < 0 || q >= h->C || w0 < 0 || n < 0 || w0 + n > h->W)
+    return fail(EBIC_ERR_ARG, "pair words out of range");
+  DeviceGuard g(h->device);
+  EBIC_CUDA_TRY(cudaDeviceSynchronize());
+  EBIC_CUDA_TRY(cudaMemcpy(host_out, h->LT + ((size_t)p * h->C + q) * h->W + w0,
+                           (size_t)n * sizeof(uint32_t), cudaMemcpyDeviceToHost));
+  return EBIC_OK;
+}
+
+ebic_status ebic_set_path(ebic_handle h, int32_t path) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  if (path < EBIC_PATH_AUTO || path > EBIC_PATH_BITMASK) return fail(EBIC_ERR_ARG, "bad path");
+  h->path = path;
+  if (path == EBIC_PATH_BITMASK && !h->LT) {
+    DeviceGuard g(h->device);
+    EBIC_TRY(build_pair_table(h, h->stream));
+    EBIC_CUDA_TRY(cudaStreamSynchronize(h->stream));
+  }
+  return EBIC_OK;
+}
+
+ebic_status ebic_set_eval_tuning(ebic_handle h, int32_t group_lanes, int32_t vecs_bitmask,
+                                 int32_t vecs_gather) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  if (group_lanes != 0 && (group_lanes < 1 || group_lanes > 32 ||
+                           (group_lanes & (group_lanes - 1)) != 0))
+    return fail(EBIC_ERR_ARG, "group_lanes must be 0 or a power of two in [1, 32]");
+  if (vecs_bitmask < 0 || vecs_gather < 0) return fail(EBIC_ERR_ARG, "negative tile size");
+  h->tune_group = group_lanes;
+  h->tune_vecs_bitmask = vecs_bitmask;
+  h->tune_vecs_gather = vecs_gather;
+  return EBIC_OK;
+}
+
+ebic_status ebic_eval_population(ebic_handle h, const int32_t* offsets, const int32_t* cols,
+                                 int32_t P, int32_t sigma, int32_t support_mode,
+                                 uint32_t* out_inc, uint32_t* out_dec, double* out_fitness) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  if (P < 0 || P > (1 << 24)) return fail(EBIC_ERR_ARG, "P = %d outside [0, 2^24]", P);
+  if (P == 0) return EBIC_OK;
+  if (!offsets || !cols || !out_inc || !out_fitness) return fail(EBIC_ERR_ARG, "null pointer");
+  if (support_mode != EBIC_SUPPORT_INC && support_mode != EBIC_SUPPORT_INC_PLUS_DEC)
+    return fail(EBIC_ERR_ARG, "bad support mode %d", support_mode);
+  if (offsets[0] != 0) return fail(EBIC_ERR_ARG, "offsets[0] must be 0");
+  for (int32_t i = 0; i < P; ++i) {
+    int32_t L = offsets[i + 1] - offsets[i];
+    if (L < 1 || L > EBIC_MAX_EVAL_LEN)
+      return fail(EBIC_ERR_ARG, "series %d has length %d outside [1, %d]", i, L,
+                  EBIC_MAX_EVAL_LEN);
+  }
+  const int32_t total = offsets[P];
+  for (int32_t k = 0; k < total; ++k)
+    if (cols[k] < 0 || cols[k] >= h->C)
+      return fail(EBIC_ERR_ARG, "column index %d at position %d outside [0, %d)", cols[k], k,
+                  h->C);
+  DeviceGuard g(h->device);
+  cudaStream_t s = h->stream;
+  EBIC_TRY(h->st_off.reserve((size_t)(P + 1) * sizeof(int32_t)));
+  EBIC_TRY(h->st_cols.reserve((size_t)std::max(total, 1) * sizeof(int32_t)));
+  EBIC_TRY(h->st_inc.reserve((size_t)P * sizeof(uint32_t)));
+  EBIC_TRY(h->st_dec.reserve((size_t)P * sizeof(uint32_t)));
+  EBIC_TRY(h->st_fit.reserve((size_t)P * sizeof(double)));
+  EBIC_CUDA_TRY(cudaMemcpyAsync(h->st_off.ptr, offsets, (size_t)(P + 1) * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, s));
+  EBIC_CUDA_TRY(cudaMemcpyAsync(h->st_cols.ptr, cols, (size_t)total * sizeof(int32_t),
+                                cudaMemcpyHostToDevice, s));
+  EvalArgs a{};
+  a.P = P;
+  a.sigma = sigma;
+  a.mode = support_mode;
+  a.want_dec = out_dec != nullptr;
+  a.inc = h->st_inc.as<uint32_t>();
+  a.dec = (out_dec || support_mode == EBIC_SUPPORT_INC_PLUS_DEC) ? h->st_dec.as<uint32_t>()
+                                                                 : nullptr;
+  a.fit = h->st_fit.as<double>();
+  a.lnf = nullptr;
+  EBIC_TRY(eval_cbf(h, h->st_off.as<int32_t>(), h->st_cols.as<int32_t>(), total, a, s));
+  EBIC_CUDA_TRY(cudaMemcpyAsync(out_inc, a.inc, (size_t)P * sizeof(uint32_t),
+                                cudaMemcpyDeviceToHost, s));
+  if (out_dec)
+    EBIC_CUDA_TRY(cudaMemcpyAsync(out_dec, a.dec, (size_t)P * sizeof(uint32_t),
+                                  cudaMemcpyDeviceToHost, s));
+  EBIC_CUDA_TRY(cudaMemcpyAsync(out_fitness, a.fit, (size_t)P * sizeof(double),
+                                cudaMemcpyDeviceToHost, s));
+  EBIC_CUDA_TRY(cudaStreamSynchronize(s));
+  return EBIC_OK;
+}
+
+ebic_status ebic_eval_population_dev(ebic_handle h, const int32_t* d_offsets,
+                                     const int32_t* d_cols, int32_t P, int32_t total_cols,
+                                     int32_t sigma, int32_t support_mode, uint32_t* d_inc,
+                                     uint32_t* d_dec, double* d_fitness, void* stream) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  if (P < 0 || P > (1 << 24)) return fail(EBIC_ERR_ARG, "P = %d outside [0, 2^24]", P);
+  if (P == 0) return EBIC_OK;
+  if (!d_offsets || !d_cols || !d_inc || !d_fitness) return fail(EBIC_ERR_ARG, "null pointer");
+  if (total_cols < 0) return fail(EBIC_ERR_ARG, "negative total_cols");
+  if (support_mode != EBIC_SUPPORT_INC && support_mode != EBIC_SUPPORT_INC_PLUS_DEC)
+    return fail(EBIC_ERR_ARG, "bad support mode %d", support_mode);
+  DeviceGuard g(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  EvalArgs a{};
+  a.P = P;
+  a.sigma = sigma;
+  a.mode = support_mode;
+  a.want_dec = d_dec != nullptr;
+  a.inc = d_inc;
+  a.fit = d_fitness;
+  a.lnf = nullptr;
+  if (d_dec) {
+    a.dec = d_dec;
+  } else if (support_mode == EBIC_SUPPORT_INC_PLUS_DEC) {
+    EBIC_TRY(h->st_dec.reserve((size_t)P * sizeof(uint32_t)));
+    a.dec = h->st_dec.as<uint32_t>();
+  }
+  return eval_cbf(h, d_offsets, d_cols, total_cols, a, s);
+}
+
+ebic_status ebic_check_device_error(ebic_handle h) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  DeviceGuard g(h->device);
+  EBIC_CUDA_TRY(cudaDeviceSynchronize());
+  int v = 0;
+  EBIC_CUDA_TRY(cudaMemcpy(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (v) {
+    EBIC_CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
+    return fail(EBIC_ERR_DEVICE, "a kernel flagged invalid input (code %d)", v);
+  }
+  return EBIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,57 @@
+"""CPU-side checks of the boundary: the CUDA library builds for sm_103a, loads,
+and exports every function include/ebic.h declares; the binding fails loudly
+when the library is missing."""
+import ctypes
+import os
+import subprocess
+import sys
+
+import pytest
+
+from helpers import ROOT, header_functions
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1801_03039_gb300 import _build
+    return _build.build()
+
+
+def test_header_declares_the_boundary():
+    names = header_functions()
+    for want in ("ebic_load_matrix", "ebic_eval_population", "ebic_run_generations",
+                 "ebic_free", "ebic_last_error"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    L = ctypes.CDLL(libpath)
+    missing = [n for n in header_functions() if not hasattr(L, n)]
+    assert not missing, missing
+
+
+def test_build_targets_sm_103a_only():
+    from paper_1801_03039_gb300 import _build
+    assert _build.ARCH == ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+
+def test_binding_marshals_names_of_the_header():
+    import paper_1801_03039_gb300 as e
+    for n in header_functions():
+        if n in ("ebic_last_error", "ebic_abi_version"):
+            continue
+        assert hasattr(e, n), n
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    code = (
+        "import paper_1801_03039_gb300 as e, paper_1801_03039_gb300._build as b\n"
+        f"b.LIB = {str(tmp_path / 'missing.so')!r}\n"
+        "try:\n    e.lib()\nexcept RuntimeError as x:\n    print('raised', x)\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT)
+    assert "raised" in r.stdout and "no CPU fallback" in r.stdout
+
+
+def test_abi_version(libpath):
+    L = ctypes.CDLL(libpath)
+    assert L.ebic_abi_version() == 1

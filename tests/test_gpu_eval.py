@@ -1,0 +1,222 @@
+"""Parity of the CUDA evaluation path (K1 placement, K2 pair table, K3 support
++ Eq. (1)) with the oracle, through the C ABI.  Counts and fitness must be
+bit-identical: integers exactly, binary64 fitness bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1801_03039_gb300 as eb
+from paper_1801_03039_gb300 import synth
+from helpers import assert_bits_equal, oracle_eval
+
+pytestmark = pytest.mark.gpu
+
+PATHS = [eb.PATH_GATHER, eb.PATH_BITMASK]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    eb.build()
+    yield
+
+
+def _check(A, off, cols, sigma, path, mode=0, want_dec=True):
+    h = eb.ebic_load_matrix(A)
+    try:
+        eb.ebic_set_path(h, path)
+        inc, dec, fit = eb.ebic_eval_population(h, off, cols, sigma, mode, want_dec)
+    finally:
+        eb.ebic_free(h)
+    oinc, odec, ofit = oracle_eval(A, off, cols, sigma, mode)
+    assert_bits_equal(inc, oinc, "inc")
+    if want_dec:
+        assert_bits_equal(dec, odec, "dec")
+    assert_bits_equal(fit, ofit, "fitness")
+    return inc, dec, fit
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("mode", [0, 1])
+def test_tiny_200x20(path, mode):
+    prob = synth.matrix_tiny(seed=0)
+    off, cols = synth.population(0, 100, 20, 2, 6, plants=prob.plants)
+    _check(prob.A, off, cols, 10, path, mode)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_paper_1000x100(path):
+    prob = synth.matrix_paper(seed=0)
+    off, cols = synth.population(1, 600, 100, 3, 20, plants=prob.plants)
+    inc, _, _ = _check(prob.A, off, cols, 25, path)
+    assert inc.max() >= 50           # planted series are found
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_expression_20000x200_full(path):
+    prob = synth.matrix_expression(seed=0)
+    off, cols = synth.population(2, 4096, 200, 3, 30, plants=prob.plants)
+    _check(prob.A, off, cols, 50, path, mode=1)
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("R,C", [(1, 3), (31, 5), (33, 7), (127, 9), (129, 4), (1001, 13),
+                                 (4097, 6), (5000, 40)])
+def test_ragged_shapes(path, R, C):
+    rng = np.random.default_rng(R * 100 + C)
+    A = rng.standard_normal((R, C)).astype(np.float32)
+    off, cols = synth.population(R + C, 300, C, 1, min(C, 8))
+    _check(A, off, cols, 5, path, mode=1)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_ties_nan_signed_zero(path):
+    rng = np.random.default_rng(11)
+    A = rng.integers(-2, 3, (700, 10)).astype(np.float32)
+    A[rng.random(A.shape) < 0.05] = np.nan
+    A[rng.random(A.shape) < 0.1] = -0.0
+    off, cols = synth.population(3, 500, 10, 1, 6, duplicates=True)
+    _check(A, off, cols, 7, path, mode=1)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_single_column_duplicates_and_long_series(path):
+    rng = np.random.default_rng(12)
+    A = rng.standard_normal((300, 1100)).astype(np.float32)
+    seqs = [[5], [5, 5], [0, 1, 0], list(range(1024)), rng.permutation(1100)[:1024].tolist(),
+            list(range(1023, -1, -1)), [7] * 1024]
+    off, cols = oracle.to_cbf(seqs)
+    inc, dec, fit = _check(A, off, cols, 3, path, mode=1)
+    assert inc[0] == dec[0] == 300 and inc[1] == dec[1] == 0 and inc[2] == 0
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_few_series_many_rows_split_into_parts(path):
+    # Few series over many rows: each series is split across warps and the
+    # last-arriving part writes Eq. (1).  Run twice (arrival counters reset).
+    prob = synth.matrix_random(5, 60000, 12, n_plants=2, plant_rows=(3000, 6000),
+                               plant_cols=(3, 6))
+    off, cols = synth.population(4, 5, 12, 2, 5, plants=prob.plants, frac_planted=1.0)
+    for _ in range(2):
+        _check(prob.A, off, cols, 100, path, mode=1)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_fitness_underflow_region(path):
+    prob = synth.matrix_paper(seed=3)
+    off, cols = synth.population(5, 600, 100, 2, 4, plants=prob.plants)
+    for sigma in (1000, 1100, 1500, 3000):
+        _check(prob.A, off, cols, sigma, path)
+
+
+def test_empty_population():
+    h = eb.ebic_load_matrix(np.zeros((10, 3), np.float32))
+    inc, dec, fit = eb.ebic_eval_population(h, np.zeros(1, np.int32), np.zeros(0, np.int32), 3)
+    assert len(inc) == len(fit) == 0
+    eb.ebic_free(h)
+
+
+def test_pair_table_words_match_numpy():
+    rng = np.random.default_rng(13)
+    R, C = 1000, 9
+    A = rng.integers(-3, 4, (R, C)).astype(np.float32)
+    A[rng.random(A.shape) < 0.03] = np.nan
+    h = eb.ebic_load_matrix(A)
+    eb.ebic_build_pair_table(h)
+    nbytes, built = eb.ebic_pair_table_bytes(h)
+    W = 1024 // 32
+    assert built and nbytes == C * C * W * 4
+    for p in range(C):
+        for q in range(C):
+            bits = np.zeros(W * 32, bool)
+            bits[:R] = A[:, p] < A[:, q]
+            want = np.packbits(bits.reshape(W, 32)[:, ::-1], axis=1)
+            want = want.astype(np.uint32)
+            want = (want[:, 0] << 24) | (want[:, 1] << 16) | (want[:, 2] << 8) | want[:, 3]
+            got = eb.ebic_read_pair_words(h, p, q, 0, W)
+            assert np.array_equal(got, want), (p, q)
+    eb.ebic_free(h)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_device_buffers_on_a_torch_stream(path):
+    torch = pytest.importorskip("torch")
+    prob = synth.matrix_paper(seed=4)
+    off, cols = synth.population(6, 600, 100, 3, 20, plants=prob.plants)
+    dev = torch.device("cuda:0")
+    s = torch.cuda.Stream()
+    dA = torch.from_numpy(prob.A).to(dev)
+    h = eb.ebic_load_matrix_dev(dA, stream=s)
+    eb.ebic_set_path(h, path)
+    d_off = torch.from_numpy(off).to(dev)
+    d_cols = torch.from_numpy(cols).to(dev)
+    d_inc = torch.zeros(600, dtype=torch.int32, device=dev)
+    d_dec = torch.zeros(600, dtype=torch.int32, device=dev)
+    d_fit = torch.zeros(600, dtype=torch.float64, device=dev)
+    with torch.cuda.stream(s):
+        eb.ebic_eval_population_dev(h, d_off, d_cols, 600, len(cols), 25, 0, d_inc, d_dec,
+                                    d_fit, stream=s)
+    s.synchronize()
+    eb.ebic_check_device_error(h)
+    oinc, odec, ofit = oracle_eval(prob.A, off, cols, 25)
+    assert_bits_equal(d_inc.cpu().numpy().view(np.uint32), oinc, "inc")
+    assert_bits_equal(d_dec.cpu().numpy().view(np.uint32), odec, "dec")
+    assert_bits_equal(d_fit.cpu().numpy(), ofit, "fitness")
+    eb.ebic_free(h)
+
+
+def test_host_variant_rejects_invalid_cbf():
+    A = np.random.default_rng(0).standard_normal((50, 4)).astype(np.float32)
+    h = eb.ebic_load_matrix(A)
+    for off, cols in [([0, 2], [0, 4]), ([0, 2], [-1, 1]), ([1, 3], [0, 1, 2]),
+                      ([0, 0], []), ([0, 2, 1], [0, 1])]:
+        with pytest.raises(eb.EbicError) as e:
+            eb.ebic_eval_population(h, np.array(off), np.array(cols), 3)
+        assert e.value.status == 1
+    eb.ebic_free(h)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_device_variant_flags_invalid_series(path):
+    torch = pytest.importorskip("torch")
+    A = np.random.default_rng(1).standard_normal((300, 6)).astype(np.float32)
+    h = eb.ebic_load_matrix(A)
+    eb.ebic_set_path(h, path)
+    dev = torch.device("cuda:0")
+    # series 1 has a column out of range; series 3 has offsets past the end
+    off = torch.tensor([0, 2, 4, 6, 99], dtype=torch.int32, device=dev)
+    cols = torch.tensor([0, 1, 2, 6, 3, 4], dtype=torch.int32, device=dev)
+    inc = torch.full((4,), 7, dtype=torch.int32, device=dev)
+    fit = torch.full((4,), 7.0, dtype=torch.float64, device=dev)
+    eb.ebic_eval_population_dev(h, off, cols, 4, 6, 3, 0, inc, None, fit)
+    with pytest.raises(eb.EbicError) as e:
+        eb.ebic_check_device_error(h)
+    assert e.value.status == 7
+    got = inc.cpu().numpy()
+    oinc, _, ofit = oracle_eval(A, np.array([0, 2, 4]), np.array([0, 1, 3, 4]), 3)
+    assert got[1] == 0 and got[3] == 0 and fit.cpu().numpy()[1] == 0.0
+    assert got[0] == oinc[0] and got[2] == oinc[1]
+    eb.ebic_check_device_error(h)      # flag was cleared
+    eb.ebic_free(h)
+
+
+@pytest.mark.parametrize("shape", [(200, 20), (1000, 100), (4097, 30), (20000, 60)])
+@pytest.mark.parametrize("tune", [(0, 0, 0), (1, 0, 0), (32, 0, 0), (32, 32, 32), (32, 64, 96)])
+def test_launch_shapes_do_not_change_results(shape, tune):
+    # lane-per-vector kernel, warp kernel, and forced splits of each series
+    R, C = shape
+    prob = synth.matrix_random(R + C, R, C, n_plants=3, plant_rows=(R // 20, R // 8),
+                               plant_cols=(3, 8))
+    off, cols = synth.population(R, 257, C, 2, 12, plants=prob.plants)
+    oinc, odec, ofit = oracle_eval(prob.A, off, cols, max(10, R // 100), 1)
+    h = eb.ebic_load_matrix(prob.A)
+    try:
+        for path in PATHS:
+            eb.ebic_set_path(h, path)
+            eb.ebic_set_eval_tuning(h, *tune)
+            inc, dec, fit = eb.ebic_eval_population(h, off, cols, max(10, R // 100), 1)
+            eb.ebic_check_device_error(h)
+            assert_bits_equal(inc, oinc, f"inc {path} {tune}")
+            assert_bits_equal(dec, odec, f"dec {path} {tune}")
+            assert_bits_equal(fit, ofit, f"fit {path} {tune}")
+    finally:
+        eb.ebic_free(h)
