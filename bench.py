@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Measurement of the EBIC hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload NAME]
+
+Prints ONE JSON line (rank 0).  Workloads (seeded synthetic inputs, see
+paper_1801_03039_gb300/synth.py):
+
+  eval-expression  20,000 x 200 log-normal matrix with 10 planted overlapping
+                   order-preserving biclusters; a population of 4,096 series of
+                   length 3-30.  A step is one fitness pass (support + Eq. (1))
+                   of the whole population through the C ABI on device buffers.
+
+Timing: W untimed warm-up steps, then K steps, each timed with CUDA events on
+the launching stream; L2 is flushed (a 512 MiB buffer is overwritten) before
+every timed step, outside the timed interval.  SM clocks and throttle reasons
+are sampled with nvidia-smi during the timed steps.  With torchrun (N > 1)
+every rank runs its own independent problem (seeded by its rank; no
+collective on the data path) and rank 0 reports the whole-job aggregate over
+the slowest rank's time (weak scaling).
+
+``--impl reference`` times the CPU oracle (the plain restatement of the
+method used by the tests) on the host cores on a bounded sample of the same
+workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "candidate×row support tests/sec and generations/sec at 1 GB300; % of roofline"
+L2_FLUSH_BYTES = 512 << 20
+
+
+# ---------------------------------------------------------------------------
+# distributed plumbing (rank-local problems, max-over-ranks timing)
+# ---------------------------------------------------------------------------
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate_max(value: float, ws: int, device=None) -> float:
+    """Max of a per-rank float over all ranks (identity for one rank)."""
+    if ws == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------------------
+# clocks
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, bus_id: str | None):
+        self.bus_id = (bus_id or "").lower()
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL,
+                stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        buses = {r[0].lower()[-7:] for r in rows}
+        if len(buses) > 1 and self.bus_id:
+            rows = [r for r in rows if r[0].lower()[-7:] == self.bus_id[-7:]]
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def load_peaks() -> dict:
+    try:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        d["source"] = "measured"
+        return d
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
+
+
+# ---------------------------------------------------------------------------
+# workload: one fitness pass over an expression-shaped matrix
+# ---------------------------------------------------------------------------
+class EvalExpression:
+    name = "eval-expression"
+    R, C, P, LMIN, LMAX, SIGMA = 20000, 200, 4096, 3, 30, 50
+
+    def __init__(self, rank: int):
+        from paper_1801_03039_gb300 import synth
+        self.prob = synth.matrix_expression(seed=rank)
+        self.off, self.cols = synth.population(2 + rank, self.P, self.C, self.LMIN, self.LMAX,
+                                               plants=self.prob.plants)
+
+    def config(self):
+        return {"workload": "eval-expression-20000x200-P4096-L3-30",
+                "rows": self.R, "cols": self.C, "population": self.P,
+                "series_len": [self.LMIN, self.LMAX], "sigma": self.SIGMA,
+                "support_path": "bitmask", "support_mode": "inc",
+                "l2": "flushed before every timed step (512 MiB overwrite)"}
+
+    def units_per_step(self) -> int:          # candidate x row tests per step
+        return self.P * self.R
+
+    # -- GPU ---------------------------------------------------------------
+    def setup_gpu(self, torch, eb):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.h = eb.ebic_load_matrix(self.prob.A)
+        eb.ebic_set_path(self.h, eb.PATH_BITMASK)
+        self.d_off = torch.from_numpy(self.off).to(dev)
+        self.d_cols = torch.from_numpy(self.cols).to(dev)
+        self.d_inc = torch.zeros(self.P, dtype=torch.int32, device=dev)
+        self.d_fit = torch.zeros(self.P, dtype=torch.float64, device=dev)
+        self.launches_per_step = 1
+        torch.cuda.synchronize()
+
+    def step_gpu(self, torch, eb, stream):
+        eb.ebic_eval_population_dev(self.h, self.d_off, self.d_cols, self.P, len(self.cols),
+                                    self.SIGMA, eb.SUPPORT_INC, self.d_inc, None, self.d_fit,
+                                    stream=stream)
+
+    def e2e_gpu(self, torch, eb, steps: int) -> dict:
+        """Same metric through the host-buffer C-ABI call (copies inside)."""
+        off = torch.from_numpy(self.off).pin_memory().numpy()
+        cols = torch.from_numpy(self.cols).pin_memory().numpy()
+        eb.ebic_eval_population(self.h, off, cols, self.SIGMA, eb.SUPPORT_INC, want_dec=False)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            inc, _, fit = eb.ebic_eval_population(self.h, off, cols, self.SIGMA, eb.SUPPORT_INC,
+                                                  want_dec=False)
+        dt = time.perf_counter() - t0
+        return {"value": self.units_per_step() * steps / dt, "unit": "tests/s",
+                "h2d_bytes_per_step": int(off.nbytes + cols.nbytes),
+                "d2h_bytes_per_step": int(inc.nbytes + fit.nbytes)}
+
+    def algorithmic_bytes(self) -> tuple[int, str]:
+        """Bytes the early-exit bitmask algorithm reads per pass: for every series
+        and every 128-row block, one 16-byte table vector per AND step taken while
+        the block's running AND is not yet zero; plus the CBF and the outputs."""
+        A = self.prob.A
+        R, C = A.shape
+        Rp = (R + 127) // 128 * 128
+        nblk = Rp // 128
+        cache = {}
+
+        def pair_bits(x, y):
+            k = (x, y)
+            if k not in cache:
+                b = np.zeros(Rp, bool)
+                b[:R] = A[:, x] < A[:, y]
+                cache[k] = np.packbits(b.reshape(nblk, 128), axis=1)   # nblk x 16 bytes
+            return cache[k]
+
+        vec_steps = 0
+        for i in range(self.P):
+            s = self.cols[self.off[i]:self.off[i + 1]]
+            if len(s) < 2:
+                continue
+            m = None
+            alive = np.ones(nblk, bool)
+            for t in range(len(s) - 1):
+                vec_steps += int(alive.sum())
+                b = pair_bits(int(s[t]), int(s[t + 1]))
+                m = b if m is None else (m & b)
+                alive = m.any(axis=1)
+                if not alive.any():
+                    break
+        io = self.off.nbytes + self.cols.nbytes + self.P * (4 + 8)
+        return vec_steps * 16 + io, ("16 B per (series, 128-row block, AND step) while the "
+                                     "block is alive + CBF in + inc/fitness out")
+
+    # -- CPU oracle ----------------------------------------------------------
+    def oracle_sample(self, oracle, budget_s: float, nthreads: int):
+        """Times the oracle on the first n series (all rows), n sized to ~budget_s."""
+        n = 64
+        while True:
+            off = self.off[:n + 1]
+            cols = self.cols[:off[-1]]
+            t0 = time.perf_counter()
+            oracle.support(self.prob.A, off, cols, nthreads=nthreads)
+            dt = time.perf_counter() - t0
+            if dt > budget_s / 4 or n >= self.P:
+                break
+            n = min(self.P, n * 4)
+        return n, dt
+
+
+WORKLOADS = {"eval-expression": EvalExpression}
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, ws, rank, local):
+    import torch
+    import paper_1801_03039_gb300 as eb
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    eb.build()
+    wl = WORKLOADS[args.workload](rank)
+    wl.setup_gpu(torch, eb)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    for i in range(args.warmup):
+        wl.step_gpu(torch, eb, stream)
+    torch.cuda.synchronize()
+    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(args.steps)]
+    props = torch.cuda.get_device_properties(local)
+    bus = getattr(props, "pci_bus_id", None)
+    clocks = ClockSampler(bus if isinstance(bus, str) else None) if rank == 0 else None
+    barrier(ws)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    l0 = eb.ebic_kernel_launches()
+    for i in range(args.steps):
+        flush.fill_(i)
+        events[i][0].record(stream)
+        wl.step_gpu(torch, eb, stream)
+        events[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = eb.ebic_kernel_launches() - l0
+    clk = clocks.stop() if clocks else None
+    per_step_ms = [a.elapsed_time(b) for a, b in events]
+    total_s = sum(per_step_ms) / 1e3
+    barrier(ws)
+    slowest = aggregate_max(total_s, ws, device=torch.device("cuda", local))
+    e2e = wl.e2e_gpu(torch, eb, max(3, args.steps))
+    if ws > 1:
+        e2e_val = aggregate_max(1.0 / e2e["value"], ws, device=torch.device("cuda", local))
+        e2e["value"] = ws / e2e_val
+    if rank != 0:
+        return None
+    value = ws * wl.units_per_step() * args.steps / slowest
+    peaks = load_peaks()
+    alg_bytes, alg_def = wl.algorithmic_bytes()
+    kernel_s = statistics.mean(per_step_ms) / 1e3
+    achieved = alg_bytes / kernel_s / 1e9
+    traffic = read_traffic(args.workload)
+    out = {
+        "metric": METRIC, "value": value, "unit": "tests/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * slowest / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-compare/u32-count/f64-fitness",
+        "data": "synthetic (seeded; stands in for the paper's benchmark data)",
+        "config": wl.config(),
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
+                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                     "traffic": traffic, "algorithmic_bytes": alg_bytes,
+                     "algorithmic_def": alg_def, "kernel": "k_support_bitmask_warp",
+                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})"},
+        "clocks": clk,
+    }
+    if ws == 1:
+        out["cpu_baseline"] = cpu_baseline(wl, budget_s=12.0)
+    return out
+
+
+def read_traffic(workload: str):
+    """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary,
+    if one exists for this workload and kernel build (else null)."""
+    p = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
+    try:
+        d = json.load(open(p))
+        return d.get("dram_bytes_per_launch")
+    except (OSError, ValueError):
+        return None
+
+
+def cpu_baseline(wl, budget_s: float):
+    import oracle
+    cores = os.cpu_count() or 1
+    n, dt = wl.oracle_sample(oracle, budget_s, cores)
+    return {"value": n * wl.R / dt, "unit": "tests/s", "cores": cores, "kind": "oracle",
+            "sample": f"first {n} of {wl.P} series x all {wl.R} rows, one pass, "
+                      f"OpenMP over series on {cores} threads ({dt:.2f} s)"}
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return None
+    import oracle
+    wl = WORKLOADS[args.workload](0)
+    cores = os.cpu_count() or 1
+    n, _ = wl.oracle_sample(oracle, 8.0, cores)
+    off = wl.off[:n + 1]
+    cols = wl.cols[:off[-1]]
+    for _ in range(args.warmup):
+        oracle.support(wl.prob.A, off, cols, nthreads=cores)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.support(wl.prob.A, off, cols, nthreads=cores)
+    dt = time.perf_counter() - t0
+    value = n * wl.R * args.steps / dt
+    sample = f"first {n} of {wl.P} series x all {wl.R} rows per step, OpenMP on {cores} threads"
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "tests/s",
+            "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32-compare/u32-count", "data": "synthetic",
+            "config": wl.config(),
+            "cpu_baseline": {"value": value, "unit": "tests/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "tests/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="eval-expression")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be at least 3")
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        out = run_reference(args, ws, rank)
+    else:
+        out = run_ours(args, ws, rank, local)
+    if out is not None:
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

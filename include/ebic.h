@@ -72,6 +72,10 @@ typedef enum {
 
 const char* ebic_last_error(void);
 int32_t ebic_abi_version(void);
+/* Number of CUDA kernels this library has launched in this process (all
+ * handles, all threads); for measurement tools.  Library-internal memsets and
+ * copies are not counted. */
+uint64_t ebic_kernel_launches(void);
 
 /* ---------------------------------------------------------------------------
  * Matrix.  Step 1 of the "EBIC Algorithm" section: the data is placed on the

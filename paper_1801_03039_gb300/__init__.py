@@ -20,7 +20,7 @@ import numpy as np
 from . import _build
 
 __all__ = [
-    "EbicError", "build", "lib", "ebic_load_matrix", "ebic_load_matrix_dev", "ebic_free",
+    "EbicError", "build", "lib", "ebic_kernel_launches", "ebic_load_matrix", "ebic_load_matrix_dev", "ebic_free",
     "ebic_matrix_shape", "ebic_build_pair_table", "ebic_pair_table_bytes",
     "ebic_read_pair_words", "ebic_set_path", "ebic_set_eval_tuning", "ebic_eval_population",
     "ebic_eval_population_dev", "ebic_check_device_error", "ebic_default_params",
@@ -71,6 +71,7 @@ _I32 = ctypes.c_int32
 _SIGS = {
     "ebic_last_error": ([], ctypes.c_char_p),
     "ebic_abi_version": ([], _I32),
+    "ebic_kernel_launches": ([], ctypes.c_uint64),
     "ebic_load_matrix": ([_P, _I32, _I32, _P], _I32),
     "ebic_load_matrix_dev": ([_P, _I32, _I32, _P, _P], _I32),
     "ebic_free": ([_P], None),
@@ -164,6 +165,10 @@ def ebic_load_matrix_dev(A, stream=None) -> ctypes.c_void_p:
     _check(lib().ebic_load_matrix_dev(_dev(A), A.shape[0], A.shape[1], _stream(stream),
                                       ctypes.byref(h)))
     return h
+
+
+def ebic_kernel_launches() -> int:
+    return int(lib().ebic_kernel_launches())
 
 
 def ebic_free(h):

@@ -129,5 +129,7 @@ int32_t resolve_path(ebic_ctx* h);
 ebic_status build_pair_table(ebic_ctx* h, cudaStream_t s);
 
 void ea_release(ebic_ctx* h);
+// Adds n to the process-wide count of kernels this library launched.
+void count_launches(uint64_t n);
 
 }  // namespace ebic

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -18,6 +19,9 @@
 #include "ebic_internal.cuh"
 
 namespace ebic {
+
+static std::atomic<uint64_t> g_launches{0};
+void count_launches(uint64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
 // ---------------------------------------------------------------------------
 // errors and buffers
@@ -254,11 +258,13 @@ k_support_bitmask_warp(const uint32_t* __restrict__ LT, int32_t C, int32_t W, in
       const int32_t wn = min(32, nsteps - w0);             // warp-uniform
       for (int32_t t = 0; alive && t < wn; t += kBatch) {
         uint4 xi[kBatch], xd[kBatch];
+        // a lane whose own block is already empty stops fetching
+        const bool live = lane_on && (nz4(mi) || (DEC && nz4(md)));
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
           const uint32_t qi = __shfl_sync(kFull, pi, (t + u) & 31);
           const uint32_t qd = DEC ? __shfl_sync(kFull, pd, (t + u) & 31) : 0u;
-          const bool use = lane_on && (t + u) < wn;
+          const bool use = live && (t + u) < wn;
           xi[u] = use ? ld_table(LT4 + (size_t)qi * row4 + vec) : ones;
           if (DEC) xd[u] = use ? ld_table(LT4 + (size_t)qd * row4 + vec) : ones;
         }
@@ -421,10 +427,11 @@ k_support_gather(const float* __restrict__ A_c, int32_t C, int32_t R_pad, int32_
       const int32_t wn = min(32, nsteps - w0);
       for (int32_t t = 0; alive && t < wn; t += kBatch) {
         float4 cur[kBatch];
+        const bool live = lane_on && (mi | md) != 0u;   // own rows still rising/falling
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
           const uint32_t c = __shfl_sync(kFull, cl, (t + u) & 31);
-          cur[u] = (lane_on && t + u < wn) ? __ldg(A4 + (size_t)c * col4 + vec) : prev;
+          cur[u] = (live && t + u < wn) ? __ldg(A4 + (size_t)c * col4 + vec) : prev;
         }
 #pragma unroll
         for (int u = 0; u < kBatch; ++u) {
@@ -510,6 +517,7 @@ static ebic_status eval_any(ebic_ctx* h, const Pop& pop, EvalArgs a, cudaStream_
     if (a.dec) EBIC_CUDA_TRY(cudaMemsetAsync(a.dec, 0, (size_t)a.P * sizeof(uint32_t), s));
   }
   uint32_t* tk = h->tickets.as<uint32_t>();
+  count_launches(1);
   if (path == EBIC_PATH_BITMASK && lane_kernel) {
     const int64_t threads = (int64_t)a.P * VP;
     const unsigned blocks = (unsigned)((threads + 255) / 256);
@@ -567,6 +575,7 @@ ebic_status build_pair_table(ebic_ctx* h, cudaStream_t s) {
   h->LT_bytes = bytes;
   dim3 grid((unsigned)((h->W + 31) / 32), (unsigned)((h->C + 7) / 8));
   k_pair_table<<<grid, 256, 0, s>>>(h->A_c, h->C, h->R_pad, h->W, h->LT);
+  count_launches(1);
   EBIC_CUDA_TRY(cudaGetLastError());
   return EBIC_OK;
 }
@@ -625,6 +634,7 @@ static ebic_status place(ebic_ctx* h, const float* rowmajor_dev, cudaStream_t s)
   EBIC_CUDA_TRY(cudaMemcpyAsync(h->LN, ln, nln * sizeof(double), cudaMemcpyHostToDevice, s));
   dim3 grid((unsigned)(h->R_pad / 32), (unsigned)((h->C + 31) / 32));
   k_load_colmajor<<<grid, 256, 0, s>>>(rowmajor_dev, h->R, h->C, h->R_pad, h->A_c);
+  count_launches(1);
   EBIC_CUDA_TRY(cudaGetLastError());
   // The pinned LN staging is reused by later calls: finish the copy first.
   EBIC_CUDA_TRY(cudaStreamSynchronize(s));
@@ -641,6 +651,7 @@ using namespace ebic;
 extern "C" {
 
 const char* ebic_last_error(void) { return g_last_error; }
+uint64_t ebic_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 int32_t ebic_abi_version(void) { return EBIC_ABI_VERSION; }
 
 ebic_status ebic_load_matrix(const float* host_rowmajor, int32_t rows, int32_t cols,
