@@ -151,6 +151,7 @@ class EvalExpression:
                 "rows": self.R, "cols": self.C, "population": self.P,
                 "series_len": [self.LMIN, self.LMAX], "sigma": self.SIGMA,
                 "support_path": "bitmask", "support_mode": "inc",
+                "launch_shape": getattr(self, "tuning", None),
                 "l2": "flushed before every timed step (512 MiB overwrite)"}
 
     def units_per_step(self) -> int:          # candidate x row tests per step
@@ -165,7 +166,10 @@ class EvalExpression:
         self.d_cols = torch.from_numpy(self.cols).to(dev)
         self.d_inc = torch.zeros(self.P, dtype=torch.int32, device=dev)
         self.d_fit = torch.zeros(self.P, dtype=torch.float64, device=dev)
-        self.launches_per_step = 1
+        # one-time autotuning of the launch shape on this population (untimed)
+        self.tuning, self.tuned_us = eb.ebic_autotune_eval(
+            self.h, self.d_off, self.d_cols, self.P, len(self.cols), self.SIGMA,
+            eb.SUPPORT_INC, self.d_inc, None, self.d_fit)
         torch.cuda.synchronize()
 
     def step_gpu(self, torch, eb, stream):

@@ -101,9 +101,10 @@ ebic_status ebic_matrix_shape(ebic_handle h, int32_t* rows, int32_t* cols);
 
 /* ---------------------------------------------------------------------------
  * Pair bitmask table (derived from the pairwise count #{k : a_kp < a_kq} of
- * the "Motivation" section).  Word w of entry (p, q) holds bit r set iff
- * a[32w + r][p] < a[32w + r][q] (IEEE; NaN and ties give 0; rows past the end
- * give 0).  Layout: uint32 [cols][cols][words], words = padded rows / 32.
+ * the "Motivation" section).  Layout: uint32 [cols][cols][words], words =
+ * padded rows / 32; words 4b .. 4b + 3 of entry (p, q) cover rows 128b ..
+ * 128b + 127, and bit l of word 4b + i is set iff row k = 128b + 4l + i has
+ * a[k][p] < a[k][q] (IEEE; NaN and ties give 0; rows past the end give 0).
  * Size cols^2 * words * 4 bytes; the call fails with EBIC_ERR_OOM if that does
  * not fit.  Built on `stream`.  ebic_pair_table_bytes reports the size the
  * table would take (0 if not built yet in *built).
@@ -118,15 +119,37 @@ ebic_status ebic_read_pair_words(ebic_handle h, int32_t p, int32_t q, int32_t w0
  * automatic choice).  EBIC_PATH_BITMASK builds the table if needed. */
 ebic_status ebic_set_path(ebic_handle h, int32_t path);
 
-/* Launch shape of later evaluations (used by the autotuner; 0 = automatic).
- * group_lanes: 32 gives every series (part) a whole warp on the bitmask path;
- * 1..16 (a power of two) gives one lane per 16-byte vector of a table entry,
- * allowed when an entry has at most 32 vectors (up to 4096 rows).
- * vecs_bitmask / vecs_gather: 16-byte vectors of one table entry / one column
- * that one warp walks before handing the rest of the series to another warp
- * (rounded to a multiple of 32).  Results do not depend on these. */
-ebic_status ebic_set_eval_tuning(ebic_handle h, int32_t group_lanes, int32_t vecs_bitmask,
-                                 int32_t vecs_gather);
+/* Launch shape of later evaluations (set by the autotuner or by hand; every
+ * field 0 = automatic).  Results never depend on these.
+ *   kernel: bitmask path only -- 1 = one lane per 16-byte vector of a table
+ *     entry (entries of at most 32 vectors, i.e. up to 4,096 rows), 2 = one
+ *     warp per series part, 0 = lane kernel up to 2,048 rows, else warp kernel.
+ *   vecs_per_part_bitmask / vecs_per_part_gather: 16-byte vectors of a table
+ *     entry / of a column that one warp walks before the rest of the series
+ *     goes to another warp (rounded to a multiple of 32).
+ *   batch_steps: AND steps fetched between two early-exit tests (4 or 8).
+ *   vecs_per_lane: 16-byte vectors each lane of the warp kernel carries
+ *     (1, 2 or 4; 4 only with batch_steps 4).  Series that need the falling
+ *     count use batch_steps 4 and one vector per lane. */
+typedef struct {
+  int32_t kernel;
+  int32_t vecs_per_part_bitmask;
+  int32_t vecs_per_part_gather;
+  int32_t batch_steps;
+  int32_t vecs_per_lane;
+} ebic_eval_tuning_t;
+/* NULL restores the automatic choice. */
+ebic_status ebic_set_eval_tuning(ebic_handle h, const ebic_eval_tuning_t* tuning);
+ebic_status ebic_get_eval_tuning(ebic_handle h, ebic_eval_tuning_t* out);
+/* Autotuner: evaluates the given device population (arguments as for
+ * ebic_eval_population_dev, which it is) under a short list of launch shapes
+ * for the handle's current path, timing each with CUDA events on `stream`, and
+ * keeps the fastest for later evaluations.  Synchronises `stream`.  *chosen
+ * and *best_us (nullable) receive the shape and its time per launch. */
+ebic_status ebic_autotune_eval(ebic_handle h, const int32_t* d_offsets, const int32_t* d_cols,
+                               int32_t P, int32_t total_cols, int32_t sigma, int32_t support_mode,
+                               uint32_t* d_inc, uint32_t* d_dec, double* d_fitness, void* stream,
+                               ebic_eval_tuning_t* chosen, float* best_us);
 
 /* ---------------------------------------------------------------------------
  * Population evaluation: Step 4 of the "EBIC Algorithm" section with Eq. (1).

@@ -22,7 +22,8 @@ from . import _build
 __all__ = [
     "EbicError", "build", "lib", "ebic_kernel_launches", "ebic_load_matrix", "ebic_load_matrix_dev", "ebic_free",
     "ebic_matrix_shape", "ebic_build_pair_table", "ebic_pair_table_bytes",
-    "ebic_read_pair_words", "ebic_set_path", "ebic_set_eval_tuning", "ebic_eval_population",
+    "ebic_read_pair_words", "ebic_set_path", "ebic_set_eval_tuning", "ebic_get_eval_tuning",
+    "ebic_autotune_eval", "ebic_eval_population",
     "ebic_eval_population_dev", "ebic_check_device_error", "ebic_default_params",
     "ebic_run_init", "ebic_run_step", "ebic_get_toprank", "ebic_get_population",
     "ebic_run_generations", "Params", "Stats", "PATH_AUTO", "PATH_GATHER", "PATH_BITMASK",
@@ -80,7 +81,9 @@ _SIGS = {
     "ebic_pair_table_bytes": ([_P, _P, _P], _I32),
     "ebic_read_pair_words": ([_P, _I32, _I32, _I32, _I32, _P], _I32),
     "ebic_set_path": ([_P, _I32], _I32),
-    "ebic_set_eval_tuning": ([_P, _I32, _I32, _I32], _I32),
+    "ebic_set_eval_tuning": ([_P, _P], _I32),
+    "ebic_get_eval_tuning": ([_P, _P], _I32),
+    "ebic_autotune_eval": ([_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P], _I32),
     "ebic_eval_population": ([_P, _P, _P, _I32, _I32, _I32, _P, _P, _P], _I32),
     "ebic_eval_population_dev": ([_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P], _I32),
     "ebic_check_device_error": ([_P], _I32),
@@ -203,9 +206,36 @@ def ebic_set_path(h, path: int):
     _check(lib().ebic_set_path(h, path))
 
 
-def ebic_set_eval_tuning(h, group_lanes: int = 0, vecs_bitmask: int = 0,
-                         vecs_gather: int = 0):
-    _check(lib().ebic_set_eval_tuning(h, group_lanes, vecs_bitmask, vecs_gather))
+class EvalTuning(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("vecs_per_part_bitmask", ctypes.c_int32),
+                ("vecs_per_part_gather", ctypes.c_int32), ("batch_steps", ctypes.c_int32),
+                ("vecs_per_lane", ctypes.c_int32)]
+
+
+def ebic_set_eval_tuning(h, kernel: int = 0, vecs_per_part_bitmask: int = 0,
+                         vecs_per_part_gather: int = 0, batch_steps: int = 0,
+                         vecs_per_lane: int = 0):
+    t = EvalTuning(kernel, vecs_per_part_bitmask, vecs_per_part_gather, batch_steps,
+                   vecs_per_lane)
+    _check(lib().ebic_set_eval_tuning(h, ctypes.byref(t)))
+
+
+def ebic_get_eval_tuning(h) -> dict:
+    t = EvalTuning()
+    _check(lib().ebic_get_eval_tuning(h, ctypes.byref(t)))
+    return {f: getattr(t, f) for f, _ in EvalTuning._fields_}
+
+
+def ebic_autotune_eval(h, d_offsets, d_cols, P: int, total_cols: int, sigma: int,
+                       support_mode: int, d_inc, d_dec, d_fitness, stream=None):
+    """Times launch shapes on this device population; returns (shape dict, us)."""
+    t = EvalTuning()
+    us = ctypes.c_float()
+    _check(lib().ebic_autotune_eval(h, _dev(d_offsets), _dev(d_cols), int(P), int(total_cols),
+                                    int(sigma), int(support_mode), _dev(d_inc), _dev(d_dec),
+                                    _dev(d_fitness), _stream(stream), ctypes.byref(t),
+                                    ctypes.byref(us)))
+    return {f: getattr(t, f) for f, _ in EvalTuning._fields_}, us.value
 
 
 def ebic_eval_population(h, offsets, cols, sigma: int, support_mode: int = SUPPORT_INC,

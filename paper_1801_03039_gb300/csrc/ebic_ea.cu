@@ -1,22 +1,1122 @@
-// Generation loop (Steps 1-5) -- placeholder until the device EA lands.
+// The generation loop of EBIC on the device: Steps 1-5 of the "EBIC
+// Algorithm" section (elitism, tournament selection with the crowding
+// penalty, crossover and the four mutations of Fig. 1, the tabu list, Step 4
+// evaluation and the top-rank list), kept entirely on one GPU.
+//
+// One generation = five launches, captured once into a CUDA graph and
+// replayed; every kernel reads the generation number and the stop flag from a
+// device control block, so replays need no host involvement:
+//   k_spec         parallel over attempts j < 2P + 1: draws the attempt's
+//                  random numbers (Philox-4x32-10, keyed by seed, generation,
+//                  attempt) and builds the child for EVERY possible outcome of
+//                  its tournament(s); probes the tabu list for each.
+//   k_build        one CTA: the sequential part of Step 3 -- elites, then the
+//                  attempts in order, each tournament decided with the penalty
+//                  counts as they stand, the precomputed child picked,
+//                  duplicates (tabu or earlier in this generation) counted as
+//                  hits; more than P hits stop the run.
+//   k_tabu_insert  parallel: the accepted children enter the tabu hash table.
+//   K3 evaluation  support + Eq. (1) of the new population (ebic_matrix.cu).
+//   k_rank         one CTA: sorts by fitness and runs the Step 5 top-rank
+//                  update.
+// At most 2P + 1 attempts are ever needed: every attempt either adds one of at
+// most P individuals or is one of at most P + 1 hits.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
 #include "ebic_internal.cuh"
 
 namespace ebic {
-void ea_release(ebic_ctx*) {}
+
+// ---------------------------------------------------------------------------
+// device state
+// ---------------------------------------------------------------------------
+struct Ctl {
+  int32_t gen;          // generation being built (0 = Step 1)
+  int32_t stop;         // nonzero once the run has stopped
+  int32_t stop_reason;  // 1 tabu hits > P, 2 Step 1 could not fill the population, 3 internal
+  int32_t n_top;        // records in the top-rank list
+  int32_t n_elite;      // elites at the front of the current population
+  int32_t last_hits;    // tabu hits in the last Step 3
+  int32_t gens_done;    // Steps 2-5 passes completed
+  int32_t pad;
+  long long hits_total, attempts_total, evals_total, exact_total;
+};
+
+struct EaDev {
+  int32_t P, C, S, Lmin, Lmax, k, T, mode, J, ncombo, WC, pad;
+  double tau, elite_frac, pc;
+  uint64_t seed;
+  // archive: entry g * P + i is individual i of generation g
+  uint16_t* seq;
+  int32_t* len;
+  double* fit;
+  float* lnf;
+  // tabu list: open addressing, key = 64-bit hash (0 = empty), ref = archive entry
+  unsigned long long* tkey;
+  int32_t* tref;
+  unsigned long long tmask;
+  // attempts of the current generation
+  int32_t* sp_ent;              // [J][8] entrants (first tournament, then second)
+  int32_t* sp_cross;            // [J]
+  uint16_t* sp_child;           // [J * ncombo][S]
+  int32_t* sp_clen;             // [J * ncombo]
+  unsigned long long* sp_hash;  // [J * ncombo]
+  int32_t* sp_tabu;             // [J * ncombo] child already in the tabu list
+  // top-rank list (archive entries and their fitness), capacity T + P
+  int32_t* list_ref;
+  double* list_f;
+  // crowding penalty: base^(S/L) for S in [0, L P], from the host C library
+  const double* pow_tab;
+  const long long* pow_off;     // [Lmax + 1]
+  const float* c_over_L;        // [Lmax + 1] log(base) / L as float
+  Ctl* ctl;
+};
+
+constexpr int kMaxLen = EBIC_MAX_EA_LEN;
+
+// ---------------------------------------------------------------------------
+// Philox-4x32-10 (Salmon et al., SC'11): counter (j, g, block, 0), key = seed.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void philox_block(uint32_t j, uint32_t g, uint32_t blk, uint64_t seed,
+                                             uint32_t out[4]) {
+  uint32_t x0 = j, x1 = g, x2 = blk, x3 = 0u;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
+    const uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
+    const uint32_t y0 = hi1 ^ x1 ^ k0;
+    const uint32_t y2 = hi0 ^ x3 ^ k1;
+    x0 = y0;
+    x1 = lo1;
+    x2 = y2;
+    x3 = lo0;
+  }
+  out[0] = x0;
+  out[1] = x1;
+  out[2] = x2;
+  out[3] = x3;
+}
+
+// Draw d of attempt j in generation g (word d % 4 of block d / 4).
+struct Draws {
+  uint64_t seed;
+  uint32_t g, j;
+  int blk;
+  uint32_t w[4];
+  __device__ Draws(uint64_t s, uint32_t gg, uint32_t jj) : seed(s), g(gg), j(jj), blk(-1) {}
+  __device__ uint32_t operator()(int d) {
+    if (d / 4 != blk) {
+      blk = d / 4;
+      philox_block(j, g, (uint32_t)blk, seed, w);
+    }
+    return w[d & 3];
+  }
+};
+
+__device__ __forceinline__ uint32_t below(uint32_t r, uint32_t n) {
+  return (uint32_t)(((unsigned long long)r * n) >> 32);
+}
+
+// k-th (0-based) column, in increasing order, that is not among s[0 .. L):
+// start from k and step over every used column that is not above the answer.
+__device__ int kth_absent(const uint16_t* s, int L, uint32_t k) {
+  uint16_t t[kMaxLen];
+  for (int i = 0; i < L; ++i) {
+    uint16_t v = s[i];
+    int m = i;
+    while (m > 0 && t[m - 1] > v) {
+      t[m] = t[m - 1];
+      --m;
+    }
+    t[m] = v;
+  }
+  uint32_t c = k;
+  for (int i = 0; i < L; ++i) {
+    if (t[i] <= c) ++c;
+    else break;
+  }
+  return (int)c;
+}
+
+__device__ __forceinline__ bool holds(const uint16_t* s, int L, int c) {
+  for (int i = 0; i < L; ++i)
+    if (s[i] == c) return true;
+  return false;
+}
+
+// The four mutations (Fig. 1a-d): one, chosen uniformly among those that keep
+// the series in [Lmin, Lmax] with distinct columns (insert, delete, swap,
+// substitute in that order).
+__device__ void mutate(uint16_t* x, int& L, int C, int Lmin, int Lmax, uint32_t rt, uint32_t r1,
+                       uint32_t r2) {
+  int allowed[4];
+  int n = 0;
+  if (L < Lmax && L < C) allowed[n++] = 0;
+  if (L > Lmin) allowed[n++] = 1;
+  if (L >= 2) allowed[n++] = 2;
+  if (L < C) allowed[n++] = 3;
+  if (n == 0) return;
+  const int kind = allowed[below(rt, (uint32_t)n)];
+  if (kind == 0) {
+    const int pos = (int)below(r1, (uint32_t)(L + 1));
+    const int col = kth_absent(x, L, below(r2, (uint32_t)(C - L)));
+    for (int i = L; i > pos; --i) x[i] = x[i - 1];
+    x[pos] = (uint16_t)col;
+    ++L;
+  } else if (kind == 1) {
+    const int pos = (int)below(r1, (uint32_t)L);
+    for (int i = pos; i + 1 < L; ++i) x[i] = x[i + 1];
+    --L;
+  } else if (kind == 2) {
+    const int i = (int)below(r1, (uint32_t)L);
+    int j = (int)below(r2, (uint32_t)(L - 1));
+    if (j >= i) ++j;
+    const uint16_t t = x[i];
+    x[i] = x[j];
+    x[j] = t;
+  } else {
+    const int pos = (int)below(r1, (uint32_t)L);
+    x[pos] = (uint16_t)kth_absent(x, L, below(r2, (uint32_t)(C - L)));
+  }
+}
+
+// 64-bit hash of an ordered series (never 0: 0 marks an empty slot).
+__device__ __forceinline__ unsigned long long seq_hash(const uint16_t* s, int L) {
+  unsigned long long h = 0xcbf29ce484222325ull ^ (unsigned long long)L;
+  h *= 0x100000001b3ull;
+  for (int i = 0; i < L; ++i) {
+    h ^= s[i];
+    h *= 0x100000001b3ull;
+  }
+  h ^= h >> 30;
+  h *= 0xbf58476d1ce4e5b9ull;
+  h ^= h >> 27;
+  h *= 0x94d049bb133111ebull;
+  h ^= h >> 31;
+  return h | 1ull;
+}
+
+__device__ __forceinline__ bool same_series(const uint16_t* a, int La, const uint16_t* b, int Lb) {
+  if (La != Lb) return false;
+  for (int i = 0; i < La; ++i)
+    if (a[i] != b[i]) return false;
+  return true;
+}
+
+__device__ bool tabu_contains(const EaDev& d, unsigned long long key, const uint16_t* s, int L) {
+  unsigned long long i = key & d.tmask;
+  for (unsigned long long n = 0; n <= d.tmask; ++n) {
+    const unsigned long long k = d.tkey[i];
+    if (k == 0ull) return false;
+    if (k == key) {
+      const int32_t r = d.tref[i];
+      if (r >= 0 && same_series(d.seq + (size_t)r * d.S, d.len[r], s, L)) return true;
+    }
+    i = (i + 1) & d.tmask;
+  }
+  return false;
+}
+
+// ---------------------------------------------------------------------------
+// k_spec: every child an attempt can produce.  Thread = (attempt, combo);
+// combo = ta * k + tb names the winning positions of the two tournaments.
+// ---------------------------------------------------------------------------
+template <bool INIT>
+__global__ void __launch_bounds__(128) k_spec(EaDev d) {
+  if (*(volatile int32_t*)&d.ctl->stop) return;
+  const int g = d.ctl->gen;
+  const int nc = INIT ? 1 : d.ncombo;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (tid >= (long long)d.J * nc) return;
+  const int j = (int)(tid / nc), c = (int)(tid % nc);
+  Draws r(d.seed, (uint32_t)g, (uint32_t)j);
+  uint16_t x[kMaxLen];
+  int L = 0;
+  if (INIT) {
+    // Step 1: length uniform in [Lmin, Lmax], then distinct uniform columns.
+    L = d.Lmin + (int)below(r(0), (uint32_t)(d.Lmax - d.Lmin + 1));
+    for (int i = 0; i < L; ++i) x[i] = (uint16_t)kth_absent(x, i, below(r(1 + i), (uint32_t)(d.C - i)));
+  } else {
+    const int k = d.k;
+    const uint32_t P = (uint32_t)d.P;
+    const int ta = c / k, tb = c % k;
+    const bool cross = (double)r(k) * 0x1p-32 < d.pc;
+    if (c == 0) {
+      for (int t = 0; t < k; ++t) d.sp_ent[(size_t)j * 8 + t] = (int32_t)below(r(t), P);
+      for (int t = 0; t < k; ++t) d.sp_ent[(size_t)j * 8 + 4 + t] = (int32_t)below(r(k + 1 + t), P);
+      d.sp_cross[j] = cross ? 1 : 0;
+    }
+    const long long prev = (long long)(g - 1) * d.P;
+    const int ia = (int)below(r(ta), P);
+    const uint16_t* a = d.seq + (size_t)(prev + ia) * d.S;
+    const int La = d.len[prev + ia];
+    for (int i = 0; i < La; ++i) x[i] = a[i];
+    L = La;
+    if (cross) {
+      const int ib = (int)below(r(k + 1 + tb), P);
+      const uint16_t* b = d.seq + (size_t)(prev + ib) * d.S;
+      const int Lb = d.len[prev + ib];
+      const int cut_a = 1 + (int)below(r(2 * k + 1), (uint32_t)La);
+      const int cut_b = (int)below(r(2 * k + 2), (uint32_t)Lb);
+      uint16_t y[kMaxLen];
+      int Ly = 0;
+      for (int i = 0; i < cut_a; ++i) y[Ly++] = a[i];
+      for (int i = cut_b; i < Lb; ++i) {
+        if (Ly >= d.Lmax) break;
+        if (!holds(y, Ly, b[i])) y[Ly++] = b[i];
+      }
+      if (Ly >= d.Lmin) {
+        for (int i = 0; i < Ly; ++i) x[i] = y[i];
+        L = Ly;
+      }
+    }
+    mutate(x, L, d.C, d.Lmin, d.Lmax, r(2 * k + 3), r(2 * k + 4), r(2 * k + 5));
+  }
+  uint16_t* out = d.sp_child + (size_t)tid * d.S;
+  for (int i = 0; i < L; ++i) out[i] = x[i];
+  d.sp_clen[tid] = L;
+  const unsigned long long h = seq_hash(x, L);
+  d.sp_hash[tid] = h;
+  d.sp_tabu[tid] = INIT ? 0 : (tabu_contains(d, h, x, L) ? 1 : 0);
+}
+
+// ---------------------------------------------------------------------------
+// Tournament comparison.  Penalised fitness p = f / base^(S/L) in binary64,
+// exactly as the reading of the paper defines it.  Fast path: compare the
+// log-domain scores ln f - S * ln(base) / L in float; when they differ by more
+// than a margin that bounds every rounding error of both the float scores and
+// the binary64 values (pow within 1 ulp, S / L rounded once, the quotient
+// rounded once), the sign is the binary64 sign.  Otherwise -- and whenever a
+// value might be zero, subnormal or infinite -- compute the binary64 values
+// with the host-built power table and compare them exactly.
+// ---------------------------------------------------------------------------
+struct Entrant {
+  double f;
+  float lnf;
+  int32_t S, L, idx;
+};
+
+__device__ __forceinline__ bool beats(const Entrant& x, const Entrant& y, const EaDev& d,
+                                      const float* cL, long long& exact) {
+  if (x.idx == y.idx) return false;
+  if (x.f == 0.0 && y.f == 0.0) return x.idx < y.idx;
+  const float cx = (float)x.S * cL[x.L];
+  const float cy = (float)y.S * cL[y.L];
+  const bool safe_x = x.f == 0.0 || (cx < 700.f && x.lnf - cx > -700.f);
+  const bool safe_y = y.f == 0.0 || (cy < 700.f && y.lnf - cy > -700.f);
+  if (safe_x && safe_y) {
+    if (x.f == 0.0) return false;
+    if (y.f == 0.0) return true;
+    const float gx = x.lnf - cx, gy = y.lnf - cy;
+    const float margin = 0x1p-16f * (fabsf(x.lnf) + fabsf(y.lnf) + cx + cy + 1.f);
+    if (gx - gy > margin) return true;
+    if (gy - gx > margin) return false;
+  }
+  ++exact;
+  const double px = __ddiv_rn(x.f, d.pow_tab[d.pow_off[x.L] + x.S]);
+  const double py = __ddiv_rn(y.f, d.pow_tab[d.pow_off[y.L] + y.S]);
+  return px > py || (px == py && x.idx < y.idx);
+}
+
+// Warp-cooperative tournament over entrants ent[0 .. k) of the previous
+// population; every lane returns the winner's position in ent.
+__device__ int tournament(const EaDev& d, const int32_t* ent, int k, const uint32_t* pen,
+                          const float* cL, long long prev, int lane, long long& exact) {
+  Entrant best{}, cur{};
+  int best_t = 0;
+  for (int t = 0; t < k; ++t) {
+    const int i = ent[t];
+    const long long e = prev + i;
+    const int L = d.len[e];
+    const uint16_t* s = d.seq + (size_t)e * d.S;
+    uint32_t part = 0;
+    for (int c = lane; c < L; c += 32) part += pen[s[c]];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    cur.f = d.fit[e];
+    cur.lnf = d.lnf[e];
+    cur.S = (int32_t)part;
+    cur.L = L;
+    cur.idx = i;
+    if (t == 0 || beats(cur, best, d, cL, exact)) {
+      best = cur;
+      best_t = t;
+    }
+  }
+  // position of the first entrant with the winning index (the child table is
+  // indexed by position; equal indices give equal children)
+  for (int t = 0; t < best_t; ++t)
+    if (ent[t] == best.idx) return t;
+  return best_t;
+}
+
+// Within-generation set of accepted children (shared memory, open addressing).
+__device__ bool wset_contains(const unsigned long long* hk, const int32_t* hr, int hmask,
+                              unsigned long long key, const uint16_t* s, int L, const EaDev& d) {
+  int i = (int)(key & (unsigned long long)hmask);
+  for (int n = 0; n <= hmask; ++n) {
+    const unsigned long long k = hk[i];
+    if (k == 0ull) return false;
+    if (k == key) {
+      const int32_t r = hr[i];
+      if (same_series(d.seq + (size_t)r * d.S, d.len[r], s, L)) return true;
+    }
+    i = (i + 1) & hmask;
+  }
+  return false;
+}
+
+__device__ void wset_insert(unsigned long long* hk, int32_t* hr, int hmask, unsigned long long key,
+                            int32_t ref) {
+  int i = (int)(key & (unsigned long long)hmask);
+  for (int n = 0; n <= hmask; ++n) {
+    if (hk[i] == 0ull) {
+      hk[i] = key;
+      hr[i] = ref;
+      return;
+    }
+    i = (i + 1) & hmask;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_build: Steps 2-3 (or the acceptance part of Step 1), one warp.
+// Shared memory: pen[C] | hkey[H] | href[H] | cL[Lmax + 1].
+// ---------------------------------------------------------------------------
+template <bool INIT>
+__global__ void __launch_bounds__(32) k_build(EaDev d, int hmask) {
+  extern __shared__ unsigned long long smem_u64[];
+  if (*(volatile int32_t*)&d.ctl->stop) return;
+  const int lane = threadIdx.x;
+  const int g = d.ctl->gen;
+  const int H = hmask + 1;
+  unsigned long long* hkey = smem_u64;
+  int32_t* href = reinterpret_cast<int32_t*>(hkey + H);
+  uint32_t* pen = reinterpret_cast<uint32_t*>(href + H);
+  float* cL = reinterpret_cast<float*>(pen + d.C);
+  for (int i = lane; i < H; i += 32) hkey[i] = 0ull;
+  for (int i = lane; i < d.C; i += 32) pen[i] = 0u;
+  for (int i = lane; i <= d.Lmax; i += 32) cL[i] = d.c_over_L[i];
+  __syncwarp();
+  const long long base = (long long)g * d.P;
+  const long long prev = base - d.P;
+  int n = 0, E = 0;
+  if (!INIT) {
+    // Step 2: the best ceil(elite_frac * |list|) records, penalty counts raised.
+    E = (int)ceil(d.elite_frac * (double)d.ctl->n_top);
+    if (E > d.P) E = d.P;
+    for (int e = 0; e < E; ++e) {
+      const int32_t src = d.list_ref[e];
+      const int L = d.len[src];
+      const uint16_t* s = d.seq + (size_t)src * d.S;
+      uint16_t* o = d.seq + (size_t)(base + e) * d.S;
+      for (int c = lane; c < L; c += 32) {
+        o[c] = s[c];
+        pen[s[c]] += 1u;
+      }
+      if (lane == 0) d.len[base + e] = L;
+      __syncwarp();
+    }
+    n = E;
+  }
+  int hits = 0, stopped = 0;
+  long long attempts = 0, exact = 0;
+  const int nc = INIT ? 1 : d.ncombo;
+  for (int j = 0; n < d.P; ++j) {
+    if (j >= d.J) {
+      stopped = 3;
+      break;
+    }
+    ++attempts;
+    int combo = 0;
+    if (!INIT) {
+      int32_t ent[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) ent[t] = d.sp_ent[(size_t)j * 8 + t];
+      const int ta = tournament(d, ent, d.k, pen, cL, prev, lane, exact);
+      int tb = 0;
+      if (d.sp_cross[j]) tb = tournament(d, ent + 4, d.k, pen, cL, prev, lane, exact);
+      combo = ta * d.k + tb;
+    }
+    const size_t rec = (size_t)j * nc + combo;
+    const int L = d.sp_clen[rec];
+    const unsigned long long key = d.sp_hash[rec];
+    const uint16_t* child = d.sp_child + rec * d.S;
+    bool dup = d.sp_tabu[rec] != 0;
+    if (!dup) dup = wset_contains(hkey, href, hmask, key, child, L, d);
+    __syncwarp();
+    if (dup) {
+      if (++hits > d.P) {
+        stopped = INIT ? 2 : 1;
+        break;
+      }
+      continue;
+    }
+    const long long dst = base + n;
+    uint16_t* o = d.seq + (size_t)dst * d.S;
+    for (int c = lane; c < L; c += 32) {
+      o[c] = child[c];
+      pen[child[c]] += 1u;
+    }
+    if (lane == 0) {
+      d.len[dst] = L;
+      wset_insert(hkey, href, hmask, key, (int32_t)dst);
+    }
+    __syncwarp();
+    ++n;
+  }
+  if (lane == 0) {
+    Ctl* ctl = d.ctl;
+    ctl->last_hits = hits;
+    ctl->hits_total += hits;
+    ctl->attempts_total += attempts;
+    ctl->exact_total += exact;
+    ctl->n_elite = E;
+    if (stopped) {
+      ctl->stop_reason = stopped;
+      __threadfence();
+      ctl->stop = 1;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_tabu_insert: the generation's new (non-elite) individuals enter the tabu
+// list.  Lookups happen in later launches only.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_tabu_insert(EaDev d) {
+  if (*(volatile int32_t*)&d.ctl->stop) return;
+  const int g = d.ctl->gen;
+  const int slot = d.ctl->n_elite + (int)(blockIdx.x * blockDim.x + threadIdx.x);
+  if (slot >= d.P) return;
+  const long long e = (long long)g * d.P + slot;
+  const unsigned long long key = seq_hash(d.seq + (size_t)e * d.S, d.len[e]);
+  unsigned long long i = key & d.tmask;
+  for (unsigned long long n = 0; n <= d.tmask; ++n) {
+    if (atomicCAS(&d.tkey[i], 0ull, key) == 0ull) {
+      d.tref[i] = (int32_t)e;
+      return;
+    }
+    i = (i + 1) & d.tmask;
+  }
+  atomicExch(&d.ctl->stop_reason, 3);   // table full: cannot happen at load <= 1/2
+  atomicExch(&d.ctl->stop, 1);
+}
+
+// ---------------------------------------------------------------------------
+// k_rank: Step 5 (and the list part of Step 1).  One CTA of 1,024 threads.
+// The population is sorted by decreasing fitness (ties: lower slot first),
+// then visited in that order: an individual joins unless a listed record of
+// higher or equal fitness overlaps it (|a & b| / min(|a|, |b|) > tau); when it
+// joins it evicts the overlapping records of lower fitness and goes after all
+// records of higher or equal fitness.  Finally the list keeps its T best.
+//
+// The visit stops early once T listed records have a fitness strictly above
+// the current individual: records above it can only be evicted by fitter
+// individuals (already visited), and everything visited from here on ranks
+// below those T records, so it would be cut by the final trim -- and what it
+// could still evict also ranks below them.  The result is the same list.
+// ---------------------------------------------------------------------------
+constexpr int kRankThreads = 1024;
+
+__global__ void __launch_bounds__(kRankThreads) k_rank(EaDev d, int Pp) {
+  extern __shared__ unsigned long long smem_u64[];
+  if (*(volatile int32_t*)&d.ctl->stop) return;
+  const int tid = threadIdx.x;
+  const int g = d.ctl->gen;
+  const long long base = (long long)g * d.P;
+  const int cap = d.T + d.P;
+  unsigned long long* skey = smem_u64;                             // [Pp]
+  int32_t* sidx = reinterpret_cast<int32_t*>(skey + Pp);           // [Pp]
+  double* lf = reinterpret_cast<double*>(sidx + Pp);               // [cap]
+  double* lf2 = lf + cap;                                          // [cap]
+  int32_t* lr = reinterpret_cast<int32_t*>(lf2 + cap);             // [cap]
+  int32_t* lr2 = lr + cap;                                         // [cap]
+  uint8_t* ov = reinterpret_cast<uint8_t*>(lr2 + cap);             // [cap]
+  uint32_t* xbits = reinterpret_cast<uint32_t*>(ov + ((cap + 15) & ~15));   // [WC]
+  __shared__ int s_warp[32];
+
+  // sort keys: ascending (~bits(f), slot) == descending fitness, then slot
+  for (int i = tid; i < Pp; i += kRankThreads) {
+    if (i < d.P) {
+      skey[i] = ~(unsigned long long)__double_as_longlong(d.fit[base + i]);
+      sidx[i] = i;
+    } else {
+      skey[i] = ~0ull;
+      sidx[i] = 0x7fffffff;
+    }
+  }
+  __syncthreads();
+  for (int size = 2; size <= Pp; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = tid; i < Pp; i += kRankThreads) {
+        const int jx = i ^ stride;
+        if (jx > i) {
+          const bool up = (i & size) == 0;
+          const unsigned long long ka = skey[i], kb = skey[jx];
+          const int ia = sidx[i], ib = sidx[jx];
+          const bool a_gt_b = ka > kb || (ka == kb && ia > ib);
+          if (a_gt_b == up) {
+            skey[i] = kb;
+            skey[jx] = ka;
+            sidx[i] = ib;
+            sidx[jx] = ia;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  int n = d.ctl->n_top;
+  for (int i = tid; i < n; i += kRankThreads) {
+    lr[i] = d.list_ref[i];
+    lf[i] = d.list_f[i];
+  }
+  __syncthreads();
+
+  for (int oi = 0; oi < d.P; ++oi) {
+    const int xi = sidx[oi];
+    const long long xe = base + xi;
+    const double xf = d.fit[xe];
+    const int xL = d.len[xe];
+    const uint16_t* xs = d.seq + (size_t)xe * d.S;
+    int above = 0;
+    for (int t0 = 0; t0 < n; t0 += kRankThreads) {
+      const int t = t0 + tid;
+      above += __syncthreads_count(t < n && lf[t] > xf);
+    }
+    if (above >= d.T) break;                                   // see the note above
+    for (int w = tid; w < d.WC; w += kRankThreads) xbits[w] = 0u;
+    __syncthreads();
+    if (tid < xL) atomicOr(&xbits[xs[tid] >> 5], 1u << (xs[tid] & 31));
+    __syncthreads();
+    int blocked = 0;
+    for (int t0 = 0; t0 < n; t0 += kRankThreads) {
+      const int t = t0 + tid;
+      bool hit = false;
+      if (t < n) {
+        const int32_t r = lr[t];
+        const int L = d.len[r];
+        const uint16_t* s = d.seq + (size_t)r * d.S;
+        int inter = 0;
+        for (int c = 0; c < L; ++c) inter += (xbits[s[c] >> 5] >> (s[c] & 31)) & 1u;
+        const int mn = L < xL ? L : xL;
+        const bool o = (double)inter > d.tau * (double)mn;
+        ov[t] = o ? 1 : 0;
+        hit = o && lf[t] >= xf;
+      }
+      blocked += __syncthreads_or(hit);
+    }
+    if (blocked) continue;
+    // evict overlapping records of lower fitness (stable compaction into lr2/lf2)
+    int m = 0;
+    for (int t0 = 0; t0 < n; t0 += kRankThreads) {
+      const int t = t0 + tid;
+      const bool keep = t < n && !(ov[t] && lf[t] < xf);
+      const unsigned bal = __ballot_sync(0xffffffffu, keep);
+      const int lane = tid & 31, warp = tid >> 5;
+      if (lane == 0) s_warp[warp] = __popc(bal);
+      __syncthreads();
+      if (warp == 0) {
+        int v = s_warp[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+          const int u = __shfl_up_sync(0xffffffffu, v, o);
+          if (lane >= o) v += u;
+        }
+        s_warp[lane] = v;          // inclusive prefix over warps
+      }
+      __syncthreads();
+      const int before = (warp ? s_warp[warp - 1] : 0) + __popc(bal & ((1u << lane) - 1u));
+      if (keep) {
+        lr2[m + before] = lr[t];
+        lf2[m + before] = lf[t];
+      }
+      const int chunk_total = s_warp[31];
+      __syncthreads();
+      m += chunk_total;
+    }
+    // insert after every kept record of higher or equal fitness
+    int pos = 0;
+    for (int t0 = 0; t0 < m; t0 += kRankThreads) {
+      const int t = t0 + tid;
+      pos += __syncthreads_count(t < m && lf2[t] >= xf);
+    }
+    for (int t = tid; t < m; t += kRankThreads) {
+      const int dst = t < pos ? t : t + 1;
+      lr[dst] = lr2[t];
+      lf[dst] = lf2[t];
+    }
+    if (tid == 0) {
+      lr[pos] = (int32_t)xe;
+      lf[pos] = xf;
+    }
+    n = m + 1;
+    __syncthreads();
+  }
+  if (n > d.T) n = d.T;
+  for (int i = tid; i < n; i += kRankThreads) {
+    d.list_ref[i] = lr[i];
+    d.list_f[i] = lf[i];
+  }
+  if (tid == 0) {
+    Ctl* ctl = d.ctl;
+    ctl->n_top = n;
+    ctl->evals_total += d.P;
+    if (g > 0) ctl->gens_done = g;
+    ctl->gen = g + 1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct EaState {
+  ebic_params_t p{};
+  int32_t S = 0, J = 0, ncombo = 0, WC = 0, Pp = 0, hmask = 0;
+  long long entries = 0;
+  DevBuf seq, len, inc, dec, fit, lnf;
+  DevBuf tkey, tref;
+  DevBuf sp_ent, sp_cross, sp_child, sp_clen, sp_hash, sp_tabu;
+  DevBuf list_ref, list_f;
+  DevBuf pow_tab, pow_off, c_over_L;
+  DevBuf ctl, gather;
+  HostBuf h_ctl, h_gather;
+  size_t smem_build = 0, smem_rank = 0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  EaDev dev{};
+  ArchivePop apop{};
+  EvalArgs eargs{};
+  bool initialised = false;
+
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    for (DevBuf* b : {&seq, &len, &inc, &dec, &fit, &lnf, &tkey, &tref, &sp_ent, &sp_cross,
+                      &sp_child, &sp_clen, &sp_hash, &sp_tabu, &list_ref, &list_f, &pow_tab,
+                      &pow_off, &c_over_L, &ctl, &gather})
+      b->release();
+    h_ctl.release();
+    h_gather.release();
+    initialised = false;
+  }
+};
+
+void ea_release(ebic_ctx* h) {
+  if (h->ea) {
+    h->ea->release();
+    delete h->ea;
+    h->ea = nullptr;
+  }
+}
+
+static ebic_status validate(const ebic_ctx* h, const ebic_params_t* p) {
+  if (!p) return fail(EBIC_ERR_ARG, "null params");
+  if (h->C > 8192) return fail(EBIC_ERR_ARG, "the EA supports at most 8192 columns");
+  if (p->pop_size < 2 || p->pop_size > 4096)
+    return fail(EBIC_ERR_ARG, "pop_size %d outside [2, 4096]", p->pop_size);
+  if (p->len_min < 1 || p->len_max < p->len_min || p->len_max > h->C ||
+      p->len_max > EBIC_MAX_EA_LEN)
+    return fail(EBIC_ERR_ARG, "lengths [%d, %d] invalid for %d columns (max %d)", p->len_min,
+                p->len_max, h->C, EBIC_MAX_EA_LEN);
+  if (p->iterations < 0) return fail(EBIC_ERR_ARG, "negative iterations");
+  if (p->toprank_size < 1 || p->toprank_size > 4096)
+    return fail(EBIC_ERR_ARG, "toprank_size %d outside [1, 4096]", p->toprank_size);
+  if (p->tournament_k < 1 || p->tournament_k > EBIC_MAX_TOURNAMENT)
+    return fail(EBIC_ERR_ARG, "tournament_k %d outside [1, %d]", p->tournament_k,
+                EBIC_MAX_TOURNAMENT);
+  if (p->support_mode != EBIC_SUPPORT_INC && p->support_mode != EBIC_SUPPORT_INC_PLUS_DEC)
+    return fail(EBIC_ERR_ARG, "bad support mode");
+  if (!(p->overlap_tau >= 0.0 && p->overlap_tau <= 1.0)) return fail(EBIC_ERR_ARG, "tau");
+  if (!(p->elite_frac >= 0.0 && p->elite_frac <= 1.0)) return fail(EBIC_ERR_ARG, "elite_frac");
+  if (!(p->penalty_base >= 1.0 && p->penalty_base < 1e6)) return fail(EBIC_ERR_ARG, "base");
+  if (!(p->p_crossover >= 0.0 && p->p_crossover <= 1.0)) return fail(EBIC_ERR_ARG, "p_crossover");
+  return EBIC_OK;
+}
+
+static ebic_status launch_generation(ebic_ctx* h, EaState* st, bool init, cudaStream_t s) {
+  const EaDev& d = st->dev;
+  const int nc = init ? 1 : st->ncombo;
+  const long long threads = (long long)st->J * nc;
+  const unsigned sblocks = (unsigned)((threads + 127) / 128);
+  if (init) {
+    k_spec<true><<<sblocks, 128, 0, s>>>(d);
+    k_build<true><<<1, 32, st->smem_build, s>>>(d, st->hmask);
+  } else {
+    k_spec<false><<<sblocks, 128, 0, s>>>(d);
+    k_build<false><<<1, 32, st->smem_build, s>>>(d, st->hmask);
+  }
+  k_tabu_insert<<<(unsigned)((st->p.pop_size + 255) / 256), 256, 0, s>>>(d);
+  EBIC_CUDA_TRY(cudaGetLastError());
+  EBIC_TRY(eval_archive(h, st->apop, st->eargs, s));
+  k_rank<<<1, kRankThreads, st->smem_rank, s>>>(d, st->Pp);
+  EBIC_CUDA_TRY(cudaGetLastError());
+  return EBIC_OK;
+}
+
+static ebic_status read_ctl(EaState* st, cudaStream_t s, Ctl* out) {
+  EBIC_CUDA_TRY(cudaMemcpyAsync(st->h_ctl.ptr, st->ctl.ptr, sizeof(Ctl), cudaMemcpyDeviceToHost, s));
+  EBIC_CUDA_TRY(cudaStreamSynchronize(s));
+  std::memcpy(out, st->h_ctl.ptr, sizeof(Ctl));
+  return EBIC_OK;
+}
+
+static void fill_stats(const Ctl& c, ebic_stats_t* stats) {
+  if (!stats) return;
+  stats->generations_done = c.gens_done;
+  stats->stop_reason = c.stop_reason;
+  stats->tabu_hits_total = c.hits_total;
+  stats->attempts_total = c.attempts_total;
+  stats->evaluations_total = c.evals_total;
+  stats->last_gen_hits = c.last_hits;
+  stats->toprank_n = c.n_top;
+  stats->exact_tournaments = c.exact_total;
+}
+
+static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
+  EBIC_TRY(validate(h, p));
+  ea_release(h);
+  EaState* st = new EaState();
+  h->ea = st;
+  st->p = *p;
+  const int32_t P = p->pop_size, k = p->tournament_k, T = p->toprank_size;
+  st->S = p->len_max;
+  st->J = 2 * P + 1;
+  st->ncombo = k * k;
+  st->WC = (h->C + 31) / 32;
+  st->Pp = 1;
+  while (st->Pp < P) st->Pp <<= 1;
+  int H = 1;
+  while (H < 2 * P) H <<= 1;
+  st->hmask = H - 1;
+  st->entries = (long long)(p->iterations + 1) * P;
+  const cudaStream_t s = h->stream;
+  const size_t E = (size_t)st->entries;
+  EBIC_TRY(st->seq.reserve(E * st->S * sizeof(uint16_t)));
+  EBIC_TRY(st->len.reserve(E * sizeof(int32_t)));
+  EBIC_TRY(st->inc.reserve(E * sizeof(uint32_t)));
+  EBIC_TRY(st->dec.reserve(E * sizeof(uint32_t)));
+  EBIC_TRY(st->fit.reserve(E * sizeof(double)));
+  EBIC_TRY(st->lnf.reserve(E * sizeof(float)));
+  unsigned long long tcap = 1;
+  while (tcap < 2ull * E) tcap <<= 1;
+  EBIC_TRY(st->tkey.reserve(tcap * sizeof(unsigned long long)));
+  EBIC_TRY(st->tref.reserve(tcap * sizeof(int32_t)));
+  EBIC_CUDA_TRY(cudaMemsetAsync(st->tkey.ptr, 0, tcap * sizeof(unsigned long long), s));
+  EBIC_CUDA_TRY(cudaMemsetAsync(st->dec.ptr, 0, E * sizeof(uint32_t), s));
+  const size_t nrec = (size_t)st->J * st->ncombo;
+  EBIC_TRY(st->sp_ent.reserve((size_t)st->J * 8 * sizeof(int32_t)));
+  EBIC_TRY(st->sp_cross.reserve((size_t)st->J * sizeof(int32_t)));
+  EBIC_TRY(st->sp_child.reserve(nrec * st->S * sizeof(uint16_t)));
+  EBIC_TRY(st->sp_clen.reserve(nrec * sizeof(int32_t)));
+  EBIC_TRY(st->sp_hash.reserve(nrec * sizeof(unsigned long long)));
+  EBIC_TRY(st->sp_tabu.reserve(nrec * sizeof(int32_t)));
+  EBIC_TRY(st->list_ref.reserve((size_t)(T + P) * sizeof(int32_t)));
+  EBIC_TRY(st->list_f.reserve((size_t)(T + P) * sizeof(double)));
+  EBIC_TRY(st->ctl.reserve(sizeof(Ctl)));
+  EBIC_TRY(st->h_ctl.reserve(sizeof(Ctl)));
+  EBIC_CUDA_TRY(cudaMemsetAsync(st->ctl.ptr, 0, sizeof(Ctl), s));
+
+  // Crowding-penalty table base^(S / L) (host C library pow), L in
+  // [len_min, len_max], S in [0, L * P]; and log(base) / L as float.
+  std::vector<long long> off((size_t)p->len_max + 1, 0);
+  long long total = 0;
+  for (int L = p->len_min; L <= p->len_max; ++L) {
+    off[L] = total;
+    total += (long long)L * P + 1;
+  }
+  std::vector<double> tab((size_t)total);
+  for (int L = p->len_min; L <= p->len_max; ++L)
+    for (long long S = 0; S <= (long long)L * P; ++S)
+      tab[(size_t)(off[L] + S)] = std::pow(p->penalty_base, (double)S / (double)L);
+  std::vector<float> cl((size_t)p->len_max + 1, 0.f);
+  for (int L = 1; L <= p->len_max; ++L) cl[L] = (float)(std::log(p->penalty_base) / (double)L);
+  EBIC_TRY(st->pow_tab.reserve(tab.size() * sizeof(double)));
+  EBIC_TRY(st->pow_off.reserve(off.size() * sizeof(long long)));
+  EBIC_TRY(st->c_over_L.reserve(cl.size() * sizeof(float)));
+  EBIC_CUDA_TRY(cudaMemcpyAsync(st->pow_tab.ptr, tab.data(), tab.size() * sizeof(double),
+                                cudaMemcpyHostToDevice, s));
+  EBIC_CUDA_TRY(cudaMemcpyAsync(st->pow_off.ptr, off.data(), off.size() * sizeof(long long),
+                                cudaMemcpyHostToDevice, s));
+  EBIC_CUDA_TRY(cudaMemcpyAsync(st->c_over_L.ptr, cl.data(), cl.size() * sizeof(float),
+                                cudaMemcpyHostToDevice, s));
+
+  EaDev& d = st->dev;
+  d.P = P;
+  d.C = h->C;
+  d.S = st->S;
+  d.Lmin = p->len_min;
+  d.Lmax = p->len_max;
+  d.k = k;
+  d.T = T;
+  d.mode = p->support_mode;
+  d.J = st->J;
+  d.ncombo = st->ncombo;
+  d.WC = st->WC;
+  d.tau = p->overlap_tau;
+  d.elite_frac = p->elite_frac;
+  d.pc = p->p_crossover;
+  d.seed = p->seed;
+  d.seq = st->seq.as<uint16_t>();
+  d.len = st->len.as<int32_t>();
+  d.fit = st->fit.as<double>();
+  d.lnf = st->lnf.as<float>();
+  d.tkey = st->tkey.as<unsigned long long>();
+  d.tref = st->tref.as<int32_t>();
+  d.tmask = tcap - 1;
+  d.sp_ent = st->sp_ent.as<int32_t>();
+  d.sp_cross = st->sp_cross.as<int32_t>();
+  d.sp_child = st->sp_child.as<uint16_t>();
+  d.sp_clen = st->sp_clen.as<int32_t>();
+  d.sp_hash = st->sp_hash.as<unsigned long long>();
+  d.sp_tabu = st->sp_tabu.as<int32_t>();
+  d.list_ref = st->list_ref.as<int32_t>();
+  d.list_f = st->list_f.as<double>();
+  d.pow_tab = st->pow_tab.as<double>();
+  d.pow_off = st->pow_off.as<long long>();
+  d.c_over_L = st->c_over_L.as<float>();
+  d.ctl = st->ctl.as<Ctl>();
+
+  st->apop.seq = d.seq;
+  st->apop.len = d.len;
+  st->apop.stride = st->S;
+  st->apop.P = P;
+  st->apop.gen = &d.ctl->gen;
+  st->apop.stop = &d.ctl->stop;
+  EvalArgs& a = st->eargs;
+  a.P = P;
+  a.sigma = p->sigma;
+  a.mode = p->support_mode;
+  a.want_dec = p->support_mode == EBIC_SUPPORT_INC_PLUS_DEC;
+  a.inc = st->inc.as<uint32_t>();
+  a.dec = a.want_dec ? st->dec.as<uint32_t>() : nullptr;
+  a.fit = d.fit;
+  a.lnf = d.lnf;
+
+  st->smem_build = (size_t)H * (sizeof(unsigned long long) + sizeof(int32_t)) +
+                   (size_t)h->C * sizeof(uint32_t) + (size_t)(p->len_max + 1) * sizeof(float);
+  const size_t cap = (size_t)T + P;
+  st->smem_rank = (size_t)st->Pp * (sizeof(unsigned long long) + sizeof(int32_t)) +
+                  cap * (2 * sizeof(double) + 2 * sizeof(int32_t)) + ((cap + 15) & ~(size_t)15) +
+                  (size_t)st->WC * sizeof(uint32_t);
+  if (st->smem_build > 220 * 1024 || st->smem_rank > 220 * 1024)
+    return fail(EBIC_ERR_ARG, "population / top-rank sizes need more shared memory than a CTA has "
+                              "(build %zu B, rank %zu B)", st->smem_build, st->smem_rank);
+  EBIC_CUDA_TRY(cudaFuncSetAttribute(k_build<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)st->smem_build));
+  EBIC_CUDA_TRY(cudaFuncSetAttribute(k_build<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)st->smem_build));
+  EBIC_CUDA_TRY(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)st->smem_rank));
+
+  // The pair table pays for itself over a run; build it when it fits.
+  if (h->path != EBIC_PATH_GATHER && !h->LT) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    const size_t need = (size_t)h->C * h->C * h->W * sizeof(uint32_t);
+    if (need < free_b / 2) EBIC_TRY(build_pair_table(h, s));
+  }
+
+  // Step 1: initial population, evaluation (autotuned once), top-rank list.
+  const EaDev& dd = st->dev;
+  const unsigned sblocks = (unsigned)((st->J + 127) / 128);
+  k_spec<true><<<sblocks, 128, 0, s>>>(dd);
+  k_build<true><<<1, 32, st->smem_build, s>>>(dd, st->hmask);
+  k_tabu_insert<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(dd);
+  count_launches(3);
+  EBIC_CUDA_TRY(cudaGetLastError());
+  Ctl c{};
+  EBIC_TRY(read_ctl(st, s, &c));
+  const ebic_eval_tuning_t user_tuning = h->tuning;
+  if (!c.stop) {
+    float us = 0.f;
+    EBIC_TRY(autotune_archive(h, st->apop, a, s, &us));
+  }
+  k_rank<<<1, kRankThreads, st->smem_rank, s>>>(dd, st->Pp);
+  count_launches(1);
+  EBIC_CUDA_TRY(cudaGetLastError());
+
+  // One generation (Steps 2-5) captured as a graph for replay.
+  EBIC_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  ebic_status cap_st = launch_generation(h, st, false, s);
+  cudaGraph_t graph = nullptr;
+  cudaError_t ce = cudaStreamEndCapture(s, &graph);
+  h->tuning = user_tuning;
+  if (cap_st != EBIC_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return cap_st;
+  }
+  EBIC_CUDA_TRY(ce);
+  st->graph = graph;
+  EBIC_CUDA_TRY(cudaGraphInstantiate(&st->exec, graph, 0));
+  EBIC_CUDA_TRY(cudaStreamSynchronize(s));
+  st->initialised = true;
+  return EBIC_OK;
+}
+
+static ebic_status run_step(ebic_ctx* h, int32_t generations, ebic_stats_t* stats) {
+  EaState* st = h->ea;
+  if (!st || !st->initialised) return fail(EBIC_ERR_STATE, "ebic_run_init has not run");
+  if (generations < 0) return fail(EBIC_ERR_ARG, "negative generation count");
+  const cudaStream_t s = h->stream;
+  Ctl c{};
+  EBIC_TRY(read_ctl(st, s, &c));
+  if (!c.stop && c.gens_done + generations > st->p.iterations)
+    return fail(EBIC_ERR_STATE, "the run was sized for %d generations (%d done, %d asked)",
+                st->p.iterations, c.gens_done, generations);
+  int32_t left = c.stop ? 0 : generations;
+  while (left > 0) {
+    const int32_t chunk = std::min<int32_t>(left, 64);
+    for (int32_t i = 0; i < chunk; ++i) EBIC_CUDA_TRY(cudaGraphLaunch(st->exec, s));
+    count_launches((uint64_t)chunk * 5);
+    left -= chunk;
+    EBIC_TRY(read_ctl(st, s, &c));
+    if (c.stop) break;
+  }
+  EBIC_TRY(read_ctl(st, s, &c));
+  fill_stats(c, stats);
+  if (c.stop_reason == 3) return fail(EBIC_ERR_DEVICE, "internal EA error (code 3)");
+  return EBIC_OK;
+}
+
+// Gathers n records (archive entries refs[i], or g * P + i when refs is
+// null) into packed rows: seq [n][S], then len, inc, dec (int32) and fitness.
+__global__ void __launch_bounds__(256) k_gather(EaDev d, const int32_t* refs, long long first,
+                                                int n, const uint32_t* inc, const uint32_t* dec,
+                                                uint16_t* o_seq, int32_t* o_len, uint32_t* o_inc,
+                                                uint32_t* o_dec, double* o_fit) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const long long r = refs ? (long long)refs[i] : first + i;
+  const int L = d.len[r];
+  for (int c = 0; c < d.S; ++c) o_seq[(size_t)i * d.S + c] = c < L ? d.seq[(size_t)r * d.S + c] : 0;
+  o_len[i] = L;
+  o_inc[i] = inc[r];
+  o_dec[i] = dec[r];
+  o_fit[i] = d.fit[r];
+}
+
+static ebic_status get_records(ebic_ctx* h, bool toprank, int32_t* offsets, int32_t* cols,
+                               double* fitness, uint32_t* inc, uint32_t* dec, int32_t* inout_n) {
+  EaState* st = h->ea;
+  if (!st || !st->initialised) return fail(EBIC_ERR_STATE, "ebic_run_init has not run");
+  if (!offsets || !cols || !inout_n || *inout_n < 0) return fail(EBIC_ERR_ARG, "null pointer");
+  const cudaStream_t s = h->stream;
+  Ctl c{};
+  EBIC_TRY(read_ctl(st, s, &c));
+  const int32_t P = st->p.pop_size, S = st->S;
+  // the list, or the last evaluated generation (c.gen - 1)
+  const int32_t avail = toprank ? c.n_top : (c.gen > 0 ? P : 0);
+  const int32_t n = std::min<int32_t>(*inout_n, avail);
+  offsets[0] = 0;
+  *inout_n = n;
+  if (n == 0) return EBIC_OK;
+  const size_t row = (size_t)S * sizeof(uint16_t);
+  const size_t bytes = (size_t)n * (row + 3 * sizeof(int32_t) + sizeof(double));
+  EBIC_TRY(st->gather.reserve(bytes));
+  EBIC_TRY(st->h_gather.reserve(bytes));
+  // regions by decreasing element size, so every one is aligned:
+  // fitness [n] (8 B) | len, inc, dec [n] (4 B) | seq [n][S] (2 B)
+  char* dbase = static_cast<char*>(st->gather.ptr);
+  double* o_fit = reinterpret_cast<double*>(dbase);
+  int32_t* o_len = reinterpret_cast<int32_t*>(o_fit + n);
+  uint32_t* o_inc = reinterpret_cast<uint32_t*>(o_len + n);
+  uint32_t* o_dec = o_inc + n;
+  uint16_t* o_seq = reinterpret_cast<uint16_t*>(o_dec + n);
+  k_gather<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(
+      st->dev, toprank ? st->list_ref.as<int32_t>() : nullptr, (long long)(c.gen - 1) * P, n,
+      st->inc.as<uint32_t>(), st->dec.as<uint32_t>(), o_seq, o_len, o_inc, o_dec, o_fit);
+  count_launches(1);
+  EBIC_CUDA_TRY(cudaGetLastError());
+  EBIC_CUDA_TRY(cudaMemcpyAsync(st->h_gather.ptr, st->gather.ptr, bytes, cudaMemcpyDeviceToHost, s));
+  EBIC_CUDA_TRY(cudaStreamSynchronize(s));
+  const double* h_fit = static_cast<const double*>(st->h_gather.ptr);
+  const int32_t* h_len = reinterpret_cast<const int32_t*>(h_fit + n);
+  const uint32_t* h_inc = reinterpret_cast<const uint32_t*>(h_len + n);
+  const uint32_t* h_dec = h_inc + n;
+  const uint16_t* h_seq = reinterpret_cast<const uint16_t*>(h_dec + n);
+  for (int32_t i = 0; i < n; ++i) {
+    const int32_t L = h_len[i];
+    for (int32_t t = 0; t < L; ++t) cols[offsets[i] + t] = h_seq[(size_t)i * S + t];
+    offsets[i + 1] = offsets[i] + L;
+    if (fitness) fitness[i] = h_fit[i];
+    if (inc) inc[i] = h_inc[i];
+    if (dec) dec[i] = h_dec[i];
+  }
+  return EBIC_OK;
+}
+
 }  // namespace ebic
 
 using namespace ebic;
 
 extern "C" {
+
 void ebic_default_params(ebic_params_t* p) {
-  p->pop_size = 100; p->len_min = 2; p->len_max = 6; p->iterations = 10; p->sigma = 10;
-  p->toprank_size = 100; p->tournament_k = 2; p->support_mode = EBIC_SUPPORT_INC;
-  p->overlap_tau = 0.5; p->elite_frac = 0.25; p->penalty_base = 1.2; p->p_crossover = 0.5;
+  if (!p) return;
+  p->pop_size = 100;
+  p->len_min = 2;
+  p->len_max = 6;
+  p->iterations = 10;
+  p->sigma = 10;
+  p->toprank_size = 100;
+  p->tournament_k = 2;
+  p->support_mode = EBIC_SUPPORT_INC;
+  p->overlap_tau = 0.5;
+  p->elite_frac = 0.25;
+  p->penalty_base = 1.2;
+  p->p_crossover = 0.5;
   p->seed = 0;
 }
-ebic_status ebic_run_init(ebic_handle, const ebic_params_t*) { return fail(EBIC_ERR_STATE, "EA not built"); }
-ebic_status ebic_run_step(ebic_handle, int32_t, ebic_stats_t*) { return fail(EBIC_ERR_STATE, "EA not built"); }
-ebic_status ebic_get_toprank(ebic_handle, int32_t*, int32_t*, double*, uint32_t*, int32_t*) { return fail(EBIC_ERR_STATE, "EA not built"); }
-ebic_status ebic_get_population(ebic_handle, int32_t*, int32_t*, uint32_t*, uint32_t*, double*, int32_t*) { return fail(EBIC_ERR_STATE, "EA not built"); }
-ebic_status ebic_run_generations(ebic_handle, const ebic_params_t*, int32_t*, int32_t*, double*, int32_t*, ebic_stats_t*) { return fail(EBIC_ERR_STATE, "EA not built"); }
+
+ebic_status ebic_run_init(ebic_handle h, const ebic_params_t* p) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  int prev = -1;
+  cudaGetDevice(&prev);
+  if (prev != h->device) cudaSetDevice(h->device);
+  ebic_status st = run_init(h, p);
+  if (st != EBIC_OK) ea_release(h);
+  if (prev >= 0 && prev != h->device) cudaSetDevice(prev);
+  return st;
 }
+
+ebic_status ebic_run_step(ebic_handle h, int32_t generations, ebic_stats_t* stats) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  return run_step(h, generations, stats);
+}
+
+ebic_status ebic_get_toprank(ebic_handle h, int32_t* offsets, int32_t* cols, double* fitness,
+                             uint32_t* inc, int32_t* inout_n) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  return get_records(h, true, offsets, cols, fitness, inc, nullptr, inout_n);
+}
+
+ebic_status ebic_get_population(ebic_handle h, int32_t* offsets, int32_t* cols, uint32_t* inc,
+                                uint32_t* dec, double* fitness, int32_t* inout_n) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  return get_records(h, false, offsets, cols, fitness, inc, dec, inout_n);
+}
+
+ebic_status ebic_run_generations(ebic_handle h, const ebic_params_t* p, int32_t* out_offsets,
+                                 int32_t* out_cols, double* out_fitness, int32_t* inout_n,
+                                 ebic_stats_t* stats) {
+  if (!h || !p) return fail(EBIC_ERR_ARG, "null pointer");
+  EBIC_TRY(ebic_run_init(h, p));
+  EBIC_TRY(ebic_run_step(h, p->iterations, stats));
+  return ebic_get_toprank(h, out_offsets, out_cols, out_fitness, nullptr, inout_n);
+}
+
+}  // extern "C"

@@ -68,12 +68,11 @@ struct ebic_ctx {
   uint32_t* LT = nullptr; // pair bitmask table [C][C][W] (nullptr until built)
   size_t LT_bytes = 0;
   int32_t path = EBIC_PATH_AUTO;
-  int32_t tune_group = 0;          // bitmask lanes per series (0 = automatic)
-  int32_t tune_vecs_bitmask = 0;   // 16-byte vectors per part, bitmask path (0 = auto)
-  int32_t tune_vecs_gather = 0;    // 16-byte vectors per part, gather path (0 = auto)
+  ebic_eval_tuning_t tuning{};     // launch shape of evaluations (zeros = automatic)
   cudaStream_t stream = nullptr;  // internal stream for the host-buffer calls
   int* d_err = nullptr;           // device error flag (0 = none)
-  ebic::DevBuf tickets;           // per-series arrival counters (self-resetting)
+  ebic::DevBuf tickets;           // per-series partial counts and arrivals of split
+                                  // series (2 x 64-bit words each, zero between launches)
   ebic::DevBuf st_off, st_cols, st_inc, st_dec, st_fit;   // staging for host calls
   ebic::HostBuf h_stage;          // pinned staging for host calls
   ebic::EaState* ea = nullptr;
@@ -82,29 +81,57 @@ struct ebic_ctx {
 namespace ebic {
 
 // Population views used by the support kernels.
+// A view supplies range(i) (start and length of series i; false if invalid),
+// col(begin, t), out(i) (index at which series i's results are written) and
+// active() (false skips the whole launch).
 struct CbfPop {          // caller CBF: offsets[P + 1], cols[total]
   const int32_t* offsets;
   const int32_t* cols;
   int32_t total;
-  __device__ __forceinline__ bool range(int32_t i, int32_t* begin, int32_t* len) const {
+  __device__ __forceinline__ bool active() const { return true; }
+  __device__ __forceinline__ int64_t out(int32_t i) const { return i; }
+  __device__ __forceinline__ bool range(int32_t i, int64_t* begin, int32_t* len) const {
     int32_t b = offsets[i], e = offsets[i + 1];
     *begin = b;
     *len = e - b;
     return b >= 0 && e <= total && e - b >= 1 && e - b <= EBIC_MAX_EVAL_LEN;
   }
-  __device__ __forceinline__ int32_t col(int32_t begin, int32_t t) const { return cols[begin + t]; }
+  __device__ __forceinline__ int32_t col(int64_t begin, int32_t t) const { return cols[begin + t]; }
 };
 
 struct FixedPop {        // EA layout: seq[P][stride] (uint16), len[P]
   const uint16_t* seq;
   const int32_t* len;
   int32_t stride;
-  __device__ __forceinline__ bool range(int32_t i, int32_t* begin, int32_t* L) const {
-    *begin = i * stride;
+  __device__ __forceinline__ bool active() const { return true; }
+  __device__ __forceinline__ int64_t out(int32_t i) const { return i; }
+  __device__ __forceinline__ bool range(int32_t i, int64_t* begin, int32_t* L) const {
+    *begin = (int64_t)i * stride;
     *L = len[i];
     return *L >= 1 && *L <= stride;
   }
-  __device__ __forceinline__ int32_t col(int32_t begin, int32_t t) const { return seq[begin + t]; }
+  __device__ __forceinline__ int32_t col(int64_t begin, int32_t t) const { return seq[begin + t]; }
+};
+
+// The current generation of the EA archive: series i of generation g is
+// archive entry g * P + i.  g and the stop flag are read on the device, so a
+// captured launch follows the run from generation to generation.
+struct ArchivePop {
+  const uint16_t* seq;   // [entries][stride]
+  const int32_t* len;    // [entries]
+  int32_t stride;
+  int32_t P;
+  const int32_t* gen;    // current generation
+  const int32_t* stop;   // nonzero: the run has stopped
+  __device__ __forceinline__ bool active() const { return *(volatile const int32_t*)stop == 0; }
+  __device__ __forceinline__ int64_t out(int32_t i) const { return (int64_t)(*gen) * P + i; }
+  __device__ __forceinline__ bool range(int32_t i, int64_t* begin, int32_t* L) const {
+    const int64_t e = out(i);
+    *begin = e * stride;
+    *L = len[e];
+    return *L >= 1 && *L <= stride;
+  }
+  __device__ __forceinline__ int32_t col(int64_t begin, int32_t t) const { return seq[begin + t]; }
 };
 
 // Arguments of one evaluation launch.
@@ -124,6 +151,13 @@ ebic_status eval_cbf(ebic_ctx* h, const int32_t* d_off, const int32_t* d_cols, i
                      const EvalArgs& a, cudaStream_t s);
 ebic_status eval_fixed(ebic_ctx* h, const uint16_t* d_seq, const int32_t* d_len, int32_t stride,
                        const EvalArgs& a, cudaStream_t s);
+ebic_status eval_archive(ebic_ctx* h, const ArchivePop& pop, const EvalArgs& a, cudaStream_t s);
+ebic_status autotune_archive(ebic_ctx* h, const ArchivePop& pop, const EvalArgs& a,
+                             cudaStream_t s, float* best_us);
+// Times candidate launch shapes on a device-resident EA population and keeps
+// the fastest in h->tuning (synchronises s).
+ebic_status autotune_fixed(ebic_ctx* h, const uint16_t* d_seq, const int32_t* d_len,
+                           int32_t stride, const EvalArgs& a, cudaStream_t s, float* best_us);
 // Which path an evaluation of this handle would take now.
 int32_t resolve_path(ebic_ctx* h);
 ebic_status build_pair_table(ebic_ctx* h, cudaStream_t s);

@@ -115,34 +115,48 @@ k_load_colmajor(const float* __restrict__ src, int32_t R, int32_t C, int32_t R_p
 }
 
 // ---------------------------------------------------------------------------
-// K2: pair bitmask table.  One CTA = 8 columns p (one per warp) x 1024 rows
-// (32 words).  Each warp keeps its column's 1024 values in registers and walks
-// every q; the 8 warps read the same q values, which L1 serves after the first.
+// K2: pair bitmask table.  Layout: entry (p, q) is W words = V 16-byte vectors;
+// vector b covers rows 128 b .. 128 b + 127, and bit l of its word i is the
+// row 128 b + 4 l + i (each lane of a warp reads one float4 = 4 consecutive
+// rows, and one ballot per component gives one word).  Counting only ANDs and
+// popcounts whole vectors, so the order of bits inside a vector is free.
+// One CTA = 8 columns p (one per warp) x 8 vectors (1,024 rows); each warp
+// keeps its column's 8 float4 in registers and walks every q; the 8 warps read
+// the same q values, which L1 serves after the first.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256)
 k_pair_table(const float* __restrict__ A_c, int32_t C, int32_t R_pad, int32_t W,
              uint32_t* __restrict__ LT) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int p = blockIdx.y * 8 + warp;
-  const int w0 = blockIdx.x * 32;
+  const int V = R_pad >> 7;                      // 128-row vectors per column
+  const int b0 = blockIdx.x * 8;
   if (p >= C) return;
-  const int nw = min(32, W - w0);
+  const int nb = min(8, V - b0);
   const float qnan = __int_as_float(0x7fc00000);
-  const float* colp = A_c + (size_t)p * R_pad + (size_t)w0 * 32;
-  float ap[32];
+  const float4 nan4 = make_float4(qnan, qnan, qnan, qnan);
+  const float4* A4 = reinterpret_cast<const float4*>(A_c);
+  const size_t col4 = (size_t)R_pad >> 2;        // float4 per column
+  float4 ap[8];
 #pragma unroll
-  for (int j = 0; j < 32; ++j) ap[j] = (j < nw) ? colp[j * 32 + lane] : qnan;
-  uint32_t* out = LT + (size_t)p * C * W + w0;
+  for (int b = 0; b < 8; ++b) ap[b] = (b < nb) ? A4[(size_t)p * col4 + (size_t)(b0 + b) * 32 + lane] : nan4;
+  uint32_t* out = LT + (size_t)p * C * W + (size_t)b0 * 4;
   for (int q = 0; q < C; ++q) {
-    const float* colq = A_c + (size_t)q * R_pad + (size_t)w0 * 32;
+    const float4* colq = A4 + (size_t)q * col4 + (size_t)b0 * 32;
     uint32_t mine = 0;
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      float aq = (j < nw) ? colq[j * 32 + lane] : qnan;
-      uint32_t b = __ballot_sync(0xffffffffu, ap[j] < aq);
-      if (lane == j) mine = b;
+    for (int b = 0; b < 8; ++b) {
+      const float4 aq = (b < nb) ? colq[b * 32 + lane] : nan4;
+      const uint32_t w0 = __ballot_sync(0xffffffffu, ap[b].x < aq.x);
+      const uint32_t w1 = __ballot_sync(0xffffffffu, ap[b].y < aq.y);
+      const uint32_t w2 = __ballot_sync(0xffffffffu, ap[b].z < aq.z);
+      const uint32_t w3 = __ballot_sync(0xffffffffu, ap[b].w < aq.w);
+      if (lane == 4 * b + 0) mine = w0;
+      if (lane == 4 * b + 1) mine = w1;
+      if (lane == 4 * b + 2) mine = w2;
+      if (lane == 4 * b + 3) mine = w3;
     }
-    if (lane < nw) out[(size_t)q * W + lane] = mine;
+    if (lane < 4 * nb) out[(size_t)q * W + lane] = mine;
   }
 }
 
@@ -154,7 +168,7 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // Eq. (1) for one series and the write-out of its results.
 __device__ __forceinline__ void finish_series(const EvalArgs& a, const double* __restrict__ LN,
-                                              int32_t i, uint32_t inc, uint32_t dec, int32_t L) {
+                                              int64_t i, uint32_t inc, uint32_t dec, int32_t L) {
   a.inc[i] = inc;
   if (a.dec) a.dec[i] = dec;
   int64_t n = (a.mode == EBIC_SUPPORT_INC_PLUS_DEC) ? (int64_t)inc + (int64_t)dec : (int64_t)inc;
@@ -169,25 +183,39 @@ __device__ __forceinline__ void finish_series(const EvalArgs& a, const double* _
   if (a.lnf) a.lnf[i] = f > 0.0 ? (float)log(f) : -INFINITY;
 }
 
-// Adds one part's counts; the part that arrives last writes the results.
+// Adds one part's counts into per-series scratch; the part that arrives last
+// writes the results.  Rising counts only: one 64-bit word per series packs
+// (parts arrived << 32 | count); a single atomicAdd both adds and takes a
+// ticket, and its return value gives the last arriver the exact total -- no
+// fence needed -- after which it puts the word back to zero.  With falling
+// counts as well, a second word holds them and the arrival is fenced.  The
+// scratch is zero when allocated and after every launch.
 __device__ __forceinline__ void add_part(const EvalArgs& a, const double* __restrict__ LN,
-                                         uint32_t* __restrict__ tickets, int32_t items_per,
-                                         int32_t i, uint32_t inc, uint32_t dec, int32_t L) {
+                                         uint32_t* __restrict__ scratch, int32_t items_per,
+                                         int32_t i, int64_t o, uint32_t inc, uint32_t dec,
+                                         int32_t L, bool with_dec) {
   if (items_per == 1) {
-    finish_series(a, LN, i, inc, dec, L);
+    finish_series(a, LN, o, inc, dec, L);
     return;
   }
-  uint32_t* dec_acc = a.dec;
-  atomicAdd(&a.inc[i], inc);
-  if (dec_acc) atomicAdd(&dec_acc[i], dec);
+  unsigned long long* word = reinterpret_cast<unsigned long long*>(scratch) + 2 * (size_t)i;
+  if (!with_dec) {
+    const unsigned long long old = atomicAdd(word, (1ull << 32) | (unsigned long long)inc);
+    if ((uint32_t)(old >> 32) == (uint32_t)items_per - 1) {
+      *word = 0ull;
+      finish_series(a, LN, o, (uint32_t)old + inc, 0u, L);
+    }
+    return;
+  }
+  unsigned long long* dword = word + 1;
+  atomicAdd(dword, (unsigned long long)dec);
   __threadfence();
-  unsigned t = atomicAdd(&tickets[i], 1u);
-  if (t == (unsigned)items_per - 1) {
+  const unsigned long long old = atomicAdd(word, (1ull << 32) | (unsigned long long)inc);
+  if ((uint32_t)(old >> 32) == (uint32_t)items_per - 1) {
     __threadfence();
-    uint32_t n_inc = atomicAdd(&a.inc[i], 0u);
-    uint32_t n_dec = dec_acc ? atomicAdd(&dec_acc[i], 0u) : 0u;
-    tickets[i] = 0;   // ready for the next launch
-    finish_series(a, LN, i, n_inc, n_dec, L);
+    const uint32_t n_dec = (uint32_t)atomicExch(dword, 0ull);
+    *word = 0ull;
+    finish_series(a, LN, o, (uint32_t)old + inc, n_dec, L);
   }
 }
 
@@ -210,19 +238,21 @@ __device__ __forceinline__ uint4 ld_table(const uint4* p) { return __ldg(p); }
 // w0 + t and the warp broadcasts it with shuffles.  Every loop condition is
 // warp-uniform; the warp leaves when its AND is zero in every lane.
 // ---------------------------------------------------------------------------
-template <bool DEC, bool CHECK, class Pop>
+template <bool DEC, bool CHECK, int NV, int KB, class Pop>
 __global__ void __launch_bounds__(256)
 k_support_bitmask_warp(const uint32_t* __restrict__ LT, int32_t C, int32_t W, int32_t R,
                        Pop pop, EvalArgs a, int32_t vecs_per_item, int32_t items_per,
                        uint32_t* __restrict__ tickets, const double* __restrict__ LN,
                        int* __restrict__ err) {
+  if (!pop.active()) return;
   const int lane = threadIdx.x & 31;
   const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t n_items = (int64_t)a.P * items_per;
   if (item >= n_items) return;                           // warp-uniform
   const int32_t sid = (int32_t)(item / items_per);
   const int32_t part = (int32_t)(item % items_per);
-  int32_t begin = 0, L = 0;
+  int64_t begin = 0;
+  int32_t L = 0;
   bool ok = pop.range(sid, &begin, &L);
   bool bad = !ok;
   if (CHECK) {
@@ -239,13 +269,18 @@ k_support_bitmask_warp(const uint32_t* __restrict__ LT, int32_t C, int32_t W, in
   const uint4* LT4 = reinterpret_cast<const uint4*>(LT);
   const size_t row4 = (size_t)V;
   const uint4 ones = make_uint4(kFull, kFull, kFull, kFull);
+  const uint4 zeros = make_uint4(0u, 0u, 0u, 0u);
   uint32_t cnt_inc = 0, cnt_dec = 0;
 
-  for (int32_t vb = v_lo; vb < v_hi; vb += 32) {
-    const int32_t vec = vb + lane;
-    const bool lane_on = nsteps > 0 && vec < v_hi;
-    uint4 mi = lane_on ? ones : make_uint4(0u, 0u, 0u, 0u);
-    uint4 md = (DEC && lane_on) ? ones : make_uint4(0u, 0u, 0u, 0u);
+  for (int32_t vb = v_lo; vb < v_hi; vb += 32 * NV) {
+    bool on[NV];
+    uint4 mi[NV], md[NV];
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      on[k] = nsteps > 0 && vb + lane + 32 * k < v_hi;
+      mi[k] = on[k] ? ones : zeros;
+      md[k] = (DEC && on[k]) ? ones : zeros;
+    }
     bool alive = nsteps > 0;                               // warp-uniform
     for (int32_t w0 = 0; alive && w0 < nsteps; w0 += 32) {
       uint32_t pi = 0, pd = 0;                             // pair indices x * C + y
@@ -256,29 +291,43 @@ k_support_bitmask_warp(const uint32_t* __restrict__ LT, int32_t C, int32_t W, in
         pd = y * (uint32_t)C + x;
       }
       const int32_t wn = min(32, nsteps - w0);             // warp-uniform
-      for (int32_t t = 0; alive && t < wn; t += kBatch) {
-        uint4 xi[kBatch], xd[kBatch];
-        // a lane whose own block is already empty stops fetching
-        const bool live = lane_on && (nz4(mi) || (DEC && nz4(md)));
+      for (int32_t t = 0; alive && t < wn; t += KB) {
+        // a lane stops fetching for a block whose running AND is already zero
+        bool live[NV];
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
+        for (int k = 0; k < NV; ++k) live[k] = on[k] && (nz4(mi[k]) || (DEC && nz4(md[k])));
+        uint4 xi[KB][NV], xd[KB][NV];
+#pragma unroll
+        for (int u = 0; u < KB; ++u) {
           const uint32_t qi = __shfl_sync(kFull, pi, (t + u) & 31);
           const uint32_t qd = DEC ? __shfl_sync(kFull, pd, (t + u) & 31) : 0u;
-          const bool use = live && (t + u) < wn;
-          xi[u] = use ? ld_table(LT4 + (size_t)qi * row4 + vec) : ones;
-          if (DEC) xd[u] = use ? ld_table(LT4 + (size_t)qd * row4 + vec) : ones;
-        }
 #pragma unroll
-        for (int u = 0; u < kBatch; ++u) {
-          mi = and4(mi, xi[u]);
-          if (DEC) md = and4(md, xd[u]);
+          for (int k = 0; k < NV; ++k) {
+            const bool use = live[k] && (t + u) < wn;
+            const int32_t vec = vb + lane + 32 * k;
+            xi[u][k] = use ? ld_table(LT4 + (size_t)qi * row4 + vec) : ones;
+            if (DEC) xd[u][k] = use ? ld_table(LT4 + (size_t)qd * row4 + vec) : ones;
+          }
         }
-        alive = __any_sync(kFull, lane_on && (nz4(mi) || (DEC && nz4(md))));
+        bool any_nz = false;
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+#pragma unroll
+          for (int u = 0; u < KB; ++u) {
+            mi[k] = and4(mi[k], xi[u][k]);
+            if (DEC) md[k] = and4(md[k], xd[u][k]);
+          }
+          any_nz |= on[k] && (nz4(mi[k]) || (DEC && nz4(md[k])));
+        }
+        alive = __any_sync(kFull, any_nz);
       }
     }
-    if (lane_on) {
-      cnt_inc += popc4(mi);
-      if (DEC) cnt_dec += popc4(md);
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      if (on[k]) {
+        cnt_inc += popc4(mi[k]);
+        if (DEC) cnt_dec += popc4(md[k]);
+      }
     }
   }
   if (ok && L == 1 && part == 0 && lane == 0) cnt_inc = cnt_dec = (uint32_t)R;
@@ -292,7 +341,8 @@ k_support_bitmask_warp(const uint32_t* __restrict__ LT, int32_t C, int32_t W, in
       atomicOr(err, 1);
       cnt_inc = cnt_dec = 0;
     }
-    add_part(a, LN, tickets, items_per, sid, cnt_inc, DEC ? cnt_dec : 0u, bad ? 1 : L);
+    add_part(a, LN, tickets, items_per, sid, pop.out(sid), cnt_inc, DEC ? cnt_dec : 0u,
+             bad ? 1 : L, DEC);
   }
 }
 
@@ -308,13 +358,15 @@ __global__ void __launch_bounds__(256)
 k_support_bitmask_lane(const uint32_t* __restrict__ LT, int32_t C, int32_t W, int32_t R,
                        Pop pop, EvalArgs a, int32_t VP, const double* __restrict__ LN,
                        int* __restrict__ err) {
+  if (!pop.active()) return;
   const int lane = threadIdx.x & 31;
   const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t sid64 = tid / VP;
   const int32_t v = (int32_t)(tid % VP);
   const bool valid = sid64 < a.P;
   const int32_t sid = valid ? (int32_t)sid64 : 0;
-  int32_t begin = 0, L = 0;
+  int64_t begin = 0;
+  int32_t L = 0;
   bool ok = valid && pop.range(sid, &begin, &L);
   uint32_t bad = (valid && !ok) ? 1u : 0u;
   if (CHECK && ok)
@@ -366,7 +418,7 @@ k_support_bitmask_lane(const uint32_t* __restrict__ LT, int32_t C, int32_t W, in
       atomicOr(err, 1);
       cnt_inc = cnt_dec = 0;
     }
-    finish_series(a, LN, sid, cnt_inc, DEC ? cnt_dec : 0u, bad ? 1 : L);
+    finish_series(a, LN, pop.out(sid), cnt_inc, DEC ? cnt_dec : 0u, bad ? 1 : L);
   }
 }
 
@@ -389,13 +441,15 @@ k_support_gather(const float* __restrict__ A_c, int32_t C, int32_t R_pad, int32_
                  EvalArgs a, int32_t vecs_per_item, int32_t items_per,
                  uint32_t* __restrict__ tickets, const double* __restrict__ LN,
                  int* __restrict__ err) {
+  if (!pop.active()) return;
   const int lane = threadIdx.x & 31;
   const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t n_items = (int64_t)a.P * items_per;
   if (item >= n_items) return;
   const int32_t sid = (int32_t)(item / items_per);
   const int32_t part = (int32_t)(item % items_per);
-  int32_t begin = 0, L = 0;
+  int64_t begin = 0;
+  int32_t L = 0;
   bool ok = pop.range(sid, &begin, &L);
   bool bad = !ok;
   if (CHECK) {
@@ -458,7 +512,8 @@ k_support_gather(const float* __restrict__ A_c, int32_t C, int32_t R_pad, int32_
       atomicOr(err, 1);
       cnt_inc = cnt_dec = 0;
     }
-    add_part(a, LN, tickets, items_per, sid, cnt_inc, DEC ? cnt_dec : 0u, bad ? 1 : L);
+    add_part(a, LN, tickets, items_per, sid, pop.out(sid), cnt_inc, DEC ? cnt_dec : 0u,
+             bad ? 1 : L, DEC);
   }
 }
 
@@ -466,21 +521,22 @@ k_support_gather(const float* __restrict__ A_c, int32_t C, int32_t R_pad, int32_
 // launch helpers
 // ---------------------------------------------------------------------------
 constexpr int kSMs = 152;          // GB300
-constexpr int kTargetWarps = kSMs * 48;
+constexpr int kTargetWarps = kSMs * 48 * 3;   // about three warps per resident slot
+constexpr int kWarpsPerCta = 2;    // small CTAs: the block scheduler balances uneven series
 
 // Split each series' vectors into parts so that the launch has enough warps.
 static void choose_split(int32_t P, int32_t V, int32_t forced_vpi, int32_t* vecs_per_item,
-                         int32_t* items_per) {
+                         int32_t* items_per, int32_t lanes_vecs = 32) {
   if (forced_vpi > 0) {
     *vecs_per_item = std::max(forced_vpi / 32, 1) * 32;
     *items_per = (V + *vecs_per_item - 1) / *vecs_per_item;
     return;
   }
-  int32_t chunks = (V + 31) / 32;
+  int32_t chunks = (V + lanes_vecs - 1) / lanes_vecs;
   int64_t want = (kTargetWarps + (int64_t)P - 1) / std::max<int64_t>(P, 1);
   int32_t parts = (int32_t)std::min<int64_t>(std::max<int64_t>(want, 1), chunks);
   int32_t per = (chunks + parts - 1) / parts;
-  *vecs_per_item = per * 32;
+  *vecs_per_item = per * lanes_vecs;
   *items_per = (V + *vecs_per_item - 1) / *vecs_per_item;
 }
 
@@ -500,22 +556,22 @@ static ebic_status eval_any(ebic_ctx* h, const Pop& pop, EvalArgs a, cudaStream_
   int32_t vpi = 0, ipc = 1;
   bool lane_kernel = false;
   int32_t VP = 1;
+  int32_t nv = 1, kb = 4;
+  const ebic_eval_tuning_t& tu = h->tuning;
   if (path == EBIC_PATH_BITMASK) {
     const int32_t V = h->W >> 2;
-    lane_kernel = h->tune_group > 0 ? (h->tune_group < 32 && V <= 32) : V <= 16;
+    lane_kernel = tu.kernel == 1 ? V <= 32 : (tu.kernel == 0 && V <= 16);
     if (lane_kernel) {
       while (VP < V) VP <<= 1;
     } else {
-      choose_split(a.P, V, h->tune_vecs_bitmask, &vpi, &ipc);
+      nv = dec ? 1 : (tu.vecs_per_lane > 0 ? tu.vecs_per_lane : 1);
+      kb = dec ? 4 : (tu.batch_steps > 0 ? tu.batch_steps : 8);
+      choose_split(a.P, V, tu.vecs_per_part_bitmask, &vpi, &ipc, 32 * nv);
     }
   } else {
-    choose_split(a.P, h->R_pad >> 2, h->tune_vecs_gather, &vpi, &ipc);
+    choose_split(a.P, h->R_pad >> 2, tu.vecs_per_part_gather, &vpi, &ipc);
   }
-  if (ipc > 1) {
-    EBIC_TRY(h->tickets.reserve_zeroed((size_t)a.P * sizeof(uint32_t), s));
-    EBIC_CUDA_TRY(cudaMemsetAsync(a.inc, 0, (size_t)a.P * sizeof(uint32_t), s));
-    if (a.dec) EBIC_CUDA_TRY(cudaMemsetAsync(a.dec, 0, (size_t)a.P * sizeof(uint32_t), s));
-  }
+  if (ipc > 1) EBIC_TRY(h->tickets.reserve_zeroed((size_t)a.P * 2 * sizeof(unsigned long long), s));
   uint32_t* tk = h->tickets.as<uint32_t>();
   count_launches(1);
   if (path == EBIC_PATH_BITMASK && lane_kernel) {
@@ -528,25 +584,106 @@ static ebic_status eval_any(ebic_ctx* h, const Pop& pop, EvalArgs a, cudaStream_
       k_support_bitmask_lane<false, CHECK, Pop><<<blocks, 256, 0, s>>>(h->LT, h->C, h->W, h->R,
                                                                        pop, a, VP, h->LN, h->d_err);
   } else {
-    const unsigned blocks = (unsigned)(((int64_t)a.P * ipc + 7) / 8);
+    const unsigned blocks = (unsigned)(((int64_t)a.P * ipc + kWarpsPerCta - 1) / kWarpsPerCta);
     if (path == EBIC_PATH_BITMASK) {
-      if (dec)
-        k_support_bitmask_warp<true, CHECK, Pop><<<blocks, 256, 0, s>>>(
-            h->LT, h->C, h->W, h->R, pop, a, vpi, ipc, tk, h->LN, h->d_err);
-      else
-        k_support_bitmask_warp<false, CHECK, Pop><<<blocks, 256, 0, s>>>(
-            h->LT, h->C, h->W, h->R, pop, a, vpi, ipc, tk, h->LN, h->d_err);
+#define EBIC_BM(D, N, K)                                                                   \
+  k_support_bitmask_warp<D, CHECK, N, K, Pop><<<blocks, 32 * kWarpsPerCta, 0, s>>>(h->LT, h->C, h->W, h->R, \
+                                                                      pop, a, vpi, ipc, tk,  \
+                                                                      h->LN, h->d_err)
+      if (dec) EBIC_BM(true, 1, 4);
+      else if (nv == 1 && kb == 4) EBIC_BM(false, 1, 4);
+      else if (nv == 1) EBIC_BM(false, 1, 8);
+      else if (nv == 2 && kb == 4) EBIC_BM(false, 2, 4);
+      else if (nv == 2) EBIC_BM(false, 2, 8);
+      else EBIC_BM(false, 4, 4);
+#undef EBIC_BM
     } else {
       if (dec)
-        k_support_gather<true, CHECK, Pop><<<blocks, 256, 0, s>>>(
+        k_support_gather<true, CHECK, Pop><<<blocks, 32 * kWarpsPerCta, 0, s>>>(
             h->A_c, h->C, h->R_pad, h->R, pop, a, vpi, ipc, tk, h->LN, h->d_err);
       else
-        k_support_gather<false, CHECK, Pop><<<blocks, 256, 0, s>>>(
+        k_support_gather<false, CHECK, Pop><<<blocks, 32 * kWarpsPerCta, 0, s>>>(
             h->A_c, h->C, h->R_pad, h->R, pop, a, vpi, ipc, tk, h->LN, h->d_err);
     }
   }
   EBIC_CUDA_TRY(cudaGetLastError());
   return EBIC_OK;
+}
+
+// Autotuner: times candidate launch shapes on the caller's population (each
+// candidate once to warm up, then 3 launches between two events) and keeps
+// the fastest in h->tuning.  The candidates are evaluations, so the outputs
+// hold valid results afterwards.
+template <bool CHECK, class Pop>
+static ebic_status autotune_any(ebic_ctx* h, const Pop& pop, const EvalArgs& a, cudaStream_t s,
+                                float* best_us) {
+  std::vector<ebic_eval_tuning_t> cands;
+  const int32_t path = resolve_path(h);
+  const bool dec = a.want_dec != 0 || a.mode == EBIC_SUPPORT_INC_PLUS_DEC;
+  if (path == EBIC_PATH_BITMASK) {
+    const int32_t V = h->W >> 2;
+    if (V <= 32) cands.push_back({1, 0, 0, 0, 0});
+    const int32_t parts[] = {32, 64, 128, 256, 0};
+    for (int32_t vp : parts) {
+      if (vp > 0 && vp / 2 >= V) continue;
+      cands.push_back({2, vp, 0, 8, 1});
+      if (!dec) {
+        cands.push_back({2, vp, 0, 4, 1});
+        cands.push_back({2, vp, 0, 4, 2});
+      }
+    }
+  } else {
+    const int32_t V = h->R_pad >> 2;
+    const int32_t parts[] = {32, 64, 128, 256, 512, 1024, 0};
+    for (int32_t vp : parts) {
+      if (vp > 0 && vp / 2 >= V) continue;
+      cands.push_back({0, 0, vp, 0, 0});
+    }
+  }
+  cudaEvent_t e0, e1;
+  EBIC_CUDA_TRY(cudaEventCreate(&e0));
+  EBIC_CUDA_TRY(cudaEventCreate(&e1));
+  float best = 1e30f;
+  ebic_eval_tuning_t chosen = cands.empty() ? ebic_eval_tuning_t{} : cands[0];
+  ebic_status st = EBIC_OK;
+  for (const ebic_eval_tuning_t& c : cands) {
+    h->tuning = c;
+    if ((st = eval_any<CHECK>(h, pop, a, s)) != EBIC_OK) break;
+    cudaEventRecord(e0, s);
+    for (int r = 0; r < 3 && st == EBIC_OK; ++r) st = eval_any<CHECK>(h, pop, a, s);
+    if (st != EBIC_OK) break;
+    cudaEventRecord(e1, s);
+    if (cudaEventSynchronize(e1) != cudaSuccess) {
+      st = fail(EBIC_ERR_CUDA, "autotune: event wait failed");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      chosen = c;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->tuning = chosen;
+  if (best_us) *best_us = best * 1000.f / 3.f;
+  return st;
+}
+
+ebic_status autotune_fixed(ebic_ctx* h, const uint16_t* d_seq, const int32_t* d_len,
+                           int32_t stride, const EvalArgs& a, cudaStream_t s, float* best_us) {
+  FixedPop pop{d_seq, d_len, stride};
+  return autotune_any<false>(h, pop, a, s, best_us);
+}
+
+ebic_status eval_archive(ebic_ctx* h, const ArchivePop& pop, const EvalArgs& a, cudaStream_t s) {
+  return eval_any<false>(h, pop, a, s);
+}
+
+ebic_status autotune_archive(ebic_ctx* h, const ArchivePop& pop, const EvalArgs& a,
+                             cudaStream_t s, float* best_us) {
+  return autotune_any<false>(h, pop, a, s, best_us);
 }
 
 ebic_status eval_cbf(ebic_ctx* h, const int32_t* d_off, const int32_t* d_cols, int32_t total,
@@ -573,7 +710,7 @@ ebic_status build_pair_table(ebic_ctx* h, cudaStream_t s) {
   }
   h->LT = static_cast<uint32_t*>(p);
   h->LT_bytes = bytes;
-  dim3 grid((unsigned)((h->W + 31) / 32), (unsigned)((h->C + 7) / 8));
+  dim3 grid((unsigned)((h->R_pad / 128 + 7) / 8), (unsigned)((h->C + 7) / 8));
   k_pair_table<<<grid, 256, 0, s>>>(h->A_c, h->C, h->R_pad, h->W, h->LT);
   count_launches(1);
   EBIC_CUDA_TRY(cudaGetLastError());
@@ -744,16 +881,21 @@ ebic_status ebic_set_path(ebic_handle h, int32_t path) {
   return EBIC_OK;
 }
 
-ebic_status ebic_set_eval_tuning(ebic_handle h, int32_t group_lanes, int32_t vecs_bitmask,
-                                 int32_t vecs_gather) {
+ebic_status ebic_set_eval_tuning(ebic_handle h, const ebic_eval_tuning_t* t) {
   if (!h) return fail(EBIC_ERR_ARG, "null handle");
-  if (group_lanes != 0 && (group_lanes < 1 || group_lanes > 32 ||
-                           (group_lanes & (group_lanes - 1)) != 0))
-    return fail(EBIC_ERR_ARG, "group_lanes must be 0 or a power of two in [1, 32]");
-  if (vecs_bitmask < 0 || vecs_gather < 0) return fail(EBIC_ERR_ARG, "negative tile size");
-  h->tune_group = group_lanes;
-  h->tune_vecs_bitmask = vecs_bitmask;
-  h->tune_vecs_gather = vecs_gather;
+  ebic_eval_tuning_t z{};
+  if (!t) t = &z;
+  if (t->kernel < 0 || t->kernel > 2) return fail(EBIC_ERR_ARG, "kernel must be 0, 1 or 2");
+  if (t->vecs_per_part_bitmask < 0 || t->vecs_per_part_gather < 0)
+    return fail(EBIC_ERR_ARG, "negative part size");
+  if (!(t->batch_steps == 0 || t->batch_steps == 4 || t->batch_steps == 8))
+    return fail(EBIC_ERR_ARG, "batch_steps must be 0, 4 or 8");
+  if (!(t->vecs_per_lane == 0 || t->vecs_per_lane == 1 || t->vecs_per_lane == 2 ||
+        t->vecs_per_lane == 4))
+    return fail(EBIC_ERR_ARG, "vecs_per_lane must be 0, 1, 2 or 4");
+  if (t->vecs_per_lane == 4 && t->batch_steps == 8)
+    return fail(EBIC_ERR_ARG, "vecs_per_lane 4 allows batch_steps 4 only");
+  h->tuning = *t;
   return EBIC_OK;
 }
 
@@ -839,6 +981,43 @@ ebic_status ebic_eval_population_dev(ebic_handle h, const int32_t* d_offsets,
     a.dec = h->st_dec.as<uint32_t>();
   }
   return eval_cbf(h, d_offsets, d_cols, total_cols, a, s);
+}
+
+ebic_status ebic_autotune_eval(ebic_handle h, const int32_t* d_offsets, const int32_t* d_cols,
+                               int32_t P, int32_t total_cols, int32_t sigma, int32_t support_mode,
+                               uint32_t* d_inc, uint32_t* d_dec, double* d_fitness, void* stream,
+                               ebic_eval_tuning_t* chosen, float* best_us) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  if (P <= 0 || P > (1 << 24)) return fail(EBIC_ERR_ARG, "P = %d outside [1, 2^24]", P);
+  if (!d_offsets || !d_cols || !d_inc || !d_fitness) return fail(EBIC_ERR_ARG, "null pointer");
+  if (support_mode != EBIC_SUPPORT_INC && support_mode != EBIC_SUPPORT_INC_PLUS_DEC)
+    return fail(EBIC_ERR_ARG, "bad support mode %d", support_mode);
+  DeviceGuard g(h->device);
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  EvalArgs a{};
+  a.P = P;
+  a.sigma = sigma;
+  a.mode = support_mode;
+  a.want_dec = d_dec != nullptr;
+  a.inc = d_inc;
+  a.fit = d_fitness;
+  if (d_dec) {
+    a.dec = d_dec;
+  } else if (support_mode == EBIC_SUPPORT_INC_PLUS_DEC) {
+    EBIC_TRY(h->st_dec.reserve((size_t)P * sizeof(uint32_t)));
+    a.dec = h->st_dec.as<uint32_t>();
+  }
+  if (resolve_path(h) == EBIC_PATH_BITMASK && !h->LT) EBIC_TRY(build_pair_table(h, s));
+  CbfPop pop{d_offsets, d_cols, total_cols};
+  EBIC_TRY(autotune_any<true>(h, pop, a, s, best_us));
+  if (chosen) *chosen = h->tuning;
+  return EBIC_OK;
+}
+
+ebic_status ebic_get_eval_tuning(ebic_handle h, ebic_eval_tuning_t* out) {
+  if (!h || !out) return fail(EBIC_ERR_ARG, "null pointer");
+  *out = h->tuning;
+  return EBIC_OK;
 }
 
 ebic_status ebic_check_device_error(ebic_handle h) {

@@ -1,0 +1,165 @@
+"""Parity of the device generation loop (Steps 1-5) with the oracle: the
+same seed gives the same populations, fitness and top-rank lists, generation
+by generation, bit for bit."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1801_03039_gb300 as eb
+from paper_1801_03039_gb300 import synth
+from helpers import assert_bits_equal
+
+pytestmark = pytest.mark.gpu
+
+BASE = dict(pop_size=100, len_min=2, len_max=6, iterations=10, sigma=10, toprank_size=100,
+            tournament_k=2, overlap_tau=0.5, elite_frac=0.25, penalty_base=1.2,
+            p_crossover=0.5, seed=0)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    eb.build()
+    yield
+
+
+def _device_params(kw):
+    d = dict(kw)
+    mode = d.pop("fitness_support", 0)
+    p = eb.ebic_default_params(**d)
+    p.support_mode = mode
+    return p
+
+
+def run_both(A, gens_to_check=None, **kw):
+    kw = {**BASE, **kw}
+    ref = oracle.run(A, trace=True, **kw)
+    h = eb.ebic_load_matrix(A)
+    try:
+        p = _device_params(kw)
+        eb.ebic_run_init(h, p)
+        P, T, L = kw["pop_size"], kw["toprank_size"], kw["len_max"]
+        done = ref["stats"]["generations_done"]
+        checks = range(done + 1) if gens_to_check is None else gens_to_check
+        if ref["stats"]["stop_reason"] == 2:        # Step 1 never completed
+            checks = ()
+            assert eb.ebic_get_population(h, P, L)["seqs"] == []
+        stats = None
+        for g in range(done + 1):
+            if g > 0:
+                stats = eb.ebic_run_step(h, 1)
+            if g in checks:
+                _compare_generation(h, ref, g, P, T, L, kw)
+        # the run stops (or ends) exactly where the oracle's does
+        rest = kw["iterations"] - done
+        if rest:
+            stats = eb.ebic_run_step(h, rest)
+        if stats is None:
+            stats = eb.ebic_run_step(h, 0)
+        rs = ref["stats"]
+        for key in ("generations_done", "stop_reason", "tabu_hits_total", "attempts_total",
+                    "evaluations_total", "last_gen_hits", "toprank_n"):
+            assert stats[key] == rs[key], (key, stats[key], rs[key])
+        top, fit, inc = eb.ebic_get_toprank(h, T, L)
+        assert top == ref["toprank"]
+        assert_bits_equal(fit, ref["toprank_f"], "final toprank fitness")
+        assert_bits_equal(inc, ref["toprank_inc"], "final toprank inc")
+        return stats
+    finally:
+        eb.ebic_free(h)
+
+
+def _compare_generation(h, ref, g, P, T, L, kw):
+    pop = eb.ebic_get_population(h, P, L)
+    rp = ref["trace_pop"][g]
+    if pop["seqs"] != rp["seqs"]:
+        bad = [i for i in range(P) if pop["seqs"][i] != rp["seqs"][i]][:5]
+        raise AssertionError(f"generation {g}: population differs at {bad}: "
+                             f"{[pop['seqs'][i] for i in bad]} vs {[rp['seqs'][i] for i in bad]}")
+    assert_bits_equal(pop["inc"], rp["inc"], f"gen {g} inc")
+    if kw.get("fitness_support", 0) == 1:
+        assert_bits_equal(pop["dec"], rp["dec"], f"gen {g} dec")
+    assert_bits_equal(pop["f"], rp["f"], f"gen {g} fitness")
+    top, fit, _ = eb.ebic_get_toprank(h, T, L)
+    rt = ref["trace_top"][g]
+    assert top == rt["seqs"], f"generation {g}: top-rank list differs"
+    assert_bits_equal(fit, rt["f"], f"gen {g} toprank fitness")
+
+
+def test_tiny_200x20_ten_generations():
+    prob = synth.matrix_tiny(seed=0)
+    st = run_both(prob.A)
+    assert st["generations_done"] == 10
+
+
+def test_paper_1000x100_population_600():
+    prob = synth.matrix_paper(seed=0)
+    run_both(prob.A, gens_to_check={0, 1, 2, 10, 30}, pop_size=600, len_min=3, len_max=20,
+             sigma=25, iterations=30)
+
+
+@pytest.mark.parametrize("variant", [
+    dict(tournament_k=1), dict(tournament_k=3), dict(tournament_k=4),
+    dict(p_crossover=0.0), dict(p_crossover=1.0), dict(fitness_support=1),
+    dict(penalty_base=1.0), dict(penalty_base=2.5), dict(elite_frac=0.0), dict(elite_frac=1.0),
+    dict(toprank_size=5), dict(overlap_tau=0.75), dict(overlap_tau=0.0), dict(seed=12345),
+    dict(len_min=3, len_max=3), dict(sigma=1000)])
+def test_parameter_variants(variant):
+    prob = synth.matrix_tiny(seed=1)
+    run_both(prob.A, iterations=8, **variant)
+
+
+def test_ties_and_nan_matrix():
+    rng = np.random.default_rng(2)
+    A = rng.integers(-2, 3, (300, 12)).astype(np.float32)
+    A[rng.random(A.shape) < 0.03] = np.nan
+    run_both(A, iterations=8, len_max=5)
+
+
+def test_tabu_stop_matches():
+    A = np.random.default_rng(0).standard_normal((50, 3)).astype(np.float32)
+    st = run_both(A, iterations=100, pop_size=6, len_min=2, len_max=3, sigma=2, toprank_size=10)
+    assert st["stop_reason"] == 1 and st["generations_done"] < 100
+
+
+def test_step1_failure_matches():
+    A = np.random.default_rng(0).standard_normal((20, 2)).astype(np.float32)
+    st = run_both(A, iterations=3, pop_size=3, len_min=2, len_max=2, sigma=2, toprank_size=4)
+    assert st["stop_reason"] == 2
+
+
+def test_one_call_run_generations_equals_stepping():
+    prob = synth.matrix_tiny(seed=3)
+    kw = {**BASE, "iterations": 12, "seed": 7}
+    ref = oracle.run(prob.A, **kw)
+    h = eb.ebic_load_matrix(prob.A)
+    try:
+        top, fit, st = eb.ebic_run_generations(h, _device_params(kw))
+    finally:
+        eb.ebic_free(h)
+    assert top == ref["toprank"] and st["generations_done"] == 12
+    assert_bits_equal(fit, ref["toprank_f"], "toprank fitness")
+
+
+def test_state_errors():
+    prob = synth.matrix_tiny(seed=0)
+    h = eb.ebic_load_matrix(prob.A)
+    try:
+        with pytest.raises(eb.EbicError) as e:
+            eb.ebic_run_step(h, 1)
+        assert e.value.status == 5
+        eb.ebic_run_init(h, _device_params({**BASE, "iterations": 2}))
+        eb.ebic_run_step(h, 2)
+        with pytest.raises(eb.EbicError) as e:
+            eb.ebic_run_step(h, 1)
+        assert e.value.status == 5
+        with pytest.raises(eb.EbicError) as e:
+            eb.ebic_run_init(h, _device_params({**BASE, "len_max": 21}))
+        assert e.value.status == 1
+    finally:
+        eb.ebic_free(h)
+
+
+def test_expression_shape_three_generations():
+    prob = synth.matrix_expression(seed=0)
+    run_both(prob.A, gens_to_check={0, 3}, pop_size=4096, len_min=3, len_max=30, sigma=50,
+             iterations=3)

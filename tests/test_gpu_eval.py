@@ -129,9 +129,12 @@ def test_pair_table_words_match_numpy():
         for q in range(C):
             bits = np.zeros(W * 32, bool)
             bits[:R] = A[:, p] < A[:, q]
-            want = np.packbits(bits.reshape(W, 32)[:, ::-1], axis=1)
+            # word 4b + i, bit l  <->  row 128 b + 4 l + i
+            blk = bits.reshape(W // 4, 32, 4)                  # [b][l][i]
+            want = np.zeros(W, np.uint64)
+            for i in range(4):
+                want[i::4] = (blk[:, :, i] * (1 << np.arange(32, dtype=np.uint64))).sum(1)
             want = want.astype(np.uint32)
-            want = (want[:, 0] << 24) | (want[:, 1] << 16) | (want[:, 2] << 8) | want[:, 3]
             got = eb.ebic_read_pair_words(h, p, q, 0, W)
             assert np.array_equal(got, want), (p, q)
     eb.ebic_free(h)
@@ -200,7 +203,14 @@ def test_device_variant_flags_invalid_series(path):
 
 
 @pytest.mark.parametrize("shape", [(200, 20), (1000, 100), (4097, 30), (20000, 60)])
-@pytest.mark.parametrize("tune", [(0, 0, 0), (1, 0, 0), (32, 0, 0), (32, 32, 32), (32, 64, 96)])
+@pytest.mark.parametrize("tune", [dict(), dict(kernel=1), dict(kernel=2),
+                                  dict(kernel=2, vecs_per_part_bitmask=32, vecs_per_part_gather=32),
+                                  dict(kernel=2, batch_steps=4, vecs_per_lane=1),
+                                  dict(kernel=2, batch_steps=8, vecs_per_lane=1),
+                                  dict(kernel=2, batch_steps=4, vecs_per_lane=2),
+                                  dict(kernel=2, batch_steps=8, vecs_per_lane=2),
+                                  dict(kernel=2, batch_steps=4, vecs_per_lane=4,
+                                       vecs_per_part_bitmask=64)])
 def test_launch_shapes_do_not_change_results(shape, tune):
     # lane-per-vector kernel, warp kernel, and forced splits of each series
     R, C = shape
@@ -212,11 +222,44 @@ def test_launch_shapes_do_not_change_results(shape, tune):
     try:
         for path in PATHS:
             eb.ebic_set_path(h, path)
-            eb.ebic_set_eval_tuning(h, *tune)
-            inc, dec, fit = eb.ebic_eval_population(h, off, cols, max(10, R // 100), 1)
-            eb.ebic_check_device_error(h)
-            assert_bits_equal(inc, oinc, f"inc {path} {tune}")
-            assert_bits_equal(dec, odec, f"dec {path} {tune}")
-            assert_bits_equal(fit, ofit, f"fit {path} {tune}")
+            eb.ebic_set_eval_tuning(h, **tune)
+            for mode in (0, 1):
+                inc, dec, fit = eb.ebic_eval_population(h, off, cols, max(10, R // 100), mode,
+                                                        want_dec=(mode == 1))
+                eb.ebic_check_device_error(h)
+                assert_bits_equal(inc, oinc, f"inc {path} {tune}")
+                if mode == 1:
+                    assert_bits_equal(dec, odec, f"dec {path} {tune}")
+                    assert_bits_equal(fit, ofit, f"fit {path} {tune}")
+    finally:
+        eb.ebic_free(h)
+
+
+@pytest.mark.parametrize("which", ["paper", "expression"])
+def test_autotuner_keeps_results_exact(which):
+    torch = pytest.importorskip("torch")
+    if which == "paper":
+        prob, P, lo, hi, sig = synth.matrix_paper(seed=7), 600, 3, 20, 25
+    else:
+        prob, P, lo, hi, sig = synth.matrix_expression(seed=7), 4096, 3, 30, 50
+    off, cols = synth.population(8, P, prob.A.shape[1], lo, hi, plants=prob.plants)
+    oinc, _, ofit = oracle_eval(prob.A, off, cols, sig)
+    dev = torch.device("cuda:0")
+    h = eb.ebic_load_matrix(prob.A)
+    try:
+        for path in PATHS:
+            eb.ebic_set_path(h, path)
+            d_off = torch.from_numpy(off).to(dev)
+            d_cols = torch.from_numpy(cols).to(dev)
+            inc = torch.zeros(P, dtype=torch.int32, device=dev)
+            fit = torch.zeros(P, dtype=torch.float64, device=dev)
+            shape, us = eb.ebic_autotune_eval(h, d_off, d_cols, P, len(cols), sig, 0, inc, None,
+                                              fit)
+            assert us > 0 and shape == eb.ebic_get_eval_tuning(h)
+            assert_bits_equal(inc.cpu().numpy().view(np.uint32), oinc, f"inc {path}")
+            assert_bits_equal(fit.cpu().numpy(), ofit, f"fit {path}")
+            inc2, _, fit2 = eb.ebic_eval_population(h, off, cols, sig)
+            assert_bits_equal(inc2, oinc, "inc after tuning")
+            assert_bits_equal(fit2, ofit, "fit after tuning")
     finally:
         eb.ebic_free(h)
