@@ -183,6 +183,32 @@ ebic_status ebic_eval_population_dev(ebic_handle h, const int32_t* d_offsets,
 /* Synchronises the handle's work and reports/clears the device error flag. */
 ebic_status ebic_check_device_error(ebic_handle h);
 
+/* Evaluation that allocates nothing (the paper has no counterpart to this
+ * entry point).  For callers that must not have a library allocate device
+ * memory -- code inside a host framework that owns the device memory through
+ * its own pool, or a latency-critical loop that cannot take the device
+ * synchronisation an allocation may cause.  It computes the same inc and
+ * fitness as ebic_eval_population_dev with EBIC_SUPPORT_INC and no dec
+ * output, queued on `stream`; the caller owns every input and output.
+ * Series split across warps keep their partial counts in one fixed static
+ * device array of 16 bytes per series, EBIC_NOALLOC_MAX_SERIES series (1 MiB),
+ * which every GPU that loads the library holds until the process exits.
+ *   - P above EBIC_NOALLOC_MAX_SERIES gives EBIC_ERR_ARG (nothing queued).
+ *   - It never builds the pair table: with the table already built (and the
+ *     path not forced to gather) it uses it, otherwise the gather path.
+ *   - The first call on each device looks up the array's device address with
+ *     that device current; make that first call before any stream capture.
+ *   - All calls share the array, which keeps the last call's contents (each
+ *     call clears the part it uses first): calls that overlap on the GPU --
+ *     from several streams, threads or handles at once -- race.
+ *   - Invalid series are reported through ebic_check_device_error, as for
+ *     ebic_eval_population_dev. */
+#define EBIC_NOALLOC_MAX_SERIES 65536
+ebic_status ebic_eval_population_dev_noalloc(ebic_handle h, const int32_t* d_offsets,
+                                             const int32_t* d_cols, int32_t P,
+                                             int32_t total_cols, int32_t sigma, uint32_t* d_inc,
+                                             double* d_fitness, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Generation loop: Steps 1-5 of the "EBIC Algorithm" section, run entirely on
  * the device.  Semantics (identical to the library's reference reading):

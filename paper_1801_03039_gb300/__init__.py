@@ -24,7 +24,7 @@ __all__ = [
     "ebic_matrix_shape", "ebic_build_pair_table", "ebic_pair_table_bytes",
     "ebic_read_pair_words", "ebic_set_path", "ebic_set_eval_tuning", "ebic_get_eval_tuning",
     "ebic_autotune_eval", "ebic_eval_population",
-    "ebic_eval_population_dev", "ebic_check_device_error", "ebic_default_params",
+    "ebic_eval_population_dev", "ebic_eval_population_dev_noalloc", "ebic_check_device_error", "ebic_default_params",
     "ebic_run_init", "ebic_run_step", "ebic_get_toprank", "ebic_get_population",
     "ebic_run_generations", "Params", "Stats", "PATH_AUTO", "PATH_GATHER", "PATH_BITMASK",
     "SUPPORT_INC", "SUPPORT_INC_PLUS_DEC",
@@ -87,6 +87,7 @@ _SIGS = {
     "ebic_eval_population": ([_P, _P, _P, _I32, _I32, _I32, _P, _P, _P], _I32),
     "ebic_eval_population_dev": ([_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P], _I32),
     "ebic_check_device_error": ([_P], _I32),
+    "ebic_eval_population_dev_noalloc": ([_P, _P, _P, _I32, _I32, _I32, _P, _P, _P], _I32),
     "ebic_default_params": ([_P], None),
     "ebic_run_init": ([_P, _P], _I32),
     "ebic_run_step": ([_P, _I32, _P], _I32),
@@ -260,6 +261,15 @@ def ebic_eval_population_dev(h, d_offsets, d_cols, P: int, total_cols: int, sigm
                                           int(total_cols), int(sigma), int(support_mode),
                                           _dev(d_inc), _dev(d_dec), _dev(d_fitness),
                                           _stream(stream)))
+
+
+def ebic_eval_population_dev_noalloc(h, d_offsets, d_cols, P: int, total_cols: int,
+                                     sigma: int, d_inc, d_fitness, stream=None):
+    """Rising support and Eq. (1) on device buffers without any allocation by
+    the library (fixed static scratch; see include/ebic.h)."""
+    _check(lib().ebic_eval_population_dev_noalloc(h, _dev(d_offsets), _dev(d_cols), int(P),
+                                                  int(total_cols), int(sigma), _dev(d_inc),
+                                                  _dev(d_fitness), _stream(stream)))
 
 
 def ebic_check_device_error(h):

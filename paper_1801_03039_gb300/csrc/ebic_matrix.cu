@@ -13,6 +13,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <mutex>
 #include <cstring>
 #include <vector>
 
@@ -778,9 +779,94 @@ static ebic_status place(ebic_ctx* h, const float* rowmajor_dev, cudaStream_t s)
   return EBIC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Evaluation without any allocation.  Some callers cannot let a library call
+// cudaMalloc: a host framework that owns all device memory through its own
+// pool, or a latency-critical loop that cannot afford the implicit device
+// synchronisation an allocation may cause.  This variant of the split-series
+// support launch keeps its per-series scratch (the partial counts and arrival
+// tickets of series that several warps share) in the fixed array below
+// instead of memory owned by the handle, and it never builds the pair table.
+// ---------------------------------------------------------------------------
+static __device__ __align__(256) unsigned long long
+    g_noalloc_scratch[2 * (size_t)EBIC_NOALLOC_MAX_SERIES];
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[256] = {};   // device address of the array, per device
+
+// Device address of g_noalloc_scratch on the current device.  Host code only
+// holds a stand-in for the symbol, so the real address is fetched once per
+// device, with that device current.
+static ebic_status noalloc_scratch(int device, void** out) {
+  if (device < 0 || device >= 256) return fail(EBIC_ERR_ARG, "device ordinal %d", device);
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[device]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+      cudaGetLastError();
+      return fail(EBIC_ERR_CUDA, "cudaGetSymbolAddress(g_noalloc_scratch) failed: %s",
+                  cudaGetErrorString(e));
+    }
+    g_noalloc_ptr[device] = p;
+  }
+  *out = g_noalloc_ptr[device];
+  return EBIC_OK;
+}
+
 }  // namespace ebic
 
 using namespace ebic;
+
+extern "C" ebic_status ebic_eval_population_dev_noalloc(ebic_handle h, const int32_t* d_offsets,
+                                                        const int32_t* d_cols, int32_t P,
+                                                        int32_t total_cols, int32_t sigma,
+                                                        uint32_t* d_inc, double* d_fitness,
+                                                        void* stream) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  if (P < 0 || P > EBIC_NOALLOC_MAX_SERIES)
+    return fail(EBIC_ERR_ARG,
+                "P = %d outside [0, %d]: the no-allocation evaluation has fixed scratch for at "
+                "most EBIC_NOALLOC_MAX_SERIES series per call",
+                P, EBIC_NOALLOC_MAX_SERIES);
+  if (P == 0) return EBIC_OK;
+  if (!d_offsets || !d_cols || !d_inc || !d_fitness) return fail(EBIC_ERR_ARG, "null pointer");
+  if (total_cols < 0) return fail(EBIC_ERR_ARG, "negative total_cols");
+  DeviceGuard g(h->device);
+  void* scratch = nullptr;
+  EBIC_TRY(noalloc_scratch(h->device, &scratch));
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the words this call uses start at zero (the kernel also leaves them zero)
+  EBIC_CUDA_TRY(cudaMemsetAsync(scratch, 0, (size_t)P * 2 * sizeof(unsigned long long), s));
+  EvalArgs a{};
+  a.P = P;
+  a.sigma = sigma;
+  a.mode = EBIC_SUPPORT_INC;
+  a.want_dec = 0;
+  a.inc = d_inc;
+  a.dec = nullptr;
+  a.fit = d_fitness;
+  a.lnf = nullptr;
+  CbfPop pop{d_offsets, d_cols, total_cols};
+  uint32_t* sc = static_cast<uint32_t*>(scratch);
+  const bool bitmask = h->LT != nullptr && h->path != EBIC_PATH_GATHER;
+  int32_t vpi = 0, ipc = 1;
+  if (bitmask) {
+    choose_split(P, h->W >> 2, 0, &vpi, &ipc, 32);
+    const unsigned blocks = (unsigned)(((int64_t)P * ipc + kWarpsPerCta - 1) / kWarpsPerCta);
+    k_support_bitmask_warp<false, true, 1, 8, CbfPop><<<blocks, 32 * kWarpsPerCta, 0, s>>>(
+        h->LT, h->C, h->W, h->R, pop, a, vpi, ipc, sc, h->LN, h->d_err);
+  } else {
+    choose_split(P, h->R_pad >> 2, 0, &vpi, &ipc);
+    const unsigned blocks = (unsigned)(((int64_t)P * ipc + kWarpsPerCta - 1) / kWarpsPerCta);
+    k_support_gather<false, true, CbfPop><<<blocks, 32 * kWarpsPerCta, 0, s>>>(
+        h->A_c, h->C, h->R_pad, h->R, pop, a, vpi, ipc, sc, h->LN, h->d_err);
+  }
+  count_launches(1);
+  EBIC_CUDA_TRY(cudaGetLastError());
+  return EBIC_OK;
+}
+
 
 // ===========================================================================
 // C ABI
