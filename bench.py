@@ -7,6 +7,10 @@
 Prints ONE JSON line (rank 0).  Workloads (seeded synthetic inputs, see
 paper_1801_03039_gb300/synth.py):
 
+  generations-paper (default) 1,000 x 100 N(0,1) matrix with shift, scale
+                   and order-preserving 50 x 10 plants; population 600 of
+                   length 3-20.  A step is one generation of Steps 2-5, run on
+                   the device as a replayed CUDA graph.
   eval-expression  20,000 x 200 log-normal matrix with 10 planted overlapping
                    order-preserving biclusters; a population of 4,096 series of
                    length 3-30.  A step is one fitness pass (support + Eq. (1))
@@ -243,7 +247,87 @@ class EvalExpression:
         return n, dt
 
 
-WORKLOADS = {"eval-expression": EvalExpression}
+class GenerationsPaper:
+    """1000 x 100 N(0,1) matrix with shift, scale and order-preserving 50 x 10
+    plants; population 600, lengths 3-20, sigma 25.  A step is one generation
+    (Steps 2-5: elitism, tournaments, operators, tabu, evaluation, top-rank)."""
+    name = "generations-paper"
+    R, C, P, LMIN, LMAX, SIGMA, T, GENS = 1000, 100, 600, 3, 20, 25, 100, 1000
+
+    def __init__(self, rank: int):
+        from paper_1801_03039_gb300 import synth
+        self.rank = rank
+        self.prob = synth.matrix_paper(seed=rank)
+
+    def params_kw(self, iterations: int):
+        return dict(pop_size=self.P, len_min=self.LMIN, len_max=self.LMAX, iterations=iterations,
+                    sigma=self.SIGMA, toprank_size=self.T, tournament_k=2, overlap_tau=0.5,
+                    elite_frac=0.25, penalty_base=1.2, p_crossover=0.5, seed=self.rank)
+
+    def config(self):
+        return {"workload": "generations-paper-1000x100-P600-L3-20",
+                "rows": self.R, "cols": self.C, "population": self.P,
+                "series_len": [self.LMIN, self.LMAX], "sigma": self.SIGMA, "toprank": self.T,
+                "tournament_k": 2, "overlap_tau": 0.5, "elite_frac": 0.25, "penalty_base": 1.2,
+                "p_crossover": 0.5, "step": "one generation (Steps 2-5) as a replayed CUDA graph",
+                "launch_shape": getattr(self, "tuning", None),
+                "l2": "flushed before every timed step (512 MiB overwrite)"}
+
+    def units_per_step(self) -> int:
+        return self.P * self.R
+
+    def setup_gpu(self, torch, eb, capacity: int):
+        self.h = eb.ebic_load_matrix(self.prob.A)
+        self.eb = eb
+        eb.ebic_run_init(self.h, eb.ebic_default_params(**self.params_kw(capacity)))
+        self.tuning = eb.ebic_get_eval_tuning(self.h)
+        self.capacity = capacity
+
+    def step_gpu(self, torch, eb, stream):
+        eb.ebic_run_step_async(self.h, 1, stream)
+
+    def check_gpu(self, torch, eb, expect_done: int):
+        st = eb.ebic_run_step(self.h, 0)
+        if st["stop_reason"] != 0 or st["generations_done"] != expect_done:
+            raise RuntimeError(f"run stopped early: {st}")
+        return st
+
+    def profile_gpu(self, eb, n: int = 5) -> dict:
+        acc = {}
+        for _ in range(n):
+            for k, v in eb.ebic_run_step_profiled(self.h).items():
+                acc.setdefault(k, []).append(v)
+        return {k: statistics.mean(v) for k, v in acc.items()}
+
+    def e2e_gpu(self, torch, eb, steps: int) -> dict:
+        """A whole user run through the host API: load the matrix, run the
+        configuration's 1,000 generations, read the top-rank list, free."""
+        t0 = time.perf_counter()
+        h = eb.ebic_load_matrix(self.prob.A)
+        top, fit, st = eb.ebic_run_generations(h, eb.ebic_default_params(
+            **self.params_kw(self.GENS)))
+        eb.ebic_free(h)
+        dt = time.perf_counter() - t0
+        gens = st["generations_done"]
+        return {"value": self.units_per_step() * gens / dt, "unit": "tests/s",
+                "generations_per_s": gens / dt, "generations": gens,
+                "h2d_bytes_per_step": int(self.prob.A.nbytes / max(gens, 1)),
+                "d2h_bytes_per_step": int(sum(len(t) for t in top) * 4 + len(fit) * 12),
+                "scope": "ebic_load_matrix + ebic_run_generations (Step 1 + 1,000 generations, "
+                         "top-rank read back) + ebic_free, wall clock"}
+
+    def oracle_generations(self, oracle, budget_s: float):
+        g = 2
+        while True:
+            t0 = time.perf_counter()
+            oracle.run(self.prob.A, **self.params_kw(g))
+            dt = time.perf_counter() - t0
+            if dt > budget_s / 4 or g >= 256:
+                return g, dt
+            g *= 4
+
+
+WORKLOADS = {"eval-expression": EvalExpression, "generations-paper": GenerationsPaper}
 
 
 # ---------------------------------------------------------------------------
@@ -256,7 +340,11 @@ def run_ours(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     eb.build()
     wl = WORKLOADS[args.workload](rank)
-    wl.setup_gpu(torch, eb)
+    gens = isinstance(wl, GenerationsPaper)
+    if gens:
+        wl.setup_gpu(torch, eb, capacity=args.warmup + args.steps + 16)
+    else:
+        wl.setup_gpu(torch, eb)
     stream = torch.cuda.current_stream()
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
     for i in range(args.warmup):
@@ -282,6 +370,12 @@ def run_ours(args, ws, rank, local):
     clk = clocks.stop() if clocks else None
     per_step_ms = [a.elapsed_time(b) for a, b in events]
     total_s = sum(per_step_ms) / 1e3
+    extra = {}
+    if gens:
+        st = wl.check_gpu(torch, eb, args.warmup + args.steps)
+        extra["run_stats"] = st
+        kern = wl.profile_gpu(eb)
+        extra["kernel_us"] = {k: round(v, 2) for k, v in kern.items()}
     barrier(ws)
     slowest = aggregate_max(total_s, ws, device=torch.device("cuda", local))
     e2e = wl.e2e_gpu(torch, eb, max(3, args.steps))
@@ -292,10 +386,6 @@ def run_ours(args, ws, rank, local):
         return None
     value = ws * wl.units_per_step() * args.steps / slowest
     peaks = load_peaks()
-    alg_bytes, alg_def = wl.algorithmic_bytes()
-    kernel_s = statistics.mean(per_step_ms) / 1e3
-    achieved = alg_bytes / kernel_s / 1e9
-    traffic = read_traffic(args.workload)
     out = {
         "metric": METRIC, "value": value, "unit": "tests/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
@@ -305,16 +395,30 @@ def run_ours(args, ws, rank, local):
         "config": wl.config(),
         "e2e": e2e,
         "gpu_launches": int(launches),
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"],
-                     "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
-                     "traffic": traffic, "algorithmic_bytes": alg_bytes,
-                     "algorithmic_def": alg_def, "kernel": "k_support_bitmask_warp",
-                     "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})"},
-        "clocks": clk,
     }
+    if gens:
+        out["generations_per_s"] = ws * args.steps / slowest
+    out.update(extra)
+    out["roofline"] = roofline(wl, gens, extra, per_step_ms, peaks)
+    out["clocks"] = clk
     if ws == 1:
         out["cpu_baseline"] = cpu_baseline(wl, budget_s=12.0)
     return out
+
+
+def roofline(wl, gens, extra, per_step_ms, peaks):
+    if not gens:
+        alg_bytes, alg_def = wl.algorithmic_bytes()
+        kernel_s = statistics.mean(per_step_ms) / 1e3
+        achieved = alg_bytes / kernel_s / 1e9
+        return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": read_traffic(wl.name),
+                "algorithmic_bytes": alg_bytes, "algorithmic_def": alg_def,
+                "kernel": "k_support_bitmask_warp",
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})"}
+    kern = extra["kernel_us"]
+    dom = max(kern, key=kern.get)
+    return {"dominant_kernel": dom, "kernel_us": kern, "note": "see DESIGN.md"}
 
 
 def read_traffic(workload: str):
@@ -330,6 +434,12 @@ def read_traffic(workload: str):
 
 def cpu_baseline(wl, budget_s: float):
     import oracle
+    if isinstance(wl, GenerationsPaper):
+        g, dt = wl.oracle_generations(oracle, budget_s)
+        return {"value": wl.units_per_step() * (g + 1) / dt, "unit": "tests/s",
+                "generations_per_s": (g + 1) / dt, "cores": 1, "kind": "oracle",
+                "sample": f"Step 1 + {g} generations of the same run, sequential oracle on one "
+                          f"core ({dt:.2f} s)"}
     cores = os.cpu_count() or 1
     n, dt = wl.oracle_sample(oracle, budget_s, cores)
     return {"value": n * wl.R / dt, "unit": "tests/s", "cores": cores, "kind": "oracle",
@@ -343,23 +453,36 @@ def run_reference(args, ws, rank):
     import oracle
     wl = WORKLOADS[args.workload](0)
     cores = os.cpu_count() or 1
-    n, _ = wl.oracle_sample(oracle, 8.0, cores)
-    off = wl.off[:n + 1]
-    cols = wl.cols[:off[-1]]
-    for _ in range(args.warmup):
-        oracle.support(wl.prob.A, off, cols, nthreads=cores)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        oracle.support(wl.prob.A, off, cols, nthreads=cores)
-    dt = time.perf_counter() - t0
-    value = n * wl.R * args.steps / dt
-    sample = f"first {n} of {wl.P} series x all {wl.R} rows per step, OpenMP on {cores} threads"
+    if isinstance(wl, GenerationsPaper):
+        g, _ = wl.oracle_generations(oracle, 4.0)
+        for _ in range(args.warmup):
+            oracle.run(wl.prob.A, **wl.params_kw(1))
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            oracle.run(wl.prob.A, **wl.params_kw(g))
+        dt = time.perf_counter() - t0
+        value = wl.units_per_step() * (g + 1) * args.steps / dt
+        sample = f"each step: Step 1 + {g} generations, sequential oracle on one core"
+        used = 1
+    else:
+        n, _ = wl.oracle_sample(oracle, 8.0, cores)
+        off = wl.off[:n + 1]
+        cols = wl.cols[:off[-1]]
+        for _ in range(args.warmup):
+            oracle.support(wl.prob.A, off, cols, nthreads=cores)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            oracle.support(wl.prob.A, off, cols, nthreads=cores)
+        dt = time.perf_counter() - t0
+        value = n * wl.R * args.steps / dt
+        sample = f"first {n} of {wl.P} series x all {wl.R} rows per step, OpenMP on {cores} threads"
+        used = cores
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "tests/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32-compare/u32-count", "data": "synthetic",
-            "config": wl.config(),
-            "cpu_baseline": {"value": value, "unit": "tests/s", "cores": cores,
+            "vs_baseline": None, "dtype": "f32-compare/u32-count/f64-fitness",
+            "data": "synthetic", "config": wl.config(),
+            "cpu_baseline": {"value": value, "unit": "tests/s", "cores": used,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "tests/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
@@ -371,7 +494,7 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="eval-expression")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="generations-paper")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

@@ -269,6 +269,17 @@ ebic_status ebic_run_init(ebic_handle h, const ebic_params_t* p);
 /* Steps 2-5, `generations` times (fewer if the tabu rule stops the run, or if
  * the archive is full: EBIC_ERR_STATE).  Synchronous. */
 ebic_status ebic_run_step(ebic_handle h, int32_t generations, ebic_stats_t* stats);
+/* Steps 2-5, `generations` times, queued on `stream` without waiting and
+ * without reading anything back: generations after a stop do nothing, and
+ * the caller learns where the run stands from ebic_run_step(h, 0, &stats) once
+ * `stream` has been synchronised.  The run must not go past the generations
+ * ebic_run_init sized it for (later generations are not written). */
+ebic_status ebic_run_step_async(ebic_handle h, int32_t generations, void* stream);
+/* One generation (Steps 2-5) as five separate launches with CUDA events between
+ * them; kernel_us[5] (nullable) receives the durations of: attempt
+ * speculation, the sequential Step 3 builder, tabu insertion, Step 4
+ * evaluation, Step 5 ranking.  Synchronous; for measurement. */
+ebic_status ebic_run_step_profiled(ebic_handle h, float* kernel_us);
 /* The current top-rank list as CBF: *inout_n = capacity in records on entry,
  * records written on return; offsets needs capacity + 1 entries and cols
  * capacity * len_max.  fitness / inc may be NULL. */

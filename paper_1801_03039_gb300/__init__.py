@@ -25,7 +25,8 @@ __all__ = [
     "ebic_read_pair_words", "ebic_set_path", "ebic_set_eval_tuning", "ebic_get_eval_tuning",
     "ebic_autotune_eval", "ebic_eval_population",
     "ebic_eval_population_dev", "ebic_eval_population_dev_noalloc", "ebic_check_device_error", "ebic_default_params",
-    "ebic_run_init", "ebic_run_step", "ebic_get_toprank", "ebic_get_population",
+    "ebic_run_init", "ebic_run_step", "ebic_run_step_async", "ebic_run_step_profiled",
+    "ebic_get_toprank", "ebic_get_population",
     "ebic_run_generations", "Params", "Stats", "PATH_AUTO", "PATH_GATHER", "PATH_BITMASK",
     "SUPPORT_INC", "SUPPORT_INC_PLUS_DEC",
 ]
@@ -91,6 +92,8 @@ _SIGS = {
     "ebic_default_params": ([_P], None),
     "ebic_run_init": ([_P, _P], _I32),
     "ebic_run_step": ([_P, _I32, _P], _I32),
+    "ebic_run_step_async": ([_P, _I32, _P], _I32),
+    "ebic_run_step_profiled": ([_P, _P], _I32),
     "ebic_get_toprank": ([_P, _P, _P, _P, _P, _P], _I32),
     "ebic_get_population": ([_P, _P, _P, _P, _P, _P, _P], _I32),
     "ebic_run_generations": ([_P, _P, _P, _P, _P, _P, _P], _I32),
@@ -292,6 +295,19 @@ def ebic_run_step(h, generations: int) -> dict:
     st = Stats()
     _check(lib().ebic_run_step(h, int(generations), ctypes.byref(st)))
     return st.as_dict()
+
+
+def ebic_run_step_async(h, generations: int, stream=None):
+    _check(lib().ebic_run_step_async(h, int(generations), _stream(stream)))
+
+
+KERNELS = ("k_spec", "k_build", "k_tabu_insert", "eval", "k_rank")
+
+
+def ebic_run_step_profiled(h) -> dict:
+    us = (ctypes.c_float * 5)()
+    _check(lib().ebic_run_step_profiled(h, us))
+    return dict(zip(KERNELS, list(us)))
 
 
 def _records(off, cols, n):

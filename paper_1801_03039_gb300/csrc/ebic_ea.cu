@@ -60,13 +60,11 @@ struct EaDev {
   unsigned long long* tkey;
   int32_t* tref;
   unsigned long long tmask;
-  // attempts of the current generation
-  int32_t* sp_ent;              // [J][8] entrants (first tournament, then second)
-  int32_t* sp_cross;            // [J]
-  uint16_t* sp_child;           // [J * ncombo][S]
-  int32_t* sp_clen;             // [J * ncombo]
-  unsigned long long* sp_hash;  // [J * ncombo]
-  int32_t* sp_tabu;             // [J * ncombo] child already in the tabu list
+  // attempts of the current generation: one record of rec_bytes per attempt
+  // (layout rec_layout), written by k_spec and streamed into k_build
+  char* rec;
+  int32_t rec_bytes;
+  int32_t pad2;
   // top-rank list (archive entries and their fitness), capacity T + P
   int32_t* list_ref;
   double* list_f;
@@ -78,6 +76,32 @@ struct EaDev {
 };
 
 constexpr int kMaxLen = EBIC_MAX_EA_LEN;
+
+// Layout of one attempt record (byte offsets; 8-byte fields first, size a
+// multiple of 16 so that records can be bulk-copied).  ne = 2k entrant slots
+// (first tournament, then second), nc = k * k candidate children (winner
+// positions ta * k + tb), S = series stride.
+struct RecLayout {
+  int chash, ef, ent, cross, elnf, eL, cL, ctabu, ecols, ccols, bytes;
+};
+
+__host__ __device__ inline RecLayout rec_layout(int k, int S, bool init) {
+  const int ne = init ? 0 : 2 * k, nc = init ? 1 : k * k;
+  RecLayout l{};
+  int o = 0;
+  l.chash = o; o += nc * 8;
+  l.ef = o;    o += ne * 8;
+  l.ent = o;   o += 8 * 4;
+  l.cross = o; o += 4;
+  l.elnf = o;  o += ne * 4;
+  l.eL = o;    o += ne * 4;
+  l.cL = o;    o += nc * 4;
+  l.ctabu = o; o += nc * 4;
+  l.ecols = o; o += ne * S * 2;
+  l.ccols = o; o += nc * S * 2;
+  l.bytes = (o + 15) & ~15;
+  return l;
+}
 
 // ---------------------------------------------------------------------------
 // Philox-4x32-10 (Salmon et al., SC'11): counter (j, g, block, 0), key = seed.
@@ -239,6 +263,8 @@ __global__ void __launch_bounds__(128) k_spec(EaDev d) {
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (tid >= (long long)d.J * nc) return;
   const int j = (int)(tid / nc), c = (int)(tid % nc);
+  const RecLayout l = rec_layout(d.k, d.S, INIT);
+  char* rec = d.rec + (size_t)j * d.rec_bytes;
   Draws r(d.seed, (uint32_t)g, (uint32_t)j);
   uint16_t x[kMaxLen];
   int L = 0;
@@ -251,12 +277,21 @@ __global__ void __launch_bounds__(128) k_spec(EaDev d) {
     const uint32_t P = (uint32_t)d.P;
     const int ta = c / k, tb = c % k;
     const bool cross = (double)r(k) * 0x1p-32 < d.pc;
-    if (c == 0) {
-      for (int t = 0; t < k; ++t) d.sp_ent[(size_t)j * 8 + t] = (int32_t)below(r(t), P);
-      for (int t = 0; t < k; ++t) d.sp_ent[(size_t)j * 8 + 4 + t] = (int32_t)below(r(k + 1 + t), P);
-      d.sp_cross[j] = cross ? 1 : 0;
-    }
     const long long prev = (long long)(g - 1) * d.P;
+    // entrant slots e = c, c + nc, ... of this attempt's record
+    for (int e = c; e < 2 * k; e += nc) {
+      const int idx = (int)below(r(e < k ? e : k + 1 + (e - k)), P);
+      const long long er = prev + idx;
+      const int eL = d.len[er];
+      reinterpret_cast<double*>(rec + l.ef)[e] = d.fit[er];
+      reinterpret_cast<float*>(rec + l.elnf)[e] = d.lnf[er];
+      reinterpret_cast<int32_t*>(rec + l.eL)[e] = eL;
+      reinterpret_cast<int32_t*>(rec + l.ent)[e < k ? e : 4 + (e - k)] = idx;
+      uint16_t* ec = reinterpret_cast<uint16_t*>(rec + l.ecols) + (size_t)e * d.S;
+      const uint16_t* src = d.seq + (size_t)er * d.S;
+      for (int i = 0; i < eL; ++i) ec[i] = src[i];
+    }
+    if (c == 0) reinterpret_cast<int32_t*>(rec + l.cross)[0] = cross ? 1 : 0;
     const int ia = (int)below(r(ta), P);
     const uint16_t* a = d.seq + (size_t)(prev + ia) * d.S;
     const int La = d.len[prev + ia];
@@ -282,12 +317,12 @@ __global__ void __launch_bounds__(128) k_spec(EaDev d) {
     }
     mutate(x, L, d.C, d.Lmin, d.Lmax, r(2 * k + 3), r(2 * k + 4), r(2 * k + 5));
   }
-  uint16_t* out = d.sp_child + (size_t)tid * d.S;
+  uint16_t* out = reinterpret_cast<uint16_t*>(rec + l.ccols) + (size_t)c * d.S;
   for (int i = 0; i < L; ++i) out[i] = x[i];
-  d.sp_clen[tid] = L;
+  reinterpret_cast<int32_t*>(rec + l.cL)[c] = L;
   const unsigned long long h = seq_hash(x, L);
-  d.sp_hash[tid] = h;
-  d.sp_tabu[tid] = INIT ? 0 : (tabu_contains(d, h, x, L) ? 1 : 0);
+  reinterpret_cast<unsigned long long*>(rec + l.chash)[c] = h;
+  reinterpret_cast<int32_t*>(rec + l.ctabu)[c] = INIT ? 0 : (tabu_contains(d, h, x, L) ? 1 : 0);
 }
 
 // ---------------------------------------------------------------------------
@@ -300,188 +335,532 @@ __global__ void __launch_bounds__(128) k_spec(EaDev d) {
 // value might be zero, subnormal or infinite -- compute the binary64 values
 // with the host-built power table and compare them exactly.
 // ---------------------------------------------------------------------------
+// One tournament entrant as the builder sees it.  f = 0 exactly when
+// lnf = -inf (lnf is log(f) rounded to float, finite for every f > 0), so the
+// fast path needs no binary64 arithmetic; f itself is read only on the exact
+// path.
 struct Entrant {
-  double f;
   float lnf;
   int32_t S, L, idx;
+  const double* f;   // the entrant's binary64 fitness (shared memory)
 };
 
-__device__ __forceinline__ bool beats(const Entrant& x, const Entrant& y, const EaDev& d,
-                                      const float* cL, long long& exact) {
-  if (x.idx == y.idx) return false;
-  if (x.f == 0.0 && y.f == 0.0) return x.idx < y.idx;
+// Bit 0 of the result: x beats y.  Bit 1: the exact path decided.
+__device__ __forceinline__ int beats(const Entrant& x, const Entrant& y, const EaDev& d,
+                                     const float* cL) {
+  if (x.idx == y.idx) return 0;
+  const bool zx = x.lnf == -INFINITY, zy = y.lnf == -INFINITY;
+  if (zx && zy) return x.idx < y.idx ? 1 : 0;
   const float cx = (float)x.S * cL[x.L];
   const float cy = (float)y.S * cL[y.L];
-  const bool safe_x = x.f == 0.0 || (cx < 700.f && x.lnf - cx > -700.f);
-  const bool safe_y = y.f == 0.0 || (cy < 700.f && y.lnf - cy > -700.f);
+  const bool safe_x = zx || (cx < 700.f && x.lnf - cx > -700.f);
+  const bool safe_y = zy || (cy < 700.f && y.lnf - cy > -700.f);
   if (safe_x && safe_y) {
-    if (x.f == 0.0) return false;
-    if (y.f == 0.0) return true;
+    if (zx) return 0;
+    if (zy) return 1;
     const float gx = x.lnf - cx, gy = y.lnf - cy;
     const float margin = 0x1p-16f * (fabsf(x.lnf) + fabsf(y.lnf) + cx + cy + 1.f);
-    if (gx - gy > margin) return true;
-    if (gy - gx > margin) return false;
+    if (gx - gy > margin) return 1;
+    if (gy - gx > margin) return 0;
   }
-  ++exact;
-  const double px = __ddiv_rn(x.f, d.pow_tab[d.pow_off[x.L] + x.S]);
-  const double py = __ddiv_rn(y.f, d.pow_tab[d.pow_off[y.L] + y.S]);
-  return px > py || (px == py && x.idx < y.idx);
+  const double px = __ddiv_rn(*x.f, d.pow_tab[d.pow_off[x.L] + x.S]);
+  const double py = __ddiv_rn(*y.f, d.pow_tab[d.pow_off[y.L] + y.S]);
+  return 2 | ((px > py || (px == py && x.idx < y.idx)) ? 1 : 0);
 }
 
-// Warp-cooperative tournament over entrants ent[0 .. k) of the previous
-// population; every lane returns the winner's position in ent.
-__device__ int tournament(const EaDev& d, const int32_t* ent, int k, const uint32_t* pen,
-                          const float* cL, long long prev, int lane, long long& exact) {
-  Entrant best{}, cur{};
+// Winner position of one tournament (entrant slots e0 .. e0 + k - 1 of the
+// record; identities ent[0 .. k)), lane-local.  Returns the position of the
+// first entrant with the winning identity; *exact counts exact decisions.
+__device__ __forceinline__ int tournament_lane(const EaDev& d, const float* cL, int k, int e0,
+                                               const int32_t* ent, const float* elnf,
+                                               const int32_t* eL, const double* ef,
+                                               const uint16_t* ecols, int S,
+                                               const uint32_t* pen, int* exact) {
+  Entrant best;
   int best_t = 0;
   for (int t = 0; t < k; ++t) {
-    const int i = ent[t];
-    const long long e = prev + i;
-    const int L = d.len[e];
-    const uint16_t* s = d.seq + (size_t)e * d.S;
-    uint32_t part = 0;
-    for (int c = lane; c < L; c += 32) part += pen[s[c]];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    cur.f = d.fit[e];
-    cur.lnf = d.lnf[e];
-    cur.S = (int32_t)part;
-    cur.L = L;
-    cur.idx = i;
-    if (t == 0 || beats(cur, best, d, cL, exact)) {
-      best = cur;
+    const int e = e0 + t;
+    Entrant x;
+    x.lnf = elnf[e];
+    x.L = eL[e];
+    x.idx = ent[t];
+    x.f = ef + e;
+    const uint16_t* cs = ecols + (size_t)e * S;
+    uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+    int c = 0;
+    for (; c + 4 <= x.L; c += 4) {
+      s0 += pen[cs[c]];
+      s1 += pen[cs[c + 1]];
+      s2 += pen[cs[c + 2]];
+      s3 += pen[cs[c + 3]];
+    }
+    for (; c < x.L; ++c) s0 += pen[cs[c]];
+    x.S = (int32_t)(s0 + s1 + s2 + s3);
+    if (t == 0) {
+      best = x;
+      continue;
+    }
+    const int r = beats(x, best, d, cL);
+    *exact += r >> 1;
+    if (r & 1) {
+      best = x;
       best_t = t;
     }
   }
-  // position of the first entrant with the winning index (the child table is
-  // indexed by position; equal indices give equal children)
   for (int t = 0; t < best_t; ++t)
     if (ent[t] == best.idx) return t;
   return best_t;
 }
 
-// Within-generation set of accepted children (shared memory, open addressing).
-__device__ bool wset_contains(const unsigned long long* hk, const int32_t* hr, int hmask,
-                              unsigned long long key, const uint16_t* s, int L, const EaDev& d) {
-  int i = (int)(key & (unsigned long long)hmask);
-  for (int n = 0; n <= hmask; ++n) {
-    const unsigned long long k = hk[i];
-    if (k == 0ull) return false;
-    if (k == key) {
-      const int32_t r = hr[i];
-      if (same_series(d.seq + (size_t)r * d.S, d.len[r], s, L)) return true;
+
+// Lane-local tournament decisions for tournament size K (1 or 2): entrant
+// slots 0 .. K - 1 form the first tournament, K .. 2K - 1 the second (when the
+// attempt crosses over).  Returns the child index ta * K + tb; *nex counts
+// exact-path comparisons.
+template <int K>
+__device__ __forceinline__ int decide_small(const EaDev& d, const float* cL, int cr,
+                                            const float (&ln)[4], const int32_t (&Sx)[4],
+                                            const int32_t (&Lx)[4], const int32_t (&id)[4],
+                                            const double* ef, int* nex) {
+  int ta = 0, tb = 0;
+  if (K == 2) {
+    {
+      const Entrant x{ln[1], Sx[1], Lx[1], id[1], ef + 1};
+      const Entrant y{ln[0], Sx[0], Lx[0], id[0], ef + 0};
+      const int r = beats(x, y, d, cL);
+      *nex += r >> 1;
+      if ((r & 1) && id[1] != id[0]) ta = 1;
     }
-    i = (i + 1) & hmask;
+    if (cr) {
+      const Entrant x{ln[3], Sx[3], Lx[3], id[3], ef + 3};
+      const Entrant y{ln[2], Sx[2], Lx[2], id[2], ef + 2};
+      const int r = beats(x, y, d, cL);
+      *nex += r >> 1;
+      if ((r & 1) && id[3] != id[2]) tb = 1;
+    }
+  }
+  return ta * K + tb;
+}
+
+// ---------------------------------------------------------------------------
+// k_build: Steps 2-3 (or the acceptance part of Step 1).  The decisions are
+// sequential (each tournament sees the penalty counts left by every earlier
+// acceptance), so warp 0 makes them from shared memory only.  The attempt
+// records (written by k_spec) are streamed in chunks of kB with TMA bulk
+// copies into a double buffer completed through mbarriers, issued by thread 0
+// two chunks ahead.  Every wait is bounded: on expiry the kernel records
+// stop reason 4, drains its own copies in flight and returns.
+// Accepted children go to the archive, copied by all warps at the end.
+//
+// Shared memory: hkey[H] (u64) | href[H] | acc[P] | pen[C] | cLf[Lmax + 1] |
+//                2 record buffers of kB records (128-byte aligned).
+// ---------------------------------------------------------------------------
+constexpr int kBuildThreads = 128;
+constexpr long long kMaxSpin = 1ll << 22;   // bounded mbarrier polling
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
+                                          unsigned long long* bar) {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Waits for phase `parity` of the barrier to complete; false after kMaxSpin polls.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
+  for (long long it = 0; it < kMaxSpin; ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
   }
   return false;
 }
 
-__device__ void wset_insert(unsigned long long* hk, int32_t* hr, int hmask, unsigned long long key,
-                            int32_t ref) {
-  int i = (int)(key & (unsigned long long)hmask);
-  for (int n = 0; n <= hmask; ++n) {
-    if (hk[i] == 0ull) {
-      hk[i] = key;
-      hr[i] = ref;
-      return;
-    }
-    i = (i + 1) & hmask;
-  }
-}
-
-// ---------------------------------------------------------------------------
-// k_build: Steps 2-3 (or the acceptance part of Step 1), one warp.
-// Shared memory: pen[C] | hkey[H] | href[H] | cL[Lmax + 1].
-// ---------------------------------------------------------------------------
 template <bool INIT>
-__global__ void __launch_bounds__(32) k_build(EaDev d, int hmask) {
-  extern __shared__ unsigned long long smem_u64[];
+__global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int kB) {
+  extern __shared__ __align__(128) unsigned long long smem_u64[];
   if (*(volatile int32_t*)&d.ctl->stop) return;
-  const int lane = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = d.ctl->gen;
-  const int H = hmask + 1;
+  const int H = hmask + 1, k = d.k, nc = INIT ? 1 : k * k, S = d.S;
+  const RecLayout l = rec_layout(k, S, INIT);
+  const int RB = d.rec_bytes;
   unsigned long long* hkey = smem_u64;
   int32_t* href = reinterpret_cast<int32_t*>(hkey + H);
-  uint32_t* pen = reinterpret_cast<uint32_t*>(href + H);
-  float* cL = reinterpret_cast<float*>(pen + d.C);
-  for (int i = lane; i < H; i += 32) hkey[i] = 0ull;
-  for (int i = lane; i < d.C; i += 32) pen[i] = 0u;
-  for (int i = lane; i <= d.Lmax; i += 32) cL[i] = d.c_over_L[i];
-  __syncwarp();
-  const long long base = (long long)g * d.P;
-  const long long prev = base - d.P;
-  int n = 0, E = 0;
-  if (!INIT) {
-    // Step 2: the best ceil(elite_frac * |list|) records, penalty counts raised.
-    E = (int)ceil(d.elite_frac * (double)d.ctl->n_top);
-    if (E > d.P) E = d.P;
-    for (int e = 0; e < E; ++e) {
-      const int32_t src = d.list_ref[e];
-      const int L = d.len[src];
-      const uint16_t* s = d.seq + (size_t)src * d.S;
-      uint16_t* o = d.seq + (size_t)(base + e) * d.S;
-      for (int c = lane; c < L; c += 32) {
-        o[c] = s[c];
-        pen[s[c]] += 1u;
-      }
-      if (lane == 0) d.len[base + e] = L;
-      __syncwarp();
-    }
-    n = E;
+  int32_t* acc = href + H;                                 // accepted record per new slot
+  uint32_t* pen = reinterpret_cast<uint32_t*>(acc + d.P);
+  float* cLf = reinterpret_cast<float*>(pen + d.C);
+  char* buf0 = reinterpret_cast<char*>(
+      (reinterpret_cast<uintptr_t>(cLf + d.Lmax + 1) + 127) & ~(uintptr_t)127);
+  char* bufs[2] = {buf0, buf0 + (size_t)kB * RB};
+  __shared__ __align__(8) unsigned long long bars[2];
+  __shared__ int s_n, s_done, s_E, s_fail;
+  __shared__ uint32_t cbits[8];          // columns of the child just accepted (fast path)
+  // fast path: tournaments of at most 2 entrants, column sets of at most 256 bits
+  const bool fast = d.k <= 2 && d.WC <= 8;
+
+  const int nchunks = (d.J + kB - 1) / kB;
+  if (tid == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    s_fail = 0;
   }
-  int hits = 0, stopped = 0;
+  __syncthreads();
+  int issued = 0;                       // chunks whose copy thread 0 has issued
+  if (tid == 0) {
+    for (; issued < 2 && issued < nchunks; ++issued) {
+      const int j0 = issued * kB, cnt = min(kB, d.J - j0);
+      bulk_load(bufs[issued & 1], d.rec + (size_t)j0 * RB, (uint32_t)cnt * RB, &bars[issued & 1]);
+    }
+  }
+  for (int i = tid; i < H; i += kBuildThreads) hkey[i] = 0ull;
+  for (int i = tid; i < d.C; i += kBuildThreads) pen[i] = 0u;
+  for (int i = tid; i <= d.Lmax; i += kBuildThreads) cLf[i] = d.c_over_L[i];
+  if (tid < 8) cbits[tid] = 0u;
+  const long long base = (long long)g * d.P;
+  if (tid == 0) {
+    int E = 0;
+    if (!INIT) {
+      E = (int)ceil(d.elite_frac * (double)d.ctl->n_top);
+      if (E > d.P) E = d.P;
+    }
+    s_E = E;
+    s_done = 0;
+  }
+  __syncthreads();
+  const int E = s_E;
+  // Step 2: elites copied in order, each column use counted.
+  for (int i = tid; i < E * S; i += kBuildThreads) {
+    const int e = i / S, c = i % S;
+    const int32_t src = d.list_ref[e];
+    const int L = d.len[src];
+    if (c < L) {
+      const uint16_t v = d.seq[(size_t)src * S + c];
+      d.seq[(size_t)(base + e) * S + c] = v;
+      atomicAdd(&pen[v], 1u);
+    }
+    if (c == 0) d.len[base + e] = L;
+  }
+  __syncthreads();
+
+  int n = E, hits = 0, stopped = 0;
   long long attempts = 0, exact = 0;
-  const int nc = INIT ? 1 : d.ncombo;
-  for (int j = 0; n < d.P; ++j) {
-    if (j >= d.J) {
-      stopped = 3;
+  int chunk = 0;
+  for (; chunk < nchunks; ++chunk) {
+    char* cur = bufs[chunk & 1];
+    if (warp == 0) {
+      const bool ok = mbar_wait(&bars[chunk & 1], (uint32_t)((chunk >> 1) & 1));
+      const int cnt = min(kB, d.J - chunk * kB);
+      if (!ok) {
+        stopped = 4;
+      } else if (!INIT && fast) {
+        // ---- speculative sub-chunks of 32 attempts, one per lane ----
+        for (int sb = 0; sb < cnt && n < d.P && !stopped; sb += 32) {
+          const int a = sb + lane;
+          const bool have = a < cnt;
+          const char* ra = cur + (size_t)(have ? a : sb) * RB;
+          const int cr = have ? *reinterpret_cast<const int32_t*>(ra + l.cross) : 0;
+          const int nE = have ? (cr ? 2 * k : k) : 0;
+          const double* efa = reinterpret_cast<const double*>(ra + l.ef);
+          float ln[4];
+          int32_t Sx[4], Lx[4], id[4];
+          uint32_t bits[4][8];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            ln[e] = 0.f;
+            Sx[e] = Lx[e] = id[e] = 0;
+#pragma unroll
+            for (int w = 0; w < 8; ++w) bits[e][w] = 0u;
+            if (e < nE) {
+              ln[e] = reinterpret_cast<const float*>(ra + l.elnf)[e];
+              Lx[e] = reinterpret_cast<const int32_t*>(ra + l.eL)[e];
+              id[e] = reinterpret_cast<const int32_t*>(ra + l.ent)[e < k ? e : 4 + (e - k)];
+              const uint16_t* cs = reinterpret_cast<const uint16_t*>(ra + l.ecols) + (size_t)e * S;
+              uint32_t sum = 0;
+              for (int c = 0; c < Lx[e]; ++c) {
+                const uint32_t col = cs[c];
+                sum += pen[col];
+#pragma unroll
+                for (int w = 0; w < 8; ++w)
+                  if ((int)(col >> 5) == w) bits[e][w] |= 1u << (col & 31);
+              }
+              Sx[e] = (int32_t)sum;
+            }
+          }
+          int my_nex = 0;
+          int dec = have ? (k == 2 ? decide_small<2>(d, cLf, cr, ln, Sx, Lx, id, efa, &my_nex)
+                                   : decide_small<1>(d, cLf, cr, ln, Sx, Lx, id, efa, &my_nex))
+                         : 0;
+          bool dirty = false;
+          for (int b = 0; b < 32 && sb + b < cnt; ++b) {
+            if (n >= d.P) break;
+            if (lane == b && dirty) {
+              my_nex = 0;
+              dec = k == 2 ? decide_small<2>(d, cLf, cr, ln, Sx, Lx, id, efa, &my_nex)
+                           : decide_small<1>(d, cLf, cr, ln, Sx, Lx, id, efa, &my_nex);
+            }
+            const int combo = __shfl_sync(0xffffffffu, dec, b);
+            exact += __shfl_sync(0xffffffffu, my_nex, b);
+            const char* rb = cur + (size_t)(sb + b) * RB;
+            const int j = chunk * kB + sb + b;
+            ++attempts;
+            const int L = reinterpret_cast<const int32_t*>(rb + l.cL)[combo];
+            const unsigned long long key = reinterpret_cast<const unsigned long long*>(rb + l.chash)[combo];
+            const uint16_t* child = reinterpret_cast<const uint16_t*>(rb + l.ccols) + (size_t)combo * S;
+            bool dup = reinterpret_cast<const int32_t*>(rb + l.ctabu)[combo] != 0;
+            int slot = (int)(key & (unsigned long long)hmask);
+            if (!dup) {
+              for (int probe = 0; probe <= hmask; ++probe) {
+                const unsigned long long kk = hkey[slot];
+                if (kk == 0ull) break;
+                if (kk == key) {
+                  const int32_t r = href[slot];
+                  const char* orec = d.rec + (size_t)(r / nc) * RB;
+                  const int oc = r % nc;
+                  const uint16_t* other = reinterpret_cast<const uint16_t*>(orec + l.ccols) + (size_t)oc * S;
+                  const int oL = reinterpret_cast<const int32_t*>(orec + l.cL)[oc];
+                  const bool same =
+                      oL == L &&
+                      __all_sync(0xffffffffu, lane >= L || other[lane] == child[lane]) &&
+                      __all_sync(0xffffffffu, lane + 32 >= L || other[lane + 32] == child[lane + 32]);
+                  if (same) {
+                    dup = true;
+                    break;
+                  }
+                }
+                slot = (slot + 1) & hmask;
+              }
+            }
+            if (dup) {
+              if (++hits > d.P) {
+                stopped = 1;
+                break;
+              }
+              continue;
+            }
+            // accept: penalty counts, child bitset, hash set, slot
+            const int c0 = lane < L ? child[lane] : 0;
+            const int c1 = lane + 32 < L ? child[lane + 32] : 0;
+            if (lane < L) {
+              pen[c0] += 1u;
+              atomicOr(&cbits[c0 >> 5], 1u << (c0 & 31));
+            }
+            if (lane + 32 < L) {
+              pen[c1] += 1u;
+              atomicOr(&cbits[c1 >> 5], 1u << (c1 & 31));
+            }
+            if (lane == 0) {
+              hkey[slot] = key;
+              href[slot] = (int32_t)(j * nc + combo);
+              acc[n] = (int32_t)(j * nc + combo);
+            }
+            __syncwarp();
+            // later attempts of this sub-chunk: penalty sums += overlap
+            if (lane > b && have) {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                if (e < nE) {
+                  uint32_t inter = 0;
+#pragma unroll
+                  for (int w = 0; w < 8; ++w) inter += __popc(bits[e][w] & cbits[w]);
+                  if (inter) {
+                    Sx[e] += (int32_t)inter;
+                    dirty = true;
+                  }
+                }
+              }
+            }
+            __syncwarp();
+            if (lane < L) cbits[c0 >> 5] = 0u;
+            if (lane + 32 < L) cbits[c1 >> 5] = 0u;
+            __syncwarp();
+            ++n;
+          }
+        }
+      } else {
+        for (int a = 0; a < kB && n < d.P; ++a) {
+          const int j = chunk * kB + a;
+          if (j >= d.J) {
+            stopped = 3;
+            break;
+          }
+          const char* rc = cur + (size_t)a * RB;
+          ++attempts;
+          int combo = 0;
+          if (!INIT) {
+            const int32_t* ent = reinterpret_cast<const int32_t*>(rc + l.ent);
+            const int cr = *reinterpret_cast<const int32_t*>(rc + l.cross);
+            const double* ef = reinterpret_cast<const double*>(rc + l.ef);
+            const float* elnf = reinterpret_cast<const float*>(rc + l.elnf);
+            const int32_t* eL = reinterpret_cast<const int32_t*>(rc + l.eL);
+            const uint16_t* ecols = reinterpret_cast<const uint16_t*>(rc + l.ecols);
+            const int nE = cr ? 2 * k : k;
+            // penalty sums: lanes 8q .. 8q + 7 sum entrant 4 * pass + q
+            uint32_t part0 = 0u, part1 = 0u;
+#pragma unroll
+            for (int pass = 0; pass < 2; ++pass) {
+              if (pass * 4 < nE) {
+                const int e = pass * 4 + (lane >> 3);
+                uint32_t v = 0;
+                if (e < nE) {
+                  const int L = eL[e];
+                  const uint16_t* cs = ecols + (size_t)e * S;
+                  for (int c = lane & 7; c < L; c += 8) v += pen[cs[c]];
+                }
+                v += __shfl_xor_sync(0xffffffffu, v, 4);
+                v += __shfl_xor_sync(0xffffffffu, v, 2);
+                v += __shfl_xor_sync(0xffffffffu, v, 1);
+                if (pass == 0) part0 = v;
+                else part1 = v;
+              }
+            }
+            // tournaments, computed alike on every lane from registers
+            int pos0 = 0, pos1 = 0, nex = 0;
+            for (int tour = 0; tour < (cr ? 2 : 1); ++tour) {
+              Entrant best, x;
+              int best_t = 0;
+              for (int t = 0; t < k; ++t) {
+                const int e = tour * k + t;
+                x.lnf = elnf[e];
+                x.S = (int32_t)__shfl_sync(0xffffffffu, e < 4 ? part0 : part1, (e & 3) * 8);
+                x.L = eL[e];
+                x.idx = ent[(tour ? 4 : 0) + t];
+                x.f = ef + e;
+                if (t == 0) {
+                  best = x;
+                } else {
+                  const int r = beats(x, best, d, cLf);
+                  nex += r >> 1;
+                  if (r & 1) {
+                    best = x;
+                    best_t = t;
+                  }
+                }
+              }
+              for (int t = 0; t < best_t; ++t)
+                if (ent[(tour ? 4 : 0) + t] == best.idx) {
+                  best_t = t;
+                  break;
+                }
+              if (tour == 0) pos0 = best_t;
+              else pos1 = best_t;
+            }
+            exact += nex;
+            combo = pos0 * k + pos1;
+          }
+          const int L = reinterpret_cast<const int32_t*>(rc + l.cL)[combo];
+          const unsigned long long key = reinterpret_cast<const unsigned long long*>(rc + l.chash)[combo];
+          const uint16_t* child = reinterpret_cast<const uint16_t*>(rc + l.ccols) + (size_t)combo * S;
+          bool dup = reinterpret_cast<const int32_t*>(rc + l.ctabu)[combo] != 0;
+          int slot = (int)(key & (unsigned long long)hmask);   // first empty slot after the probe
+          if (!dup) {
+            // within this generation: open addressing on the 64-bit hash; a
+            // hash match is confirmed on the columns of the earlier child
+            for (int probe = 0; probe <= hmask; ++probe) {
+              const unsigned long long kk = hkey[slot];
+              if (kk == 0ull) break;
+              if (kk == key) {
+                const int32_t r = href[slot];
+                const char* orec = d.rec + (size_t)(r / nc) * RB;
+                const int oc = r % nc;
+                const uint16_t* other = reinterpret_cast<const uint16_t*>(orec + l.ccols) + (size_t)oc * S;
+                const int oL = reinterpret_cast<const int32_t*>(orec + l.cL)[oc];
+                const bool same =
+                    oL == L &&
+                    __all_sync(0xffffffffu, lane >= L || other[lane] == child[lane]) &&
+                    __all_sync(0xffffffffu, lane + 32 >= L || other[lane + 32] == child[lane + 32]);
+                if (same) {
+                  dup = true;
+                  break;
+                }
+              }
+              slot = (slot + 1) & hmask;
+            }
+          }
+          if (dup) {
+            if (++hits > d.P) {
+              stopped = INIT ? 2 : 1;
+              break;
+            }
+            continue;
+          }
+          const int32_t rec_id = (int32_t)(j * nc + combo);
+          if (lane < L) pen[child[lane]] += 1u;
+          if (lane + 32 < L) pen[child[lane + 32]] += 1u;
+          if (lane == 0) {
+            hkey[slot] = key;
+            href[slot] = rec_id;
+            acc[n] = rec_id;
+          }
+          __syncwarp();
+          ++n;
+        }
+      }
+      if (lane == 0) {
+        s_n = n;
+        s_done = (n >= d.P || stopped) ? 1 : 0;
+        if (stopped == 4) s_fail = 1;
+      }
+    }
+    __syncthreads();            // the consumed buffer may now be refilled
+    if (s_done) {
+      ++chunk;
       break;
     }
-    ++attempts;
-    int combo = 0;
-    if (!INIT) {
-      int32_t ent[8];
-#pragma unroll
-      for (int t = 0; t < 8; ++t) ent[t] = d.sp_ent[(size_t)j * 8 + t];
-      const int ta = tournament(d, ent, d.k, pen, cL, prev, lane, exact);
-      int tb = 0;
-      if (d.sp_cross[j]) tb = tournament(d, ent + 4, d.k, pen, cL, prev, lane, exact);
-      combo = ta * d.k + tb;
+    if (tid == 0 && issued < nchunks) {
+      const int j0 = issued * kB, cnt = min(kB, d.J - j0);
+      bulk_load(bufs[issued & 1], d.rec + (size_t)j0 * RB, (uint32_t)cnt * RB, &bars[issued & 1]);
+      ++issued;
     }
-    const size_t rec = (size_t)j * nc + combo;
-    const int L = d.sp_clen[rec];
-    const unsigned long long key = d.sp_hash[rec];
-    const uint16_t* child = d.sp_child + rec * d.S;
-    bool dup = d.sp_tabu[rec] != 0;
-    if (!dup) dup = wset_contains(hkey, href, hmask, key, child, L, d);
-    __syncwarp();
-    if (dup) {
-      if (++hits > d.P) {
-        stopped = INIT ? 2 : 1;
-        break;
-      }
-      continue;
-    }
-    const long long dst = base + n;
-    uint16_t* o = d.seq + (size_t)dst * d.S;
-    for (int c = lane; c < L; c += 32) {
-      o[c] = child[c];
-      pen[child[c]] += 1u;
-    }
-    if (lane == 0) {
-      d.len[dst] = L;
-      wset_insert(hkey, href, hmask, key, (int32_t)dst);
-    }
-    __syncwarp();
-    ++n;
   }
-  if (lane == 0) {
+  // every attempt consumed without filling the population: cannot happen
+  // (2P + 1 attempts always suffice), reported as an internal error
+  if (tid == 0 && s_n < d.P && !s_done) s_fail = 2;
+  // drain: copies issued but not consumed must land before the CTA exits
+  if (tid == 0) {
+    for (int c = chunk; c < issued; ++c)
+      if (!mbar_wait(&bars[c & 1], (uint32_t)((c >> 1) & 1))) s_fail = 1;
+  }
+  __syncthreads();
+  n = s_n;
+  // accepted children into the archive, in acceptance order after the elites
+  for (int i = tid; i < (n - E) * S; i += kBuildThreads) {
+    const int slot = E + i / S, c = i % S;
+    const int32_t r = acc[slot];
+    const char* rec = d.rec + (size_t)(r / nc) * RB;
+    const int L = reinterpret_cast<const int32_t*>(rec + l.cL)[r % nc];
+    if (c < L) d.seq[(size_t)(base + slot) * S + c] =
+        reinterpret_cast<const uint16_t*>(rec + l.ccols)[(size_t)(r % nc) * S + c];
+    if (c == 0) d.len[base + slot] = L;
+  }
+  if (tid == 0) {
     Ctl* ctl = d.ctl;
     ctl->last_hits = hits;
     ctl->hits_total += hits;
     ctl->attempts_total += attempts;
     ctl->exact_total += exact;
     ctl->n_elite = E;
+    if (s_fail) stopped = s_fail == 2 ? 3 : 4;
     if (stopped) {
       ctl->stop_reason = stopped;
       __threadfence();
@@ -683,11 +1062,12 @@ __global__ void __launch_bounds__(kRankThreads) k_rank(EaDev d, int Pp) {
 // ---------------------------------------------------------------------------
 struct EaState {
   ebic_params_t p{};
-  int32_t S = 0, J = 0, ncombo = 0, WC = 0, Pp = 0, hmask = 0;
+  int32_t S = 0, J = 0, ncombo = 0, WC = 0, Pp = 0, hmask = 0, kB = 64;
   long long entries = 0;
   DevBuf seq, len, inc, dec, fit, lnf;
   DevBuf tkey, tref;
-  DevBuf sp_ent, sp_cross, sp_child, sp_clen, sp_hash, sp_tabu;
+  DevBuf rec;
+  int32_t rec_bytes = 0;
   DevBuf list_ref, list_f;
   DevBuf pow_tab, pow_off, c_over_L;
   DevBuf ctl, gather;
@@ -698,6 +1078,7 @@ struct EaState {
   EaDev dev{};
   ArchivePop apop{};
   EvalArgs eargs{};
+  ebic_eval_tuning_t tuning{};   // evaluation shape chosen at Step 1
   bool initialised = false;
 
   void release() {
@@ -705,9 +1086,8 @@ struct EaState {
     if (graph) cudaGraphDestroy(graph);
     exec = nullptr;
     graph = nullptr;
-    for (DevBuf* b : {&seq, &len, &inc, &dec, &fit, &lnf, &tkey, &tref, &sp_ent, &sp_cross,
-                      &sp_child, &sp_clen, &sp_hash, &sp_tabu, &list_ref, &list_f, &pow_tab,
-                      &pow_off, &c_over_L, &ctl, &gather})
+    for (DevBuf* b : {&seq, &len, &inc, &dec, &fit, &lnf, &tkey, &tref, &rec, &list_ref,
+                      &list_f, &pow_tab, &pow_off, &c_over_L, &ctl, &gather})
       b->release();
     h_ctl.release();
     h_gather.release();
@@ -754,10 +1134,10 @@ static ebic_status launch_generation(ebic_ctx* h, EaState* st, bool init, cudaSt
   const unsigned sblocks = (unsigned)((threads + 127) / 128);
   if (init) {
     k_spec<true><<<sblocks, 128, 0, s>>>(d);
-    k_build<true><<<1, 32, st->smem_build, s>>>(d, st->hmask);
+    k_build<true><<<1, kBuildThreads, st->smem_build, s>>>(d, st->hmask, st->kB);
   } else {
     k_spec<false><<<sblocks, 128, 0, s>>>(d);
-    k_build<false><<<1, 32, st->smem_build, s>>>(d, st->hmask);
+    k_build<false><<<1, kBuildThreads, st->smem_build, s>>>(d, st->hmask, st->kB);
   }
   k_tabu_insert<<<(unsigned)((st->p.pop_size + 255) / 256), 256, 0, s>>>(d);
   EBIC_CUDA_TRY(cudaGetLastError());
@@ -817,13 +1197,9 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
   EBIC_TRY(st->tref.reserve(tcap * sizeof(int32_t)));
   EBIC_CUDA_TRY(cudaMemsetAsync(st->tkey.ptr, 0, tcap * sizeof(unsigned long long), s));
   EBIC_CUDA_TRY(cudaMemsetAsync(st->dec.ptr, 0, E * sizeof(uint32_t), s));
-  const size_t nrec = (size_t)st->J * st->ncombo;
-  EBIC_TRY(st->sp_ent.reserve((size_t)st->J * 8 * sizeof(int32_t)));
-  EBIC_TRY(st->sp_cross.reserve((size_t)st->J * sizeof(int32_t)));
-  EBIC_TRY(st->sp_child.reserve(nrec * st->S * sizeof(uint16_t)));
-  EBIC_TRY(st->sp_clen.reserve(nrec * sizeof(int32_t)));
-  EBIC_TRY(st->sp_hash.reserve(nrec * sizeof(unsigned long long)));
-  EBIC_TRY(st->sp_tabu.reserve(nrec * sizeof(int32_t)));
+  // attempt records: sized for the larger (Steps 2-5) layout
+  st->rec_bytes = rec_layout(k, st->S, false).bytes;
+  EBIC_TRY(st->rec.reserve((size_t)st->J * st->rec_bytes));
   EBIC_TRY(st->list_ref.reserve((size_t)(T + P) * sizeof(int32_t)));
   EBIC_TRY(st->list_f.reserve((size_t)(T + P) * sizeof(double)));
   EBIC_TRY(st->ctl.reserve(sizeof(Ctl)));
@@ -877,12 +1253,8 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
   d.tkey = st->tkey.as<unsigned long long>();
   d.tref = st->tref.as<int32_t>();
   d.tmask = tcap - 1;
-  d.sp_ent = st->sp_ent.as<int32_t>();
-  d.sp_cross = st->sp_cross.as<int32_t>();
-  d.sp_child = st->sp_child.as<uint16_t>();
-  d.sp_clen = st->sp_clen.as<int32_t>();
-  d.sp_hash = st->sp_hash.as<unsigned long long>();
-  d.sp_tabu = st->sp_tabu.as<int32_t>();
+  d.rec = st->rec.as<char>();
+  d.rec_bytes = st->rec_bytes;
   d.list_ref = st->list_ref.as<int32_t>();
   d.list_f = st->list_f.as<double>();
   d.pow_tab = st->pow_tab.as<double>();
@@ -906,8 +1278,13 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
   a.fit = d.fit;
   a.lnf = d.lnf;
 
-  st->smem_build = (size_t)H * (sizeof(unsigned long long) + sizeof(int32_t)) +
-                   (size_t)h->C * sizeof(uint32_t) + (size_t)(p->len_max + 1) * sizeof(float);
+  // build: wset + accepted + pen + cL, then two record buffers of kB attempts
+  const size_t fixed = (size_t)H * (sizeof(unsigned long long) + sizeof(int32_t)) +
+                       (size_t)P * sizeof(int32_t) + (size_t)h->C * sizeof(uint32_t) +
+                       (size_t)(p->len_max + 2) * sizeof(float) + 128;
+  st->kB = 64;
+  while (st->kB > 2 && fixed + 2 * (size_t)st->kB * st->rec_bytes > 200 * 1024) st->kB >>= 1;
+  st->smem_build = fixed + 2 * (size_t)st->kB * st->rec_bytes;
   const size_t cap = (size_t)T + P;
   st->smem_rank = (size_t)st->Pp * (sizeof(unsigned long long) + sizeof(int32_t)) +
                   cap * (2 * sizeof(double) + 2 * sizeof(int32_t)) + ((cap + 15) & ~(size_t)15) +
@@ -934,7 +1311,7 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
   const EaDev& dd = st->dev;
   const unsigned sblocks = (unsigned)((st->J + 127) / 128);
   k_spec<true><<<sblocks, 128, 0, s>>>(dd);
-  k_build<true><<<1, 32, st->smem_build, s>>>(dd, st->hmask);
+  k_build<true><<<1, kBuildThreads, st->smem_build, s>>>(dd, st->hmask, st->kB);
   k_tabu_insert<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(dd);
   count_launches(3);
   EBIC_CUDA_TRY(cudaGetLastError());
@@ -950,6 +1327,7 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
   EBIC_CUDA_TRY(cudaGetLastError());
 
   // One generation (Steps 2-5) captured as a graph for replay.
+  st->tuning = h->tuning;
   EBIC_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   ebic_status cap_st = launch_generation(h, st, false, s);
   cudaGraph_t graph = nullptr;
@@ -1007,6 +1385,52 @@ __global__ void __launch_bounds__(256) k_gather(EaDev d, const int32_t* refs, lo
   o_inc[i] = inc[r];
   o_dec[i] = dec[r];
   o_fit[i] = d.fit[r];
+}
+
+// Steps 2-5 replayed on the caller's stream without waiting or reading back.
+static ebic_status run_step_async(ebic_ctx* h, int32_t generations, cudaStream_t s) {
+  EaState* st = h->ea;
+  if (!st || !st->initialised) return fail(EBIC_ERR_STATE, "ebic_run_init has not run");
+  if (generations < 0) return fail(EBIC_ERR_ARG, "negative generation count");
+  for (int32_t i = 0; i < generations; ++i) EBIC_CUDA_TRY(cudaGraphLaunch(st->exec, s));
+  count_launches((uint64_t)generations * 5);
+  return EBIC_OK;
+}
+
+// One generation as five separate launches with events between them.
+static ebic_status run_step_profiled(ebic_ctx* h, float* us) {
+  EaState* st = h->ea;
+  if (!st || !st->initialised) return fail(EBIC_ERR_STATE, "ebic_run_init has not run");
+  const cudaStream_t s = h->stream;
+  cudaEvent_t ev[6];
+  for (int i = 0; i < 6; ++i) EBIC_CUDA_TRY(cudaEventCreate(&ev[i]));
+  const EaDev& d = st->dev;
+  const long long threads = (long long)st->J * st->ncombo;
+  cudaEventRecord(ev[0], s);
+  k_spec<false><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(d);
+  cudaEventRecord(ev[1], s);
+  k_build<false><<<1, kBuildThreads, st->smem_build, s>>>(d, st->hmask, st->kB);
+  cudaEventRecord(ev[2], s);
+  k_tabu_insert<<<(unsigned)((st->p.pop_size + 255) / 256), 256, 0, s>>>(d);
+  cudaEventRecord(ev[3], s);
+  const ebic_eval_tuning_t user = h->tuning;
+  h->tuning = st->tuning;
+  ebic_status es = eval_archive(h, st->apop, st->eargs, s);
+  h->tuning = user;
+  cudaEventRecord(ev[4], s);
+  k_rank<<<1, kRankThreads, st->smem_rank, s>>>(d, st->Pp);
+  cudaEventRecord(ev[5], s);
+  count_launches(4);
+  cudaError_t e = cudaEventSynchronize(ev[5]);
+  for (int i = 0; i < 5 && us; ++i) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+    us[i] = ms * 1000.f;
+  }
+  for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+  EBIC_TRY(es);
+  EBIC_CUDA_TRY(e);
+  return EBIC_OK;
 }
 
 static ebic_status get_records(ebic_ctx* h, bool toprank, int32_t* offsets, int32_t* cols,
@@ -1096,6 +1520,16 @@ ebic_status ebic_run_init(ebic_handle h, const ebic_params_t* p) {
 ebic_status ebic_run_step(ebic_handle h, int32_t generations, ebic_stats_t* stats) {
   if (!h) return fail(EBIC_ERR_ARG, "null handle");
   return run_step(h, generations, stats);
+}
+
+ebic_status ebic_run_step_async(ebic_handle h, int32_t generations, void* stream) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  return run_step_async(h, generations, static_cast<cudaStream_t>(stream));
+}
+
+ebic_status ebic_run_step_profiled(ebic_handle h, float* kernel_us) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  return run_step_profiled(h, kernel_us);
 }
 
 ebic_status ebic_get_toprank(ebic_handle h, int32_t* offsets, int32_t* cols, double* fitness,
