@@ -399,7 +399,9 @@ def run_ours(args, ws, rank, local):
     if gens:
         out["generations_per_s"] = ws * args.steps / slowest
     out.update(extra)
+    extra["sm_mhz"] = clk.get("sm_mhz") if clk else None
     out["roofline"] = roofline(wl, gens, extra, per_step_ms, peaks)
+    out.pop("sm_mhz", None)
     out["clocks"] = clk
     if ws == 1:
         out["cpu_baseline"] = cpu_baseline(wl, budget_s=12.0)
@@ -418,7 +420,32 @@ def roofline(wl, gens, extra, per_step_ms, peaks):
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})"}
     kern = extra["kernel_us"]
     dom = max(kern, key=kern.get)
-    return {"dominant_kernel": dom, "kernel_us": kern, "note": "see DESIGN.md"}
+    if dom != "k_build":
+        return {"dominant_kernel": dom, "kernel_us": kern}
+    # The Step 3 builder is sequential: one warp decides attempt after attempt.
+    # Its bound is that warp's issue rate: one warp-instruction per cycle at
+    # the SM clock.  Work per launch = the kernel's warp-instructions (ncu
+    # count committed under profiles/ for this kernel build).
+    prof = read_profile("k_build-generations-paper-1000x100.json")
+    inst = prof.get("smsp__inst_executed.sum") if prof else None
+    mhz = (extra.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0)
+    peak = mhz * 1e6 / 1e9                       # G warp-instructions / s
+    dur = kern["k_build"] * 1e-6
+    achieved = inst / dur / 1e9 if inst else None
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G warp-inst/s",
+            "frac": achieved / peak if achieved else None,
+            "traffic": prof.get("dram_bytes_per_launch") if prof else None,
+            "kernel": "k_build (Step 3 builder, one CTA, one deciding warp)",
+            "work_per_launch": inst, "work_def": "warp-instructions per launch (ncu)",
+            "peak_source": "1 warp-instruction/cycle x median SM clock sampled in this run",
+            "kernel_us": kern}
+
+
+def read_profile(name: str):
+    try:
+        return json.load(open(os.path.join(ROOT, "profiles", name)))
+    except (OSError, ValueError):
+        return None
 
 
 def read_traffic(workload: str):

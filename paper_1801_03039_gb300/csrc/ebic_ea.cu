@@ -1367,6 +1367,8 @@ static ebic_status run_step(ebic_ctx* h, int32_t generations, ebic_stats_t* stat
   EBIC_TRY(read_ctl(st, s, &c));
   fill_stats(c, stats);
   if (c.stop_reason == 3) return fail(EBIC_ERR_DEVICE, "internal EA error (code 3)");
+  if (c.stop_reason == 4)
+    return fail(EBIC_ERR_TIMEOUT, "a bounded wait for streamed attempt records expired");
   return EBIC_OK;
 }
 
