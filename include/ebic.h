@@ -210,6 +210,49 @@ ebic_status ebic_eval_population_dev_noalloc(ebic_handle h, const int32_t* d_off
                                              double* d_fitness, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Many problems in one launch (Step 4 repeated over independent problems, e.g.
+ * restarts or datasets side by side).  A batch binds n (handle, population)
+ * pairs; ebic_batch_eval then evaluates all of them -- rising support and
+ * Eq. (1) fitness, exactly as ebic_eval_population_dev with
+ * EBIC_SUPPORT_INC -- in one persistent launch that pulls (problem, series,
+ * part) work items longest-first.  All handles must be on one device.
+ * Flags:
+ *   EBIC_BATCH_BUILD_TABLES  build each problem's pair table if it fits in
+ *                            half the free device memory (cumulative);
+ *   EBIC_BATCH_AUTOTUNE      time the gather and bitmask paths and a few part
+ *                            sizes per problem (on the problem's own
+ *                            population, writing its outputs) and keep the
+ *                            fastest; otherwise bitmask where the table
+ *                            exists, whole series per warp;
+ *   EBIC_BATCH_GRAPH         capture the launch as a CUDA graph on the first
+ *                            ebic_batch_eval and replay it afterwards.
+ * The item buffers are caller-owned and must stay valid while the batch
+ * exists.  ebic_batch_create synchronises `stream` and reads the offsets. */
+typedef struct ebic_batch_ctx* ebic_batch;
+typedef struct {
+  const int32_t* d_offsets;  /* device, P + 1 entries */
+  const int32_t* d_cols;     /* device, total_cols entries */
+  int32_t P;
+  int32_t total_cols;
+  int32_t sigma;
+  uint32_t* d_inc;           /* device, P entries (output) */
+  double* d_fitness;         /* device, P entries (output) */
+} ebic_batch_item_t;
+#define EBIC_BATCH_AUTOTUNE 1
+#define EBIC_BATCH_GRAPH 2
+#define EBIC_BATCH_BUILD_TABLES 4
+ebic_status ebic_batch_create(const ebic_handle* handles, const ebic_batch_item_t* items,
+                              int32_t n, int32_t flags, void* stream, ebic_batch* out);
+/* One evaluation of every problem, queued on `stream`. */
+ebic_status ebic_batch_eval(ebic_batch b, void* stream);
+/* The path (EBIC_PATH_*), vectors per part and parts per series chosen for a
+ * problem; the total work items and the persistent grid size. */
+ebic_status ebic_batch_describe(ebic_batch b, int32_t problem, int32_t* path,
+                                int32_t* vecs_per_part, int32_t* parts, int64_t* work_items,
+                                int32_t* grid);
+void ebic_batch_free(ebic_batch b);
+
+/* ---------------------------------------------------------------------------
  * Generation loop: Steps 1-5 of the "EBIC Algorithm" section, run entirely on
  * the device.  Semantics (identical to the library's reference reading):
  *   Step 1: distinct random series (length uniform in [len_min, len_max],

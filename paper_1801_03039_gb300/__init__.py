@@ -25,6 +25,8 @@ __all__ = [
     "ebic_read_pair_words", "ebic_set_path", "ebic_set_eval_tuning", "ebic_get_eval_tuning",
     "ebic_autotune_eval", "ebic_eval_population",
     "ebic_eval_population_dev", "ebic_eval_population_dev_noalloc", "ebic_check_device_error", "ebic_default_params",
+    "ebic_batch_create", "ebic_batch_eval", "ebic_batch_describe", "ebic_batch_free",
+    "BATCH_AUTOTUNE", "BATCH_GRAPH", "BATCH_BUILD_TABLES",
     "ebic_run_init", "ebic_run_step", "ebic_run_step_async", "ebic_run_step_profiled",
     "ebic_get_toprank", "ebic_get_population",
     "ebic_run_generations", "Params", "Stats", "PATH_AUTO", "PATH_GATHER", "PATH_BITMASK",
@@ -90,6 +92,10 @@ _SIGS = {
     "ebic_check_device_error": ([_P], _I32),
     "ebic_eval_population_dev_noalloc": ([_P, _P, _P, _I32, _I32, _I32, _P, _P, _P], _I32),
     "ebic_default_params": ([_P], None),
+    "ebic_batch_create": ([_P, _P, _I32, _I32, _P, _P], _I32),
+    "ebic_batch_eval": ([_P, _P], _I32),
+    "ebic_batch_describe": ([_P, _I32, _P, _P, _P, _P, _P], _I32),
+    "ebic_batch_free": ([_P], None),
     "ebic_run_init": ([_P, _P], _I32),
     "ebic_run_step": ([_P, _I32, _P], _I32),
     "ebic_run_step_async": ([_P, _I32, _P], _I32),
@@ -277,6 +283,49 @@ def ebic_eval_population_dev_noalloc(h, d_offsets, d_cols, P: int, total_cols: i
 
 def ebic_check_device_error(h):
     _check(lib().ebic_check_device_error(h))
+
+
+BATCH_AUTOTUNE, BATCH_GRAPH, BATCH_BUILD_TABLES = 1, 2, 4
+
+
+class BatchItem(ctypes.Structure):
+    _fields_ = [("d_offsets", ctypes.c_void_p), ("d_cols", ctypes.c_void_p),
+                ("P", ctypes.c_int32), ("total_cols", ctypes.c_int32), ("sigma", ctypes.c_int32),
+                ("d_inc", ctypes.c_void_p), ("d_fitness", ctypes.c_void_p)]
+
+
+def ebic_batch_create(handles, items, flags: int, stream=None):
+    """items: sequence of (d_offsets, d_cols, P, total_cols, sigma, d_inc, d_fitness)
+    with torch CUDA tensors for the device buffers.  Returns the batch handle."""
+    n = len(handles)
+    H = (ctypes.c_void_p * n)(*[h.value for h in handles])
+    arr = (BatchItem * n)()
+    for k, (off, cols, P, total, sigma, inc, fit) in enumerate(items):
+        arr[k] = BatchItem(_dev(off).value, _dev(cols).value, int(P), int(total), int(sigma),
+                           _dev(inc).value, _dev(fit).value)
+    b = ctypes.c_void_p()
+    _check(lib().ebic_batch_create(H, arr, n, int(flags), _stream(stream), ctypes.byref(b)))
+    return b
+
+
+def ebic_batch_eval(b, stream=None):
+    _check(lib().ebic_batch_eval(b, _stream(stream)))
+
+
+def ebic_batch_describe(b, problem: int) -> dict:
+    path, vpp, parts, grid = (ctypes.c_int32() for _ in range(4))
+    items = ctypes.c_int64()
+    _check(lib().ebic_batch_describe(b, int(problem), ctypes.byref(path), ctypes.byref(vpp),
+                                     ctypes.byref(parts), ctypes.byref(items),
+                                     ctypes.byref(grid)))
+    return dict(path=path.value, vecs_per_part=vpp.value, parts=parts.value,
+                work_items=items.value, grid=grid.value)
+
+
+def ebic_batch_free(b):
+    if b is not None and b.value:
+        lib().ebic_batch_free(b)
+        b.value = None
 
 
 def ebic_default_params(**overrides) -> Params:
