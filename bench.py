@@ -327,7 +327,99 @@ class GenerationsPaper:
             g *= 4
 
 
-WORKLOADS = {"eval-expression": EvalExpression, "generations-paper": GenerationsPaper}
+class EvalBatch:
+    """64 independent problems of uneven size (rows 500-50,000, columns
+    20-500, populations 256-2,048, lengths 3-30): one step is one persistent
+    launch over all of them (graph replay)."""
+    name = "eval-batch"
+
+    def __init__(self, rank: int):
+        from paper_1801_03039_gb300 import synth
+        self.items = synth.batch_uneven(seed=rank, n=64)
+        self.P = sum(len(it.offsets) - 1 for it in self.items)
+        self.R = None
+
+    def config(self):
+        return {"workload": "eval-batch-64-uneven", "problems": len(self.items),
+                "rows": [500, 50000], "cols": [20, 500], "population": [256, 2048],
+                "series_total": self.P, "series_len": [3, 30],
+                "paths": getattr(self, "paths", None),
+                "step": "one persistent launch over all problems (CUDA graph replay)",
+                "l2": "flushed before every timed step (512 MiB overwrite)"}
+
+    def units_per_step(self) -> int:
+        return sum((len(it.offsets) - 1) * it.problem.A.shape[0] for it in self.items)
+
+    def setup_gpu(self, torch, eb):
+        dev = torch.device("cuda", torch.cuda.current_device())
+        self.handles, bitems, self.outs = [], [], []
+        for it in self.items:
+            h = eb.ebic_load_matrix(it.problem.A)
+            P = len(it.offsets) - 1
+            off = torch.from_numpy(it.offsets).to(dev)
+            cols = torch.from_numpy(it.cols).to(dev)
+            inc = torch.zeros(P, dtype=torch.int32, device=dev)
+            fit = torch.zeros(P, dtype=torch.float64, device=dev)
+            self.handles.append(h)
+            self.outs.append((off, cols, inc, fit))
+            bitems.append((off, cols, P, len(it.cols), it.problem.sigma, inc, fit))
+        self.b = eb.ebic_batch_create(self.handles, bitems, eb.BATCH_BUILD_TABLES |
+                                      eb.BATCH_AUTOTUNE | eb.BATCH_GRAPH)
+        d = [eb.ebic_batch_describe(self.b, k) for k in range(len(self.items))]
+        self.paths = {"bitmask": sum(x["path"] == 2 for x in d),
+                      "gather": sum(x["path"] == 1 for x in d),
+                      "work_items": d[0]["work_items"], "grid": d[0]["grid"]}
+        torch.cuda.synchronize()
+
+    def step_gpu(self, torch, eb, stream):
+        eb.ebic_batch_eval(self.b, stream)
+
+    def e2e_gpu(self, torch, eb, steps: int) -> dict:
+        """Per step: every population's CBF copied in from pinned host memory,
+        one batch launch, every result copied back to pinned host memory."""
+        host_in = [(torch.from_numpy(it.offsets).pin_memory(), torch.from_numpy(it.cols).pin_memory())
+                   for it in self.items]
+        host_out = [(torch.empty(o[2].shape, dtype=o[2].dtype).pin_memory(),
+                     torch.empty(o[3].shape, dtype=o[3].dtype).pin_memory()) for o in self.outs]
+        s = torch.cuda.current_stream()
+
+        def one():
+            for (ho, hc), (off, cols, _, _) in zip(host_in, self.outs):
+                off.copy_(ho, non_blocking=True)
+                cols.copy_(hc, non_blocking=True)
+            eb.ebic_batch_eval(self.b, s)
+            for (hi, hf), (_, _, inc, fit) in zip(host_out, self.outs):
+                hi.copy_(inc, non_blocking=True)
+                hf.copy_(fit, non_blocking=True)
+            s.synchronize()
+
+        one()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            one()
+        dt = time.perf_counter() - t0
+        h2d = sum(a.nbytes + b.nbytes for a, b in ((it.offsets, it.cols) for it in self.items))
+        d2h = sum(o[2].numel() * 4 + o[3].numel() * 8 for o in self.outs)
+        return {"value": self.units_per_step() * steps / dt, "unit": "tests/s",
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
+
+    def oracle_sample(self, oracle, budget_s: float, nthreads: int):
+        it = max(self.items, key=lambda x: x.problem.A.shape[0])
+        n = 16
+        while True:
+            off = it.offsets[:n + 1]
+            cols = it.cols[:off[-1]]
+            t0 = time.perf_counter()
+            oracle.support(it.problem.A, off, cols, nthreads=nthreads)
+            dt = time.perf_counter() - t0
+            if dt > budget_s / 4 or n >= len(it.offsets) - 1:
+                self.R = it.problem.A.shape[0]
+                return n, dt
+            n = min(len(it.offsets) - 1, n * 4)
+
+
+WORKLOADS = {"eval-expression": EvalExpression, "generations-paper": GenerationsPaper,
+             "eval-batch": EvalBatch}
 
 
 # ---------------------------------------------------------------------------
@@ -409,6 +501,11 @@ def run_ours(args, ws, rank, local):
 
 
 def roofline(wl, gens, extra, per_step_ms, peaks):
+    if isinstance(wl, EvalBatch):
+        return {"kernel": "k_support_batch", "bound": "hbm", "achieved": None,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": None, "traffic": None,
+                "note": "mixed bitmask / gather problems: no algorithmic-byte model; the "
+                        "per-problem kernels' rooflines are those of the single-problem workloads"}
     if not gens:
         alg_bytes, alg_def = wl.algorithmic_bytes()
         kernel_s = statistics.mean(per_step_ms) / 1e3
@@ -470,7 +567,7 @@ def cpu_baseline(wl, budget_s: float):
     cores = os.cpu_count() or 1
     n, dt = wl.oracle_sample(oracle, budget_s, cores)
     return {"value": n * wl.R / dt, "unit": "tests/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {n} of {wl.P} series x all {wl.R} rows, one pass, "
+            "sample": f"first {n} series x all {wl.R} rows of {'the largest problem' if isinstance(wl, EvalBatch) else 'the population'}, one pass, "
                       f"OpenMP over series on {cores} threads ({dt:.2f} s)"}
 
 
@@ -493,16 +590,22 @@ def run_reference(args, ws, rank):
         used = 1
     else:
         n, _ = wl.oracle_sample(oracle, 8.0, cores)
-        off = wl.off[:n + 1]
-        cols = wl.cols[:off[-1]]
+        if isinstance(wl, EvalBatch):
+            big = max(wl.items, key=lambda x: x.problem.A.shape[0])
+            A, off, cols = big.problem.A, big.offsets[:n + 1], big.cols[:big.offsets[n]]
+            where = "the largest problem"
+        else:
+            A, off, cols = wl.prob.A, wl.off[:n + 1], wl.cols[:wl.off[n]]
+            where = "the population"
         for _ in range(args.warmup):
-            oracle.support(wl.prob.A, off, cols, nthreads=cores)
+            oracle.support(A, off, cols, nthreads=cores)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            oracle.support(wl.prob.A, off, cols, nthreads=cores)
+            oracle.support(A, off, cols, nthreads=cores)
         dt = time.perf_counter() - t0
-        value = n * wl.R * args.steps / dt
-        sample = f"first {n} of {wl.P} series x all {wl.R} rows per step, OpenMP on {cores} threads"
+        value = n * A.shape[0] * args.steps / dt
+        sample = (f"first {n} series x all {A.shape[0]} rows of {where} per step, "
+                  f"OpenMP on {cores} threads")
         used = cores
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "tests/s",
             "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
