@@ -11,6 +11,11 @@ paper_1801_03039_gb300/synth.py):
                    and order-preserving 50 x 10 plants; population 600 of
                    length 3-20.  A step is one generation of Steps 2-5, run on
                    the device as a replayed CUDA graph.
+  generations-screened  the generations-paper run with offspring screening
+                   (8 candidate children per attempt, best surrogate score
+                   goes on); the surrogate is trained first on pairs logged
+                   from plain runs of other seeds.  Reports the plain-vs-
+                   screened comparison and the held-out ranking quality.
   eval-expression  20,000 x 200 log-normal matrix with 10 planted overlapping
                    order-preserving biclusters; a population of 4,096 series of
                    length 3-30.  A step is one fitness pass (support + Eq. (1))
@@ -327,6 +332,187 @@ class GenerationsPaper:
             g *= 4
 
 
+class GenerationsScreened(GenerationsPaper):
+    """The generations-paper run with offspring screening by the learned
+    surrogate: the surrogate is trained on (series, exact fitness) pairs logged
+    from plain runs of the same matrix (other seeds), then every attempt of
+    Step 3 builds 8 candidate children and the best-scoring one goes on to the
+    tabu check and exact evaluation.  A step is one screened generation.
+    Training, the held-out ranking quality and the plain-vs-screened
+    comparison (1,000 generations each, same seed) run outside the timed
+    region."""
+    name = "generations-screened"
+    V = 8
+    TRAIN_SEEDS = (1001, 1002)       # 2 plain runs x 1,001 generations x 600 = 1.2M pairs
+    HOLDOUT_SEED = 1003
+    STEPS, BATCH, LR = 3000, 4096, 1e-3
+
+    def config(self):
+        c = super().config()
+        c.update({"workload": "generations-screened-1000x100-P600-L3-20-V8",
+                  "oversample": self.V,
+                  "step": "one screened generation (candidate children, surrogate forward, "
+                          "pick, Steps 2-5) as a replayed CUDA graph",
+                  "surrogate": "bf16 MLP 80-256-256-1 on sum-pooled column embeddings + "
+                               "column mean/sd + length",
+                  "training": getattr(self, "train_info", None)})
+        return c
+
+    def _params(self, iterations, seed):
+        kw = self.params_kw(iterations)
+        kw["seed"] = seed
+        return self.eb.ebic_default_params(**kw)
+
+    def _plain_run(self, seed, track=False):
+        eb = self.eb
+        eb.ebic_run_screen(self.h, None, 1, eb.SCREEN_OFF)
+        eb.ebic_run_init(self.h, self._params(self.GENS, seed))
+        if not track:
+            eb.ebic_run_step(self.h, self.GENS)
+            return None
+        return self._tracked(self.GENS)
+
+    def _tracked(self, gens):
+        eb = self.eb
+        best = []
+        for _ in range(gens):
+            eb.ebic_run_step(self.h, 1)
+            _, fit, _ = eb.ebic_get_toprank(self.h, 1, self.LMAX)
+            best.append(float(fit[0]) if len(fit) else 0.0)
+        return best
+
+    def setup_gpu(self, torch, eb, capacity: int):
+        self.eb = eb
+        self.h = eb.ebic_load_matrix(self.prob.A)
+        t0 = time.perf_counter()
+        self.sur = eb.ebic_surrogate_create(self.h, self.LMAX, self.rank)
+        n = 0
+        for seed in self.TRAIN_SEEDS:
+            self._plain_run(seed)
+            n = eb.ebic_surrogate_log(self.sur, self.h)
+        t_log = time.perf_counter() - t0
+        first = eb.ebic_surrogate_train(self.sur, 1, self.BATCH, self.LR)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        last = eb.ebic_surrogate_train(self.sur, self.STEPS - 1, self.BATCH, self.LR)
+        t_train = time.perf_counter() - t1
+        self.train_info = {"pairs": n, "runs": list(self.TRAIN_SEEDS), "steps": self.STEPS,
+                           "batch": self.BATCH, "lr": self.LR, "loss_first": first,
+                           "loss_last": last, "train_s": round(t_train, 3),
+                           "train_steps_per_s": round((self.STEPS - 1) / t_train, 1),
+                           "logging_runs_s": round(t_log, 3)}
+        self.quality = self._holdout_quality(torch)
+        eb.ebic_run_screen(self.h, self.sur, self.V, eb.SCREEN_SURROGATE)
+        eb.ebic_run_init(self.h, self._params(capacity, self.rank))
+        self.tuning = eb.ebic_get_eval_tuning(self.h)
+        self.capacity = capacity
+
+    def _holdout_quality(self, torch):
+        """Spearman correlation and top-10% recall of the predictions on the
+        populations of a held-out plain run (every 10th generation)."""
+        eb = self.eb
+        eb.ebic_run_screen(self.h, None, 1, eb.SCREEN_OFF)
+        eb.ebic_run_init(self.h, self._params(self.GENS, self.HOLDOUT_SEED))
+        seqs, fit = [], []
+        for g in range(0, self.GENS + 1, 10):
+            if g:
+                eb.ebic_run_step(self.h, 10)
+            pop = eb.ebic_get_population(self.h, self.P, self.LMAX)
+            seqs += pop["seqs"]
+            fit.append(pop["f"])
+        fit = np.concatenate(fit)
+        n = len(seqs)
+        arr = np.zeros((n, self.LMAX), np.int16)
+        lens = np.zeros(n, np.int32)
+        for i, x in enumerate(seqs):
+            arr[i, :len(x)] = x
+            lens[i] = len(x)
+        d_seq = torch.from_numpy(arr).cuda()
+        d_len = torch.from_numpy(lens).cuda()
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+        eb.ebic_surrogate_predict(self.sur, d_seq, d_len, self.LMAX, n, out)
+        pred = out.cpu().numpy().astype(np.float64)
+        target = np.log1p(fit)
+        ra = np.argsort(np.argsort(pred)).astype(np.float64)
+        rb = np.argsort(np.argsort(target)).astype(np.float64)
+        rho = float(np.corrcoef(ra, rb)[0, 1])
+        k = max(1, n // 10)
+        top_true = set(np.argsort(-target, kind="stable")[:k].tolist())
+        top_pred = set(np.argsort(-pred, kind="stable")[:k].tolist())
+        return {"pairs": n, "spearman": rho, "top10pct_recall": len(top_true & top_pred) / k,
+                "source": f"plain run seed {self.HOLDOUT_SEED}, populations of every 10th "
+                          "generation (not in the training log)"}
+
+    COMPARE_SEEDS = 3
+
+    def compare(self) -> dict:
+        """1,000-generation runs with the same seeds in three arms: plain EBIC,
+        screening with the trained surrogate, and screening with random
+        (Philox) scores -- the same oversampling and the same preference for
+        candidates outside the tabu list, without the model.  Per arm: wall
+        time, final best exact fitness, and the generation at which the run
+        first reaches 99% of the plain run's final best."""
+        eb = self.eb
+        arms = (("plain", None, 1, eb.SCREEN_OFF),
+                ("screened", self.sur, self.V, eb.SCREEN_SURROGATE),
+                ("random_scores", None, self.V, eb.SCREEN_PSEUDO))
+        per_seed = []
+        for i in range(self.COMPARE_SEEDS):
+            seed = 10 * self.rank + i
+            row = {"seed": seed}
+            for name, sur, V, mode in arms:
+                eb.ebic_run_screen(self.h, sur, V, mode)
+                eb.ebic_run_init(self.h, self._params(self.GENS, seed))
+                t0 = time.perf_counter()
+                st = eb.ebic_run_step(self.h, self.GENS)
+                dt = time.perf_counter() - t0
+                _, fit, _ = eb.ebic_get_toprank(self.h, self.T, self.LMAX)
+                eb.ebic_run_init(self.h, self._params(self.GENS, seed))
+                curve = self._tracked(self.GENS)
+                row[name] = {"generations_per_s": round(st["generations_done"] / dt, 1),
+                             "generations": st["generations_done"],
+                             "final_best_fitness": float(fit[0]),
+                             "tabu_hits": st["tabu_hits_total"], "curve": curve}
+            target = 0.99 * row["plain"]["final_best_fitness"]
+            for name, *_ in arms:
+                curve = row[name].pop("curve")
+                hit = next((g + 1 for g, b in enumerate(curve) if b >= target), None)
+                row[name]["generations_to_99pct_of_plain_best"] = hit
+            row["screened_best_over_plain_best"] = (row["screened"]["final_best_fitness"] /
+                                                    row["plain"]["final_best_fitness"])
+            per_seed.append(row)
+        eb.ebic_run_screen(self.h, None, 1, eb.SCREEN_OFF)
+        summary = {}
+        for name, *_ in arms:
+            summary[name] = {
+                "mean_generations_per_s": statistics.mean(r[name]["generations_per_s"] for r in per_seed),
+                "mean_final_best_fitness": statistics.mean(r[name]["final_best_fitness"] for r in per_seed)}
+        ratios = [r["screened_best_over_plain_best"] for r in per_seed]
+        return {"per_seed": per_seed, "summary": summary,
+                "screened_best_over_plain_best_min": min(ratios),
+                "within_1pct_every_seed": all(x >= 0.99 for x in ratios),
+                "holdout": self.quality}
+
+    def e2e_gpu(self, torch, eb, steps: int) -> dict:
+        """A whole screened user run through the host API with the trained
+        surrogate: attach it, Step 1 + 1,000 screened generations, read the
+        top-rank list back."""
+        h = eb.ebic_load_matrix(self.prob.A)
+        t0 = time.perf_counter()
+        eb.ebic_run_screen(h, self.sur, self.V, eb.SCREEN_SURROGATE)
+        top, fit, st = eb.ebic_run_generations(h, self._params(self.GENS, self.rank))
+        dt = time.perf_counter() - t0
+        eb.ebic_free(h)
+        gens = st["generations_done"]
+        return {"value": self.units_per_step() * gens / dt, "unit": "tests/s",
+                "generations_per_s": gens / dt, "generations": gens,
+                "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(sum(len(t) for t in top) * 4 + len(fit) * 12),
+                "scope": "ebic_run_screen + ebic_run_generations (Step 1 + 1,000 screened "
+                         "generations, top-rank read back), wall clock; the matrix was "
+                         "loaded before the timer started"}
+
+
 class EvalBatch:
     """64 independent problems of uneven size (rows 500-50,000, columns
     20-500, populations 256-2,048, lengths 3-30): one step is one persistent
@@ -419,7 +605,7 @@ class EvalBatch:
 
 
 WORKLOADS = {"eval-expression": EvalExpression, "generations-paper": GenerationsPaper,
-             "eval-batch": EvalBatch}
+             "eval-batch": EvalBatch, "generations-screened": GenerationsScreened}
 
 
 # ---------------------------------------------------------------------------
@@ -468,6 +654,8 @@ def run_ours(args, ws, rank, local):
         extra["run_stats"] = st
         kern = wl.profile_gpu(eb)
         extra["kernel_us"] = {k: round(v, 2) for k, v in kern.items()}
+        if isinstance(wl, GenerationsScreened):
+            extra["surrogate"] = wl.compare()
     barrier(ws)
     slowest = aggregate_max(total_s, ws, device=torch.device("cuda", local))
     e2e = wl.e2e_gpu(torch, eb, max(3, args.steps))

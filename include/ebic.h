@@ -337,6 +337,94 @@ ebic_status ebic_run_generations(ebic_handle h, const ebic_params_t* p, int32_t*
                                  int32_t* out_cols, double* out_fitness, int32_t* inout_n,
                                  ebic_stats_t* stats);
 
+/* ---------------------------------------------------------------------------
+ * Fitness surrogate and offspring screening.  The paper has no counterpart:
+ * EBIC evaluates every child exactly (Step 4).  This is an optional
+ * pre-screen: a small learned model predicts which of several candidate
+ * children scores best, and only the chosen one goes on to Step 3's
+ * acceptance and Step 4's exact evaluation, so every individual that enters a
+ * population is still scored by Eq. (1) on exact support.
+ *
+ * Model: x[0:64] = sum over the series' columns of a learned 64-dimensional
+ * column embedding, x[64] / x[65] = mean over the series' columns of the
+ * column mean / population standard deviation of the matrix (NaN skipped),
+ * x[66] = length / len_scale, x[67:80] = 0;  h1 = relu(x W1 + b1) (256),
+ * h2 = relu(h1 W2 + b2) (256), y = h2 . w3 + b3.  y predicts the standardised
+ * target (log1p(fitness) - mean) / sd, mean and sd taken over the training
+ * set.  Operands bf16 on the tensor cores, fp32 accumulation, fp32 master
+ * weights, Adam (beta1 0.9, beta2 0.999, eps 1e-8) on mean squared error.
+ *
+ * Parameter layout of the flat fp32 vector (ebic_surrogate_params):
+ *   Emb [C][64] | W1 [80][256] | b1 [256] | W2 [256][256] | b2 [256] |
+ *   w3 [256] | b3 [1]
+ * ------------------------------------------------------------------------- */
+typedef struct ebic_surrogate_ctx* ebic_surrogate;
+
+/* A surrogate for the handle's matrix (column count and column statistics are
+ * taken from it; the handle must outlive the surrogate).  Weights are
+ * initialised from `seed` (embeddings N(0, 0.01), W1 / W2 He-scaled normal,
+ * w3 N(0, 1/256), biases 0). */
+ebic_status ebic_surrogate_create(ebic_handle h, int32_t len_scale, uint64_t seed,
+                                  ebic_surrogate* out);
+/* Releases the surrogate.  EBIC_ERR_STATE (and nothing is released) while a
+ * run of some handle is screening with it: detach it first with
+ * ebic_run_screen(h, NULL, 1, EBIC_SCREEN_OFF) or free that handle. */
+ebic_status ebic_surrogate_free(ebic_surrogate s);
+/* Reads (write = 0) or replaces (write != 0) the fp32 parameters, layout
+ * above.  *n_params = capacity on entry (ignored when host_params is NULL),
+ * parameter count on return. */
+ebic_status ebic_surrogate_params(ebic_surrogate s, float* host_params, int64_t* n_params,
+                                  int32_t write);
+/* The parameter gradients left by the last ebic_surrogate_step or training
+ * step (same layout; n >= the parameter count). */
+ebic_status ebic_surrogate_grads(ebic_surrogate s, float* host_grads, int64_t n);
+/* Column mean and population standard deviation used as features (C each). */
+ebic_status ebic_surrogate_colstats(ebic_surrogate s, float* host_mean, float* host_sd);
+/* One forward + backward pass on explicit standardised targets (device
+ * pointers): series r of the batch is row d_idx[b] (d_idx NULL: row b) of
+ * d_seq[.][stride] / d_len; target d_target[r].  update != 0 also takes one Adam
+ * step with learning rate lr.  *out_loss (nullable) = mean squared error before
+ * the step.  Synchronous. */
+ebic_status ebic_surrogate_step(ebic_surrogate s, const uint16_t* d_seq, const int32_t* d_len,
+                                int32_t stride, const float* d_target, const int32_t* d_idx,
+                                int32_t batch, float lr, int32_t update, float* out_loss);
+/* Appends every evaluated individual of the handle's current run (series and
+ * exact fitness) to the surrogate's training log.  *out_total (nullable) = log
+ * size afterwards. */
+ebic_status ebic_surrogate_log(ebic_surrogate s, ebic_handle h, int64_t* out_total);
+/* Training on device arrays: n (series, fitness) pairs; targets standardised
+ * over the n pairs; `steps` Adam steps on minibatches of `batch` rows drawn
+ * uniformly with replacement (Philox-4x32-10 keyed by the creation seed and
+ * the step number).  d_seq/d_len/d_fitness NULL: train on the log.  *out_loss
+ * = minibatch loss of the last step.  Synchronous. */
+ebic_status ebic_surrogate_train(ebic_surrogate s, const uint16_t* d_seq, const int32_t* d_len,
+                                 int32_t stride, const double* d_fitness, int64_t n,
+                                 int32_t steps, int32_t batch, float lr, float* out_loss);
+/* The target standardisation of the last training call. */
+ebic_status ebic_surrogate_target_norm(ebic_surrogate s, float* mean, float* sd);
+/* Predicted standardised targets of n series (device pointers; d_out[n] fp32),
+ * queued on `stream` (NULL: the surrogate's own stream, then synchronised). */
+ebic_status ebic_surrogate_predict(ebic_surrogate s, const uint16_t* d_seq, const int32_t* d_len,
+                                   int32_t stride, int64_t n, float* d_out, void* stream);
+
+typedef enum {
+  EBIC_SCREEN_OFF = 0,        /* plain EBIC */
+  EBIC_SCREEN_SURROGATE = 1,  /* score candidates with the surrogate */
+  EBIC_SCREEN_PSEUDO = 2      /* score candidates with Philox draws (testing the
+                                 screening logic without a model) */
+} ebic_screen_mode;
+
+/* Screening for the next ebic_run_init of h.  Each attempt of Step 3 builds
+ * `oversample` candidate children (1 .. 16) for its tournament outcome:
+ * candidate v repeats the crossover cuts and the mutation with draws
+ * 2k + 1 + 5v .. 2k + 5 + 5v (v = 0 is the plain child), and the candidate
+ * with the highest score goes on (ties: lowest v).  Pseudo scores: candidate v
+ * of tournament outcome c (= ta * k + tb; tb = 0 without crossover) scores
+ * word 0 of Philox(counter (j, g, 65536 + c * oversample + v, 0), key = seed)
+ * shifted right by 8.  oversample 1 or mode EBIC_SCREEN_OFF is plain EBIC.
+ * The surrogate must stay alive while a run screens with it. */
+ebic_status ebic_run_screen(ebic_handle h, ebic_surrogate s, int32_t oversample, int32_t mode);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,6 +51,7 @@ class Params(ctypes.Structure):
         ("overlap_tau", ctypes.c_double), ("elite_frac", ctypes.c_double),
         ("penalty_base", ctypes.c_double), ("p_crossover", ctypes.c_double),
         ("seed", ctypes.c_uint64),
+        ("oversample", ctypes.c_int32), ("reserved", ctypes.c_int32),
     ]
 
 
@@ -226,7 +227,7 @@ def toprank_update(list_seqs, list_f, pop_seqs, pop_f, T, tau):
 def make_params(**kw) -> Params:
     d = dict(pop_size=100, len_min=2, len_max=6, iterations=10, sigma=10, toprank_size=100,
              tournament_k=2, fitness_support=0, overlap_tau=0.5, elite_frac=0.25,
-             penalty_base=1.2, p_crossover=0.5, seed=0)
+             penalty_base=1.2, p_crossover=0.5, seed=0, oversample=1)
     d.update(kw)
     p = Params()
     for k, v in d.items():

@@ -145,6 +145,7 @@ struct Params {
   double penalty_base;      // crowding penalty base (1.2)
   double p_crossover;       // probability that an attempt uses crossover
   uint64_t seed;
+  int32_t oversample = 1;   // candidates per attempt (offspring screening, not in the paper)
 };
 
 struct Entry {
@@ -271,8 +272,20 @@ Seq mutate(const Seq& s, int32_t C, int32_t Lmin, int32_t Lmax, uint32_t r_type,
 // Draw layout for attempt j of generation g (k = tournament size):
 //   0..k-1 first tournament, k crossover coin, k+1..2k second tournament,
 //   2k+1 / 2k+2 crossover cuts, 2k+3 mutation kind, 2k+4 / 2k+5 its operands.
+//
+// Offspring screening (not in the paper), oversample V > 1: candidate v
+// repeats the crossover cuts and the mutation with draws 2k+1+5v .. 2k+5+5v
+// (v = 0 is the plain child).  The candidates are taken by decreasing pseudo
+// score (ties: lowest v) and the first one that is not in the tabu list as it
+// stood when the generation began is the child; when all of them are, the
+// best-scoring one is (a tabu hit).  The pseudo score of candidate v is word
+// 0 of Philox(counter (j, g, 65536 + c V + v, 0), key = seed) shifted right by
+// 8, where c = ta k + tb names the tournament outcome: ta (tb) is the first
+// position in the first (second) tournament holding its winner, tb = 0
+// without crossover.
 Seq make_child(const Params& p, int32_t C, int32_t g, int32_t j, const std::vector<Seq>& prev,
-               const std::vector<double>& prev_f, const std::vector<int64_t>& pen) {
+               const std::vector<double>& prev_f, const std::vector<int64_t>& pen,
+               const std::set<Seq>& tabu_at_start) {
   const int32_t k = p.tournament_k;
   const uint32_t Pprev = (uint32_t)prev.size();
   int32_t ea[8], eb[8];
@@ -280,22 +293,43 @@ Seq make_child(const Params& p, int32_t C, int32_t g, int32_t j, const std::vect
   bool cross = (double)draw(p.seed, g, j, k) * 0x1p-32 < p.p_crossover;
   for (int32_t t = 0; t < k; ++t) eb[t] = (int32_t)below(draw(p.seed, g, j, k + 1 + t), Pprev);
 
-  int32_t wa = tournament(ea, k, prev, prev_f, pen, p.penalty_base);
-  Seq child = prev[wa];
-  if (cross) {
-    int32_t wb = tournament(eb, k, prev, prev_f, pen, p.penalty_base);
-    const Seq& a = prev[wa];
-    const Seq& b = prev[wb];
-    int32_t cut_a = 1 + (int32_t)below(draw(p.seed, g, j, 2 * k + 1), (uint32_t)a.size());
-    int32_t cut_b = (int32_t)below(draw(p.seed, g, j, 2 * k + 2), (uint32_t)b.size());
-    Seq x = crossover(a, b, cut_a, cut_b, p.len_max);
-    // Reading: a crossover child shorter than len_min is dropped and the
-    // first parent goes on to the mutation instead.
-    if ((int32_t)x.size() >= p.len_min) child = x;
+  const int32_t wa = tournament(ea, k, prev, prev_f, pen, p.penalty_base);
+  const int32_t wb = cross ? tournament(eb, k, prev, prev_f, pen, p.penalty_base) : -1;
+  const int32_t V = p.oversample;
+  std::vector<Seq> cand;
+  std::vector<uint32_t> score;
+  for (int32_t v = 0; v < V; ++v) {
+    const int32_t base = 2 * k + 1 + 5 * v;
+    Seq child = prev[wa];
+    if (cross) {
+      const Seq& a = prev[wa];
+      const Seq& b = prev[wb];
+      int32_t cut_a = 1 + (int32_t)below(draw(p.seed, g, j, base), (uint32_t)a.size());
+      int32_t cut_b = (int32_t)below(draw(p.seed, g, j, base + 1), (uint32_t)b.size());
+      Seq x = crossover(a, b, cut_a, cut_b, p.len_max);
+      // Reading: a crossover child shorter than len_min is dropped and the
+      // first parent goes on to the mutation instead.
+      if ((int32_t)x.size() >= p.len_min) child = x;
+    }
+    int32_t kind;
+    Seq m = mutate(child, C, p.len_min, p.len_max, draw(p.seed, g, j, base + 2),
+                   draw(p.seed, g, j, base + 3), draw(p.seed, g, j, base + 4), &kind);
+    if (V == 1) return m;
+    int32_t ta = 0, tb = 0;
+    while (ea[ta] != wa) ++ta;
+    if (cross)
+      while (eb[tb] != wb) ++tb;
+    const int32_t c = ta * k + tb;
+    cand.push_back(m);
+    score.push_back(draw(p.seed, g, j, 4 * (65536 + c * V + v)) >> 8);
   }
-  int32_t kind;
-  return mutate(child, C, p.len_min, p.len_max, draw(p.seed, g, j, 2 * k + 3),
-                draw(p.seed, g, j, 2 * k + 4), draw(p.seed, g, j, 2 * k + 5), &kind);
+  std::vector<int32_t> order((size_t)V);
+  for (int32_t v = 0; v < V; ++v) order[v] = v;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int32_t a, int32_t b) { return score[a] > score[b]; });
+  for (int32_t i = 0; i < V; ++i)
+    if (!tabu_at_start.count(cand[order[i]])) return cand[order[i]];
+  return cand[order[0]];
 }
 
 // Top-rank overlap (Step 5 and the Discussion: the list compares column sets,
@@ -363,6 +397,8 @@ typedef struct {
       fitness_support;
   double overlap_tau, elite_frac, penalty_base, p_crossover;
   uint64_t seed;
+  int32_t oversample;   // offspring screening with pseudo scores (1: plain EBIC)
+  int32_t reserved;
 } or_params;
 
 typedef struct {
@@ -492,6 +528,7 @@ int32_t or_run(const float* A, int32_t R, int32_t C, const or_params* pp, int32_
   p.tournament_k = pp->tournament_k; p.fitness_support = pp->fitness_support;
   p.overlap_tau = pp->overlap_tau; p.elite_frac = pp->elite_frac;
   p.penalty_base = pp->penalty_base; p.p_crossover = pp->p_crossover; p.seed = pp->seed;
+  p.oversample = pp->oversample < 1 ? 1 : pp->oversample;
   if (p.pop_size < 2 || p.len_min < 1 || p.len_max < p.len_min || p.len_max > C ||
       p.tournament_k < 1 || p.tournament_k > 4 || p.toprank_size < 1 || p.iterations < 0)
     return -1;
@@ -573,8 +610,10 @@ int32_t or_run(const float* A, int32_t R, int32_t C, const or_params* pp, int32_
       prev_f[i] = pop[i].f;
     }
     int32_t hits = 0;
+    std::set<Seq> tabu_at_start;
+    if (p.oversample > 1) tabu_at_start = tabu;
     for (int32_t j = 0; (int32_t)next.size() < P; ++j) {
-      Seq child = make_child(p, C, g, j, prev_seq, prev_f, pen);
+      Seq child = make_child(p, C, g, j, prev_seq, prev_f, pen, tabu_at_start);
       st->attempts_total++;
       if (tabu.count(child)) {
         ++hits;

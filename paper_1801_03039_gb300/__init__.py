@@ -31,10 +31,15 @@ __all__ = [
     "ebic_get_toprank", "ebic_get_population",
     "ebic_run_generations", "Params", "Stats", "PATH_AUTO", "PATH_GATHER", "PATH_BITMASK",
     "SUPPORT_INC", "SUPPORT_INC_PLUS_DEC",
+    "ebic_surrogate_create", "ebic_surrogate_free", "ebic_surrogate_params", "ebic_surrogate_grads",
+    "ebic_surrogate_colstats", "ebic_surrogate_step", "ebic_surrogate_log", "ebic_surrogate_train",
+    "ebic_surrogate_target_norm", "ebic_surrogate_predict", "ebic_run_screen",
+    "SCREEN_OFF", "SCREEN_SURROGATE", "SCREEN_PSEUDO",
 ]
 
 PATH_AUTO, PATH_GATHER, PATH_BITMASK = 0, 1, 2
 SUPPORT_INC, SUPPORT_INC_PLUS_DEC = 0, 1
+SCREEN_OFF, SCREEN_SURROGATE, SCREEN_PSEUDO = 0, 1, 2
 STATUS = {0: "EBIC_OK", 1: "EBIC_ERR_ARG", 2: "EBIC_ERR_CUDA", 3: "EBIC_ERR_OOM",
           4: "EBIC_ERR_TIMEOUT", 5: "EBIC_ERR_STATE", 6: "EBIC_ERR_CANCELLED",
           7: "EBIC_ERR_DEVICE"}
@@ -103,6 +108,18 @@ _SIGS = {
     "ebic_get_toprank": ([_P, _P, _P, _P, _P, _P], _I32),
     "ebic_get_population": ([_P, _P, _P, _P, _P, _P, _P], _I32),
     "ebic_run_generations": ([_P, _P, _P, _P, _P, _P, _P], _I32),
+    "ebic_surrogate_create": ([_P, _I32, ctypes.c_uint64, _P], _I32),
+    "ebic_surrogate_free": ([_P], _I32),
+    "ebic_surrogate_params": ([_P, _P, _P, _I32], _I32),
+    "ebic_surrogate_grads": ([_P, _P, ctypes.c_int64], _I32),
+    "ebic_surrogate_colstats": ([_P, _P, _P], _I32),
+    "ebic_surrogate_step": ([_P, _P, _P, _I32, _P, _P, _I32, ctypes.c_float, _I32, _P], _I32),
+    "ebic_surrogate_log": ([_P, _P, _P], _I32),
+    "ebic_surrogate_train": ([_P, _P, _P, _I32, _P, ctypes.c_int64, _I32, _I32, ctypes.c_float,
+                              _P], _I32),
+    "ebic_surrogate_target_norm": ([_P, _P, _P], _I32),
+    "ebic_surrogate_predict": ([_P, _P, _P, _I32, ctypes.c_int64, _P, _P], _I32),
+    "ebic_run_screen": ([_P, _P, _I32, _I32], _I32),
 }
 
 _lock = threading.Lock()
@@ -404,3 +421,100 @@ def ebic_run_generations(h, params: Params, capacity: int | None = None):
                                       ctypes.byref(n), ctypes.byref(st)))
     k = n.value
     return _records(off, cols, k), fit[:k].copy(), st.as_dict()
+
+
+# ---------------------------------------------------------------------------
+# Fitness surrogate and offspring screening (no counterpart in the paper)
+SUR_F, SUR_EMB, SUR_H = 80, 64, 256
+
+
+def ebic_surrogate_create(h, len_scale: int = 64, seed: int = 0) -> ctypes.c_void_p:
+    out = ctypes.c_void_p()
+    _check(lib().ebic_surrogate_create(h, int(len_scale), int(seed), ctypes.byref(out)))
+    return out
+
+
+def ebic_surrogate_free(s):
+    _check(lib().ebic_surrogate_free(s))
+
+
+def ebic_surrogate_params(s, values=None) -> np.ndarray:
+    """Reads the flat fp32 parameters, or replaces them with `values`."""
+    n = ctypes.c_int64(0)
+    _check(lib().ebic_surrogate_params(s, None, ctypes.byref(n), 0))
+    if values is None:
+        out = np.zeros(n.value, np.float32)
+        _check(lib().ebic_surrogate_params(s, out.ctypes.data_as(_P), ctypes.byref(n), 0))
+        return out
+    v, p = _host(values, np.float32)
+    if v.size != n.value:
+        raise ValueError(f"expected {n.value} parameters, got {v.size}")
+    _check(lib().ebic_surrogate_params(s, p, ctypes.byref(n), 1))
+    return v
+
+
+def ebic_surrogate_split(flat: np.ndarray, C: int) -> dict:
+    """Views of the flat parameter vector by name (Emb, W1, b1, W2, b2, w3, b3)."""
+    shapes = [("Emb", (C, SUR_EMB)), ("W1", (SUR_F, SUR_H)), ("b1", (SUR_H,)),
+              ("W2", (SUR_H, SUR_H)), ("b2", (SUR_H,)), ("w3", (SUR_H,)), ("b3", ())]
+    out, o = {}, 0
+    for name, shp in shapes:
+        n = int(np.prod(shp)) if shp else 1
+        out[name] = flat[o:o + n].reshape(shp)
+        o += n
+    return out
+
+
+def ebic_surrogate_grads(s) -> np.ndarray:
+    n = ctypes.c_int64(0)
+    _check(lib().ebic_surrogate_params(s, None, ctypes.byref(n), 0))
+    out = np.zeros(n.value, np.float32)
+    _check(lib().ebic_surrogate_grads(s, out.ctypes.data_as(_P), n.value))
+    return out
+
+
+def ebic_surrogate_colstats(s, C: int):
+    m = np.zeros(C, np.float32)
+    d = np.zeros(C, np.float32)
+    _check(lib().ebic_surrogate_colstats(s, m.ctypes.data_as(_P), d.ctypes.data_as(_P)))
+    return m, d
+
+
+def ebic_surrogate_step(s, d_seq, d_len, stride: int, d_target, batch: int, lr: float = 0.0,
+                        update: bool = False, d_idx=None) -> float:
+    loss = ctypes.c_float(0)
+    _check(lib().ebic_surrogate_step(s, _dev(d_seq), _dev(d_len), int(stride), _dev(d_target),
+                                     _dev(d_idx), int(batch), float(lr), int(bool(update)),
+                                     ctypes.byref(loss)))
+    return loss.value
+
+
+def ebic_surrogate_log(s, h) -> int:
+    n = ctypes.c_int64(0)
+    _check(lib().ebic_surrogate_log(s, h, ctypes.byref(n)))
+    return n.value
+
+
+def ebic_surrogate_train(s, steps: int, batch: int, lr: float, d_seq=None, d_len=None,
+                         stride: int = 0, d_fitness=None, n: int = 0) -> float:
+    """Adam steps on device pairs (or on the log when no arrays are given)."""
+    loss = ctypes.c_float(0)
+    _check(lib().ebic_surrogate_train(s, _dev(d_seq), _dev(d_len), int(stride), _dev(d_fitness),
+                                      int(n), int(steps), int(batch), float(lr),
+                                      ctypes.byref(loss)))
+    return loss.value
+
+
+def ebic_surrogate_target_norm(s):
+    m, d = ctypes.c_float(0), ctypes.c_float(0)
+    _check(lib().ebic_surrogate_target_norm(s, ctypes.byref(m), ctypes.byref(d)))
+    return m.value, d.value
+
+
+def ebic_surrogate_predict(s, d_seq, d_len, stride: int, n: int, d_out, stream=None):
+    _check(lib().ebic_surrogate_predict(s, _dev(d_seq), _dev(d_len), int(stride), int(n),
+                                        _dev(d_out), _stream(stream)))
+
+
+def ebic_run_screen(h, s=None, oversample: int = 1, mode: int = SCREEN_OFF):
+    _check(lib().ebic_run_screen(h, s, int(oversample), int(mode)))

@@ -73,6 +73,12 @@ struct EaDev {
   const long long* pow_off;     // [Lmax + 1]
   const float* c_over_L;        // [Lmax + 1] log(base) / L as float
   Ctl* ctl;
+  // offspring screening (V candidates per attempt and tournament outcome):
+  // candidate v of (attempt j, outcome c) is row (j * ncombo + c) * V + v
+  int32_t V, screen;
+  uint16_t* var_seq;            // [rows][S]
+  int32_t* var_len;             // [rows]
+  float* var_score;             // [rows]
 };
 
 constexpr int kMaxLen = EBIC_MAX_EA_LEN;
@@ -255,14 +261,21 @@ __device__ bool tabu_contains(const EaDev& d, unsigned long long key, const uint
 // k_spec: every child an attempt can produce.  Thread = (attempt, combo);
 // combo = ta * k + tb names the winning positions of the two tournaments.
 // ---------------------------------------------------------------------------
-template <bool INIT>
+// SCREEN: thread = (attempt, combo, candidate v); candidate v repeats the
+// crossover cuts and the mutation with draws 2k + 1 + 5v .. 2k + 5 + 5v (v = 0
+// is the plain child) and goes to the candidate buffers; k_pick completes the
+// record once the candidates are scored.
+template <bool INIT, bool SCREEN>
 __global__ void __launch_bounds__(128) k_spec(EaDev d) {
   if (*(volatile int32_t*)&d.ctl->stop) return;
   const int g = d.ctl->gen;
   const int nc = INIT ? 1 : d.ncombo;
+  const int V = SCREEN ? d.V : 1;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (tid >= (long long)d.J * nc) return;
-  const int j = (int)(tid / nc), c = (int)(tid % nc);
+  if (tid >= (long long)d.J * nc * V) return;
+  const int v = SCREEN ? (int)(tid % V) : 0;
+  const long long jc = SCREEN ? tid / V : tid;
+  const int j = (int)(jc / nc), c = (int)(jc % nc);
   const RecLayout l = rec_layout(d.k, d.S, INIT);
   char* rec = d.rec + (size_t)j * d.rec_bytes;
   Draws r(d.seed, (uint32_t)g, (uint32_t)j);
@@ -279,7 +292,7 @@ __global__ void __launch_bounds__(128) k_spec(EaDev d) {
     const bool cross = (double)r(k) * 0x1p-32 < d.pc;
     const long long prev = (long long)(g - 1) * d.P;
     // entrant slots e = c, c + nc, ... of this attempt's record
-    for (int e = c; e < 2 * k; e += nc) {
+    for (int e = c; e < 2 * k && v == 0; e += nc) {
       const int idx = (int)below(r(e < k ? e : k + 1 + (e - k)), P);
       const long long er = prev + idx;
       const int eL = d.len[er];
@@ -291,7 +304,8 @@ __global__ void __launch_bounds__(128) k_spec(EaDev d) {
       const uint16_t* src = d.seq + (size_t)er * d.S;
       for (int i = 0; i < eL; ++i) ec[i] = src[i];
     }
-    if (c == 0) reinterpret_cast<int32_t*>(rec + l.cross)[0] = cross ? 1 : 0;
+    if (c == 0 && v == 0) reinterpret_cast<int32_t*>(rec + l.cross)[0] = cross ? 1 : 0;
+    const int base = 2 * k + 1 + 5 * v;
     const int ia = (int)below(r(ta), P);
     const uint16_t* a = d.seq + (size_t)(prev + ia) * d.S;
     const int La = d.len[prev + ia];
@@ -301,8 +315,8 @@ __global__ void __launch_bounds__(128) k_spec(EaDev d) {
       const int ib = (int)below(r(k + 1 + tb), P);
       const uint16_t* b = d.seq + (size_t)(prev + ib) * d.S;
       const int Lb = d.len[prev + ib];
-      const int cut_a = 1 + (int)below(r(2 * k + 1), (uint32_t)La);
-      const int cut_b = (int)below(r(2 * k + 2), (uint32_t)Lb);
+      const int cut_a = 1 + (int)below(r(base), (uint32_t)La);
+      const int cut_b = (int)below(r(base + 1), (uint32_t)Lb);
       uint16_t y[kMaxLen];
       int Ly = 0;
       for (int i = 0; i < cut_a; ++i) y[Ly++] = a[i];
@@ -315,7 +329,14 @@ __global__ void __launch_bounds__(128) k_spec(EaDev d) {
         L = Ly;
       }
     }
-    mutate(x, L, d.C, d.Lmin, d.Lmax, r(2 * k + 3), r(2 * k + 4), r(2 * k + 5));
+    mutate(x, L, d.C, d.Lmin, d.Lmax, r(base + 2), r(base + 3), r(base + 4));
+  }
+  if (SCREEN) {
+    const long long row = jc * V + v;
+    uint16_t* out = d.var_seq + (size_t)row * d.S;
+    for (int i = 0; i < L; ++i) out[i] = x[i];
+    d.var_len[row] = L;
+    return;
   }
   uint16_t* out = reinterpret_cast<uint16_t*>(rec + l.ccols) + (size_t)c * d.S;
   for (int i = 0; i < L; ++i) out[i] = x[i];
@@ -323,6 +344,77 @@ __global__ void __launch_bounds__(128) k_spec(EaDev d) {
   const unsigned long long h = seq_hash(x, L);
   reinterpret_cast<unsigned long long*>(rec + l.chash)[c] = h;
   reinterpret_cast<int32_t*>(rec + l.ctabu)[c] = INIT ? 0 : (tabu_contains(d, h, x, L) ? 1 : 0);
+}
+
+// Pseudo scores (testing the screening logic without a model): candidate v of
+// (attempt j, outcome c) scores word 0 of Philox(j, g, 65536 + c * V + v) >> 8.
+__global__ void __launch_bounds__(256) k_pseudo_score(EaDev d) {
+  if (*(volatile int32_t*)&d.ctl->stop) return;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)d.J * d.ncombo * d.V) return;
+  const int v = (int)(t % d.V);
+  const long long jc = t / d.V;
+  const int j = (int)(jc / d.ncombo), c = (int)(jc % d.ncombo);
+  uint32_t w[4];
+  philox_block((uint32_t)j, (uint32_t)d.ctl->gen, 65536u + (uint32_t)(c * d.V + v), d.seed, w);
+  d.var_score[t] = (float)(w[0] >> 8);
+}
+
+// k_pick: the candidates of each (attempt, outcome) are visited by decreasing
+// score (ties: lower v; NaN after every number) and the first one that is not
+// in the tabu list becomes the record's child; when all are, the
+// best-scoring one does (a tabu hit).  The tabu list is the one left by the
+// previous generation: this generation's own duplicates are the builder's.
+__global__ void __launch_bounds__(128) k_pick(EaDev d) {
+  if (*(volatile int32_t*)&d.ctl->stop) return;
+  const long long jc = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (jc >= (long long)d.J * d.ncombo) return;
+  const int j = (int)(jc / d.ncombo), c = (int)(jc % d.ncombo);
+  const float* sc = d.var_score + jc * d.V;
+  uint32_t seen = 0u;
+  int first = -1, chosen = -1;
+  unsigned long long chosen_h = 0ull, first_h = 0ull;
+  for (int r = 0; r < d.V && chosen < 0; ++r) {
+    int bv = -1;
+    float bs = 0.f;
+    for (int v = 0; v < d.V; ++v) {
+      if ((seen >> v) & 1u) continue;
+      float x = sc[v];
+      if (x != x) x = -INFINITY;
+      if (bv < 0 || x > bs) {
+        bv = v;
+        bs = x;
+      }
+    }
+    seen |= 1u << bv;
+    const long long row = jc * d.V + bv;
+    const int L = d.var_len[row];
+    const uint16_t* x = d.var_seq + (size_t)row * d.S;
+    const unsigned long long h = seq_hash(x, L);
+    if (first < 0) {
+      first = bv;
+      first_h = h;
+    }
+    if (!tabu_contains(d, h, x, L)) {
+      chosen = bv;
+      chosen_h = h;
+    }
+  }
+  const bool hit = chosen < 0;
+  if (hit) {
+    chosen = first;
+    chosen_h = first_h;
+  }
+  const long long row = jc * d.V + chosen;
+  const int L = d.var_len[row];
+  const uint16_t* x = d.var_seq + (size_t)row * d.S;
+  const RecLayout l = rec_layout(d.k, d.S, false);
+  char* rec = d.rec + (size_t)j * d.rec_bytes;
+  uint16_t* out = reinterpret_cast<uint16_t*>(rec + l.ccols) + (size_t)c * d.S;
+  for (int i = 0; i < L; ++i) out[i] = x[i];
+  reinterpret_cast<int32_t*>(rec + l.cL)[c] = L;
+  reinterpret_cast<unsigned long long*>(rec + l.chash)[c] = chosen_h;
+  reinterpret_cast<int32_t*>(rec + l.ctabu)[c] = hit ? 1 : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -1080,6 +1172,11 @@ struct EaState {
   EvalArgs eargs{};
   ebic_eval_tuning_t tuning{};   // evaluation shape chosen at Step 1
   bool initialised = false;
+  // offspring screening
+  ebic_surrogate_ctx* sur = nullptr;   // attached surrogate (EBIC_SCREEN_SURROGATE)
+  long long var_rows = 0;
+  DevBuf var_seq, var_len, var_score, act;
+  int32_t launches_per_gen = 5;
 
   void release() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -1087,8 +1184,10 @@ struct EaState {
     exec = nullptr;
     graph = nullptr;
     for (DevBuf* b : {&seq, &len, &inc, &dec, &fit, &lnf, &tkey, &tref, &rec, &list_ref,
-                      &list_f, &pow_tab, &pow_off, &c_over_L, &ctl, &gather})
+                      &list_f, &pow_tab, &pow_off, &c_over_L, &ctl, &gather, &var_seq, &var_len,
+                      &var_score, &act})
       b->release();
+    sur = nullptr;
     h_ctl.release();
     h_gather.release();
     initialised = false;
@@ -1127,16 +1226,41 @@ static ebic_status validate(const ebic_ctx* h, const ebic_params_t* p) {
   return EBIC_OK;
 }
 
+// Attempt records of one Steps 2-5 generation: k_spec, or (screening) the
+// candidates, their scores and the pick.  Returns the launch count in *n.
+static ebic_status launch_records(EaState* st, cudaStream_t s, int* n) {
+  const EaDev& d = st->dev;
+  const long long jc = (long long)st->J * st->ncombo;
+  if (d.V <= 1) {
+    k_spec<false, false><<<(unsigned)((jc + 127) / 128), 128, 0, s>>>(d);
+    *n = 1;
+    return EBIC_OK;
+  }
+  const long long rows = jc * d.V;
+  k_spec<false, true><<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(d);
+  int ns = 1;
+  if (d.screen == EBIC_SCREEN_SURROGATE) {
+    EBIC_TRY(sur_forward_scores(st->sur, d.var_seq, d.var_len, d.S, (int32_t)rows, st->act.ptr,
+                                d.var_score, s, &ns));
+  } else {
+    k_pseudo_score<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(d);
+  }
+  k_pick<<<(unsigned)((jc + 127) / 128), 128, 0, s>>>(d);
+  *n = 2 + ns;
+  EBIC_CUDA_TRY(cudaGetLastError());
+  return EBIC_OK;
+}
+
 static ebic_status launch_generation(ebic_ctx* h, EaState* st, bool init, cudaStream_t s) {
   const EaDev& d = st->dev;
-  const int nc = init ? 1 : st->ncombo;
-  const long long threads = (long long)st->J * nc;
-  const unsigned sblocks = (unsigned)((threads + 127) / 128);
   if (init) {
-    k_spec<true><<<sblocks, 128, 0, s>>>(d);
+    const unsigned sblocks = (unsigned)((st->J + 127) / 128);
+    k_spec<true, false><<<sblocks, 128, 0, s>>>(d);
     k_build<true><<<1, kBuildThreads, st->smem_build, s>>>(d, st->hmask, st->kB);
   } else {
-    k_spec<false><<<sblocks, 128, 0, s>>>(d);
+    int nrec = 0;
+    EBIC_TRY(launch_records(st, s, &nrec));
+    st->launches_per_gen = nrec + 4;
     k_build<false><<<1, kBuildThreads, st->smem_build, s>>>(d, st->hmask, st->kB);
   }
   k_tabu_insert<<<(unsigned)((st->p.pop_size + 255) / 256), 256, 0, s>>>(d);
@@ -1262,6 +1386,33 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
   d.c_over_L = st->c_over_L.as<float>();
   d.ctl = st->ctl.as<Ctl>();
 
+  // Offspring screening: candidate buffers (zeroed, so that a pass over rows
+  // no k_spec has written yet reads empty series), scores, activations.
+  d.V = 1;
+  d.screen = EBIC_SCREEN_OFF;
+  if (h->screen_mode != EBIC_SCREEN_OFF && h->screen_v > 1) {
+    const int32_t V = h->screen_v;
+    if (h->screen_mode == EBIC_SCREEN_SURROGATE && !h->screen_sur)
+      return fail(EBIC_ERR_STATE, "surrogate screening without a surrogate");
+    const long long rows = (long long)st->J * st->ncombo * V;
+    if (rows > (1ll << 22))
+      return fail(EBIC_ERR_ARG, "screening needs %lld candidate rows per generation (max %lld)",
+                  rows, 1ll << 22);
+    EBIC_TRY(st->var_seq.reserve_zeroed((size_t)rows * st->S * sizeof(uint16_t), s));
+    EBIC_TRY(st->var_len.reserve_zeroed((size_t)rows * sizeof(int32_t), s));
+    EBIC_TRY(st->var_score.reserve((size_t)rows * sizeof(float)));
+    if (h->screen_mode == EBIC_SCREEN_SURROGATE) {
+      EBIC_TRY(st->act.reserve(sur_act_bytes(rows)));
+      st->sur = h->screen_sur;
+    }
+    st->var_rows = rows;
+    d.V = V;
+    d.screen = h->screen_mode;
+    d.var_seq = st->var_seq.as<uint16_t>();
+    d.var_len = st->var_len.as<int32_t>();
+    d.var_score = st->var_score.as<float>();
+  }
+
   st->apop.seq = d.seq;
   st->apop.len = d.len;
   st->apop.stride = st->S;
@@ -1310,7 +1461,7 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
   // Step 1: initial population, evaluation (autotuned once), top-rank list.
   const EaDev& dd = st->dev;
   const unsigned sblocks = (unsigned)((st->J + 127) / 128);
-  k_spec<true><<<sblocks, 128, 0, s>>>(dd);
+  k_spec<true, false><<<sblocks, 128, 0, s>>>(dd);
   k_build<true><<<1, kBuildThreads, st->smem_build, s>>>(dd, st->hmask, st->kB);
   k_tabu_insert<<<(unsigned)((P + 255) / 256), 256, 0, s>>>(dd);
   count_launches(3);
@@ -1359,7 +1510,7 @@ static ebic_status run_step(ebic_ctx* h, int32_t generations, ebic_stats_t* stat
   while (left > 0) {
     const int32_t chunk = std::min<int32_t>(left, 64);
     for (int32_t i = 0; i < chunk; ++i) EBIC_CUDA_TRY(cudaGraphLaunch(st->exec, s));
-    count_launches((uint64_t)chunk * 5);
+    count_launches((uint64_t)chunk * st->launches_per_gen);
     left -= chunk;
     EBIC_TRY(read_ctl(st, s, &c));
     if (c.stop) break;
@@ -1369,6 +1520,21 @@ static ebic_status run_step(ebic_ctx* h, int32_t generations, ebic_stats_t* stat
   if (c.stop_reason == 3) return fail(EBIC_ERR_DEVICE, "internal EA error (code 3)");
   if (c.stop_reason == 4)
     return fail(EBIC_ERR_TIMEOUT, "a bounded wait for streamed attempt records expired");
+  return EBIC_OK;
+}
+
+ebic_status ea_archive(ebic_ctx* h, const uint16_t** seq, const int32_t** len, const double** fit,
+                       long long* n, int32_t* stride) {
+  EaState* st = h->ea;
+  if (!st || !st->initialised) return fail(EBIC_ERR_STATE, "the handle has no run");
+  Ctl c{};
+  EBIC_TRY(read_ctl(st, h->stream, &c));
+  *seq = st->seq.as<uint16_t>();
+  *len = st->len.as<int32_t>();
+  *fit = st->fit.as<double>();
+  *stride = st->S;
+  // generations 0 .. c.gen - 1 are evaluated (c.gen counts Step 1 as one)
+  *n = std::min<long long>((long long)c.gen * st->p.pop_size, st->entries);
   return EBIC_OK;
 }
 
@@ -1395,7 +1561,7 @@ static ebic_status run_step_async(ebic_ctx* h, int32_t generations, cudaStream_t
   if (!st || !st->initialised) return fail(EBIC_ERR_STATE, "ebic_run_init has not run");
   if (generations < 0) return fail(EBIC_ERR_ARG, "negative generation count");
   for (int32_t i = 0; i < generations; ++i) EBIC_CUDA_TRY(cudaGraphLaunch(st->exec, s));
-  count_launches((uint64_t)generations * 5);
+  count_launches((uint64_t)generations * st->launches_per_gen);
   return EBIC_OK;
 }
 
@@ -1407,9 +1573,14 @@ static ebic_status run_step_profiled(ebic_ctx* h, float* us) {
   cudaEvent_t ev[6];
   for (int i = 0; i < 6; ++i) EBIC_CUDA_TRY(cudaEventCreate(&ev[i]));
   const EaDev& d = st->dev;
-  const long long threads = (long long)st->J * st->ncombo;
   cudaEventRecord(ev[0], s);
-  k_spec<false><<<(unsigned)((threads + 127) / 128), 128, 0, s>>>(d);
+  int nrec = 0;
+  ebic_status rs = launch_records(st, s, &nrec);
+  if (rs != EBIC_OK) {
+    cudaStreamSynchronize(s);
+    for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+    return rs;
+  }
   cudaEventRecord(ev[1], s);
   k_build<false><<<1, kBuildThreads, st->smem_build, s>>>(d, st->hmask, st->kB);
   cudaEventRecord(ev[2], s);
@@ -1422,7 +1593,7 @@ static ebic_status run_step_profiled(ebic_ctx* h, float* us) {
   cudaEventRecord(ev[4], s);
   k_rank<<<1, kRankThreads, st->smem_rank, s>>>(d, st->Pp);
   cudaEventRecord(ev[5], s);
-  count_launches(4);
+  count_launches((uint64_t)(3 + nrec));
   cudaError_t e = cudaEventSynchronize(ev[5]);
   for (int i = 0; i < 5 && us; ++i) {
     float ms = 0.f;
@@ -1532,6 +1703,24 @@ ebic_status ebic_run_step_async(ebic_handle h, int32_t generations, void* stream
 ebic_status ebic_run_step_profiled(ebic_handle h, float* kernel_us) {
   if (!h) return fail(EBIC_ERR_ARG, "null handle");
   return run_step_profiled(h, kernel_us);
+}
+
+ebic_status ebic_run_screen(ebic_handle h, ebic_surrogate s, int32_t oversample, int32_t mode) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  if (oversample < 1 || oversample > 16)
+    return fail(EBIC_ERR_ARG, "oversample %d outside [1, 16]", oversample);
+  if (mode != EBIC_SCREEN_OFF && mode != EBIC_SCREEN_SURROGATE && mode != EBIC_SCREEN_PSEUDO)
+    return fail(EBIC_ERR_ARG, "bad screening mode %d", mode);
+  if (mode == EBIC_SCREEN_SURROGATE && !s) return fail(EBIC_ERR_ARG, "surrogate mode needs a surrogate");
+  if (mode == EBIC_SCREEN_SURROGATE && sur_columns(s) != h->C)
+    return fail(EBIC_ERR_ARG, "the surrogate has %d columns, the matrix %d", sur_columns(s), h->C);
+  // the handle holds one reference to its screening surrogate
+  if (h->screen_sur) sur_attach(h->screen_sur, -1);
+  h->screen_sur = mode == EBIC_SCREEN_SURROGATE ? s : nullptr;
+  if (h->screen_sur) sur_attach(h->screen_sur, +1);
+  h->screen_v = oversample;
+  h->screen_mode = mode;
+  return EBIC_OK;
 }
 
 ebic_status ebic_get_toprank(ebic_handle h, int32_t* offsets, int32_t* cols, double* fitness,

@@ -76,6 +76,10 @@ struct ebic_ctx {
   ebic::DevBuf st_off, st_cols, st_inc, st_dec, st_fit;   // staging for host calls
   ebic::HostBuf h_stage;          // pinned staging for host calls
   ebic::EaState* ea = nullptr;
+  // offspring screening applied by the next ebic_run_init
+  ebic_surrogate_ctx* screen_sur = nullptr;
+  int32_t screen_v = 1;
+  int32_t screen_mode = 0;
 };
 
 namespace ebic {
@@ -163,6 +167,20 @@ int32_t resolve_path(ebic_ctx* h);
 ebic_status build_pair_table(ebic_ctx* h, cudaStream_t s);
 
 void ea_release(ebic_ctx* h);
+// The evaluated part of the handle's run archive (device pointers; entry e is
+// seq[e * stride ..], len[e], fit[e]; n entries).  Synchronises the stream.
+ebic_status ea_archive(ebic_ctx* h, const uint16_t** seq, const int32_t** len, const double** fit,
+                       long long* n, int32_t* stride);
+
+// Surrogate forward pass for screening (ebic_surrogate.cu).  act holds
+// sur_act_bytes(n) bytes of activations; y[n] receives the predictions.
+// Launches only (no allocation, no synchronisation): safe under stream capture.
+size_t sur_act_bytes(long long rows);
+ebic_status sur_forward_scores(ebic_surrogate_ctx* s, const uint16_t* seq, const int32_t* len,
+                               int32_t stride, int32_t n, void* act, float* y, cudaStream_t st,
+                               int* launches);
+int32_t sur_columns(const ebic_surrogate_ctx* s);
+void sur_attach(ebic_surrogate_ctx* s, int delta);
 // Adds n to the process-wide count of kernels this library launched.
 void count_launches(uint64_t n);
 

@@ -496,6 +496,8 @@ static void destroy(ebic_ctx* h) {
   DeviceGuard g(h->device);
   if (h->stream) cudaStreamSynchronize(h->stream);
   ea_release(h);
+  if (h->screen_sur) sur_attach(h->screen_sur, -1);
+  h->screen_sur = nullptr;
   if (h->A_c) cudaFree(h->A_c);
   if (h->LN) cudaFree(h->LN);
   if (h->LT) cudaFree(h->LT);

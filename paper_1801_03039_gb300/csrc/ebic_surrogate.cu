@@ -1,0 +1,833 @@
+// Fitness surrogate: a small MLP that predicts a series' standardised
+// log-fitness from sum-pooled column features, trained on (series, exact
+// fitness) pairs that EBIC runs log, and used to pre-screen oversampled
+// offspring.  Not part of the paper: the exact evaluator (Eq. (1) on exact
+// support) still scores every individual that enters a population.
+//
+//   features  x[0:64] = sum of learned column embeddings, x[64] = mean column
+//             mean, x[65] = mean column standard deviation, x[66] = length /
+//             len_scale, x[67:80] = 0
+//   h1 = relu(x W1 + b1), h2 = relu(h1 W2 + b2), y = h2 . w3 + b3
+//
+// Forward and backward are this file's kernels: bf16 operands on the tensor
+// cores (mma.sync m16n8k16, fp32 accumulation) with the bias / ReLU / ReLU-mask
+// epilogues fused into the GEMM, fp32 master weights, Adam.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "ebic_internal.cuh"
+
+namespace ebic {
+
+constexpr int kF = 80;     // feature width (67 used, padded to a multiple of 16)
+constexpr int kEmb = 64;
+constexpr int kH = 256;
+
+typedef __nv_bfloat16 bf16;
+
+// ---------------------------------------------------------------------------
+// column statistics of the handle's matrix (mean, population sd; NaN skipped)
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_colstats(const float* __restrict__ A_c, int32_t R,
+                                                  int32_t R_pad, float* mean, float* sd) {
+  const int c = blockIdx.x;
+  const float* col = A_c + (size_t)c * R_pad;
+  double s = 0.0, s2 = 0.0;
+  long long n = 0;
+  for (int r = threadIdx.x; r < R; r += blockDim.x) {
+    const float v = col[r];
+    if (v == v) {
+      s += v;
+      s2 += (double)v * v;
+      ++n;
+    }
+  }
+  __shared__ double ss[256], ss2[256];
+  __shared__ long long sn[256];
+  ss[threadIdx.x] = s;
+  ss2[threadIdx.x] = s2;
+  sn[threadIdx.x] = n;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      ss[threadIdx.x] += ss[threadIdx.x + o];
+      ss2[threadIdx.x] += ss2[threadIdx.x + o];
+      sn[threadIdx.x] += sn[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    const double m = sn[0] ? ss[0] / (double)sn[0] : 0.0;
+    const double var = sn[0] ? ss2[0] / (double)sn[0] - m * m : 0.0;
+    mean[c] = (float)m;
+    sd[c] = (float)sqrt(var > 0.0 ? var : 0.0);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// features: one warp per series (lanes over the 64 embedding dimensions x 2)
+// ---------------------------------------------------------------------------
+// (a length outside [0, stride] is clamped and a column >= C skipped, so that
+// stale or unused rows read nothing out of bounds)
+__global__ void __launch_bounds__(256)
+k_features(const uint16_t* __restrict__ seq, const int32_t* __restrict__ len, int32_t stride,
+           const int32_t* __restrict__ idx, int32_t n, int32_t C, const float* __restrict__ emb,
+           const float* __restrict__ cmean, const float* __restrict__ csd, float len_scale,
+           bf16* __restrict__ x) {
+  const int lane = threadIdx.x & 31;
+  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (b >= n) return;
+  const long long r = idx ? (long long)idx[b] : b;
+  const int L = min(max(len[r], 0), stride);
+  const uint16_t* s = seq + (size_t)r * stride;
+  float e0 = 0.f, e1 = 0.f, m = 0.f, d = 0.f;
+  for (int i = 0; i < L; ++i) {
+    const int c = s[i];
+    if (c >= C) continue;
+    e0 += emb[(size_t)c * kEmb + lane];
+    e1 += emb[(size_t)c * kEmb + 32 + lane];
+    m += cmean[c];
+    d += csd[c];
+  }
+  bf16* o = x + (size_t)b * kF;
+  o[lane] = __float2bfloat16_rn(e0);
+  o[32 + lane] = __float2bfloat16_rn(e1);
+  if (lane < 16) {
+    float v = 0.f;
+    if (lane == 0) v = L ? m / (float)L : 0.f;
+    if (lane == 1) v = L ? d / (float)L : 0.f;
+    if (lane == 2) v = (float)L / len_scale;
+    o[64 + lane] = __float2bfloat16_rn(v);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// GEMM on the tensor cores: C[M x N] = op(A)[M x K] . op(B)[K x N], bf16
+// operands, fp32 accumulation (mma.sync m16n8k16).  op(A)(m, k) = A[m*lda+k]
+// (TA: A[k*lda+m]); op(B)(k, n) = B[k*ldb+n] (TB: B[n*ldb+k]).  CTA tile
+// 64 x 64 x 32, four warps of 32 x 32.  gridDim.z splits K (fp32 atomic
+// accumulation, EPI_F32_ADD only).  grid = (M tiles, N tiles, K splits).
+// ---------------------------------------------------------------------------
+enum { EPI_BIAS_RELU_BF16 = 0, EPI_MASK_BF16 = 1, EPI_F32 = 2, EPI_F32_ADD = 3 };
+constexpr int kBM = 64, kBN = 64, kBK = 32;
+
+__device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+template <bool TA, bool TB, int EPI>
+__global__ void __launch_bounds__(128)
+k_gemm_bf16(int M, int N, int K, const bf16* __restrict__ A, int lda, const bf16* __restrict__ B,
+            int ldb, const float* __restrict__ bias, const bf16* __restrict__ mask, int ldm,
+            float* __restrict__ Cf, bf16* __restrict__ Cb, int ldc) {
+  __shared__ bf16 As[kBM][kBK + 8];    // (m, k)
+  __shared__ bf16 Bs[kBN][kBK + 8];    // (n, k)
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;   // M can exceed 65535 tiles
+  const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
+  const int g = lane >> 2, tq = lane & 3;
+  const int ksplit = gridDim.z;
+  const int kchunk = ((K + ksplit - 1) / ksplit + kBK - 1) / kBK * kBK;
+  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+  const bf16 zero = __float2bfloat16_rn(0.f);
+  for (int k0 = kbeg; k0 < kend; k0 += kBK) {
+    for (int e = tid; e < kBM * kBK; e += 128) {
+      const int mm = TA ? e % kBM : e / kBK, kk = TA ? e / kBM : e % kBK;
+      const int gm = m0 + mm, gk = k0 + kk;
+      As[mm][kk] = (gm < M && gk < kend) ? (TA ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk])
+                                         : zero;
+    }
+    for (int e = tid; e < kBN * kBK; e += 128) {
+      const int nn = TB ? e / kBK : e % kBN, kk = TB ? e % kBK : e / kBN;
+      const int gn = n0 + nn, gk = k0 + kk;
+      Bs[nn][kk] = (gn < N && gk < kend) ? (TB ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn])
+                                         : zero;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kBK; kk += 16) {
+      uint32_t a[2][4], bq[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const int r = wm + i * 16 + g;
+        a[i][0] = pack2(As[r][kk + tq * 2], As[r][kk + tq * 2 + 1]);
+        a[i][1] = pack2(As[r + 8][kk + tq * 2], As[r + 8][kk + tq * 2 + 1]);
+        a[i][2] = pack2(As[r][kk + 8 + tq * 2], As[r][kk + 8 + tq * 2 + 1]);
+        a[i][3] = pack2(As[r + 8][kk + 8 + tq * 2], As[r + 8][kk + 8 + tq * 2 + 1]);
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = wn + j * 8 + g;
+        bq[j][0] = pack2(Bs[c][kk + tq * 2], Bs[c][kk + tq * 2 + 1]);
+        bq[j][1] = pack2(Bs[c][kk + 8 + tq * 2], Bs[c][kk + 8 + tq * 2 + 1]);
+      }
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          asm volatile(
+              "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, "
+              "{%4,%5,%6,%7}, {%8,%9}, {%0,%1,%2,%3};\n"
+              : "+f"(acc[i][j][0]), "+f"(acc[i][j][1]), "+f"(acc[i][j][2]), "+f"(acc[i][j][3])
+              : "r"(a[i][0]), "r"(a[i][1]), "r"(a[i][2]), "r"(a[i][3]), "r"(bq[j][0]),
+                "r"(bq[j][1]));
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int m = m0 + wm + i * 16 + g + (q >= 2 ? 8 : 0);
+        const int n = n0 + wn + j * 8 + tq * 2 + (q & 1);
+        if (m >= M || n >= N) continue;
+        float v = acc[i][j][q];
+        if (EPI == EPI_BIAS_RELU_BF16) {
+          v = fmaxf(v + bias[n], 0.f);
+          Cb[(size_t)m * ldc + n] = __float2bfloat16_rn(v);
+        } else if (EPI == EPI_MASK_BF16) {
+          v = __bfloat162float(mask[(size_t)m * ldm + n]) > 0.f ? v : 0.f;
+          Cb[(size_t)m * ldc + n] = __float2bfloat16_rn(v);
+        } else if (EPI == EPI_F32) {
+          Cf[(size_t)m * ldc + n] = v;
+        } else {
+          atomicAdd(&Cf[(size_t)m * ldc + n], v);
+        }
+      }
+}
+
+// y = h2 . w3 + b3 (warp per row); with targets: loss sum and dy = 2 (y - t) / B
+__global__ void __launch_bounds__(256)
+k_out(const bf16* __restrict__ h2, const float* __restrict__ w3, const float* __restrict__ b3,
+      int n, float* __restrict__ y, const float* __restrict__ t, const int32_t* __restrict__ idx,
+      float* __restrict__ dy, float* __restrict__ loss_sum) {
+  const int lane = threadIdx.x & 31;
+  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (b >= n) return;
+  float s = 0.f;
+  for (int j = lane; j < kH; j += 32) s += __bfloat162float(h2[(size_t)b * kH + j]) * w3[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  s += b3[0];
+  if (lane == 0) {
+    y[b] = s;
+    if (t) {
+      const float tt = t[idx ? idx[b] : b];
+      const float r = s - tt;
+      dy[b] = 2.f * r / (float)n;
+      atomicAdd(loss_sum, r * r / (float)n);
+    }
+  }
+}
+
+// dh2[b][j] = dy[b] w3[j] [h2[b][j] > 0]  (bf16)
+__global__ void __launch_bounds__(256) k_dh2(const float* __restrict__ dy,
+                                             const float* __restrict__ w3,
+                                             const bf16* __restrict__ h2, int n,
+                                             bf16* __restrict__ dh2) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)n * kH) return;
+  const int b = (int)(i / kH), j = (int)(i % kH);
+  const float v = __bfloat162float(h2[i]) > 0.f ? dy[b] * w3[j] : 0.f;
+  dh2[i] = __float2bfloat16_rn(v);
+}
+
+// out[j] = sum_b scale[b] * X[b][j] for j < cols (scale = nullptr: 1);
+// one block per 32 columns, X bf16 (or fp32 via Xf)
+__global__ void __launch_bounds__(256)
+k_colsum(const bf16* __restrict__ Xb, const float* __restrict__ Xf, int n, int cols,
+         const float* __restrict__ scale, float* __restrict__ out) {
+  const int c = blockIdx.x * 32 + (threadIdx.x & 31);
+  const int r0 = threadIdx.x >> 5;
+  float s = 0.f;
+  if (c < cols)
+    for (int b = r0; b < n; b += 8) {
+      const float v = Xb ? __bfloat162float(Xb[(size_t)b * cols + c]) : Xf[(size_t)b * cols + c];
+      s += scale ? scale[b] * v : v;
+    }
+  __shared__ float red[8][33];
+  red[r0][threadIdx.x & 31] = s;
+  __syncthreads();
+  if (r0 == 0 && c < cols) {
+    float t = 0.f;
+    for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x & 31];
+    out[c] = t;
+  }
+}
+
+// dEmb[c] += dx[b][0:64] for every column c of series b
+__global__ void __launch_bounds__(256)
+k_emb_scatter(const uint16_t* __restrict__ seq, const int32_t* __restrict__ len, int32_t stride,
+              const int32_t* __restrict__ idx, int n, int32_t C, const float* __restrict__ dx,
+              float* __restrict__ demb) {
+  const int lane = threadIdx.x & 31;
+  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (b >= n) return;
+  const long long r = idx ? (long long)idx[b] : b;
+  const int L = min(max(len[r], 0), stride);
+  const uint16_t* s = seq + (size_t)r * stride;
+  const float g0 = dx[(size_t)b * kF + lane], g1 = dx[(size_t)b * kF + 32 + lane];
+  for (int i = 0; i < L; ++i) {
+    const int c = s[i];
+    if (c >= C) continue;
+    atomicAdd(&demb[(size_t)c * kEmb + lane], g0);
+    atomicAdd(&demb[(size_t)c * kEmb + 32 + lane], g1);
+  }
+}
+
+// Adam over one flat parameter array; optional bf16 copy of the result
+__global__ void __launch_bounds__(256)
+k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+       float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
+       float c2, bf16* __restrict__ copy) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float gi = g[i];
+  const float mi = b1 * m[i] + (1.f - b1) * gi;
+  const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+  m[i] = mi;
+  v[i] = vi;
+  const float pi = p[i] - lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  p[i] = pi;
+  if (copy) copy[i] = __float2bfloat16_rn(pi);
+}
+
+__global__ void k_to_bf16(const float* __restrict__ src, bf16* __restrict__ dst, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
+}
+
+// standardised log1p targets: t = (log1p(f) - mean) / sd
+__global__ void k_targets(const double* __restrict__ f, long long n, float mean, float sd,
+                          float* __restrict__ t) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) t[i] = (float)((log1p(f[i]) - (double)mean) / (double)sd);
+}
+
+__global__ void k_sum_log1p(const double* __restrict__ f, long long n, double* out) {
+  double s = 0.0, s2 = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double v = log1p(f[i]);
+    s += v;
+    s2 += v * v;
+  }
+  atomicAdd(&out[0], s);
+  atomicAdd(&out[1], s2);
+}
+
+// minibatch indices: idx[b] = floor(u * n), u from Philox-4x32-10 keyed by (seed, step)
+__global__ void k_sample(uint64_t seed, uint32_t step, long long n, int B, int32_t* idx) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= B) return;
+  uint32_t x0 = (uint32_t)b, x1 = step, x2 = 0x5EEDu, x3 = 0u;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint32_t lo0 = 0xD2511F53u * x0, hi0 = __umulhi(0xD2511F53u, x0);
+    const uint32_t lo1 = 0xCD9E8D57u * x2, hi1 = __umulhi(0xCD9E8D57u, x2);
+    const uint32_t y0 = hi1 ^ x1 ^ k0, y2 = hi0 ^ x3 ^ k1;
+    x0 = y0;
+    x1 = lo1;
+    x2 = y2;
+    x3 = lo0;
+  }
+  idx[b] = (int32_t)((((unsigned long long)x0 << 32 | x1) % (unsigned long long)n));
+}
+
+}  // namespace ebic
+
+using namespace ebic;
+
+struct ebic_surrogate_ctx {
+  int device = 0;
+  int32_t C = 0;
+  float len_scale = 64.f;
+  float t_mean = 0.f, t_sd = 1.f;
+  int32_t steps_done = 0;
+  int32_t attached = 0;        // runs screening with this surrogate
+  uint64_t seed = 0;
+  ebic_handle h = nullptr;
+  cudaStream_t stream = nullptr;
+  // fp32 master parameters, gradients and Adam moments: one flat buffer each,
+  // Emb[C * 64] | W1[80 * 256] | b1[256] | W2[256 * 256] | b2[256] | w3[256] | b3[1]
+  long long n_par = 0;
+  long long o_emb = 0, o_w1 = 0, o_b1 = 0, o_w2 = 0, o_b2 = 0, o_w3 = 0, o_b3 = 0;
+  DevBuf par, grad, mom, vel, w1b, w2b, cmean, csd;
+  // training activations (capacity rows)
+  int32_t cap = 0;
+  DevBuf act, dh1, dh2, dx, y, dy, idx, loss, tgt, tmp;
+  // training log: series [log_n][kLogStride], lengths, exact fitness
+  long long log_n = 0, log_cap = 0;
+  DevBuf log_seq, log_len, log_fit;
+};
+
+namespace ebic {
+
+constexpr int kLogStride = EBIC_MAX_EA_LEN;
+
+// x [rows][80] | h1 [rows][256] | h2 [rows][256], bf16, each 256-byte aligned
+static inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+size_t sur_act_bytes(long long rows) {
+  const size_t r = (size_t)rows;
+  return round256(r * kF * sizeof(bf16)) + 2 * round256(r * kH * sizeof(bf16));
+}
+struct ActView {
+  bf16 *x, *h1, *h2;
+};
+static ActView act_view(void* base, long long rows) {
+  char* p = static_cast<char*>(base);
+  ActView a;
+  a.x = reinterpret_cast<bf16*>(p);
+  p += round256((size_t)rows * kF * sizeof(bf16));
+  a.h1 = reinterpret_cast<bf16*>(p);
+  p += round256((size_t)rows * kH * sizeof(bf16));
+  a.h2 = reinterpret_cast<bf16*>(p);
+  return a;
+}
+
+int32_t sur_columns(const ebic_surrogate_ctx* s) { return s->C; }
+void sur_attach(ebic_surrogate_ctx* s, int delta) { s->attached += delta; }
+
+static ebic_status sur_reserve(ebic_surrogate_ctx* s, int32_t rows) {
+  if (rows <= s->cap) return EBIC_OK;
+  const size_t r = (size_t)rows;
+  EBIC_TRY(s->act.reserve(sur_act_bytes(rows)));
+  EBIC_TRY(s->dh1.reserve(r * kH * sizeof(bf16)));
+  EBIC_TRY(s->dh2.reserve(r * kH * sizeof(bf16)));
+  EBIC_TRY(s->dx.reserve(r * kF * sizeof(float)));
+  EBIC_TRY(s->y.reserve(r * sizeof(float)));
+  EBIC_TRY(s->dy.reserve(r * sizeof(float)));
+  EBIC_TRY(s->idx.reserve(r * sizeof(int32_t)));
+  s->cap = rows;
+  return EBIC_OK;
+}
+
+template <bool TA, bool TB, int EPI>
+static void gemm(int M, int N, int K, const bf16* A, int lda, const bf16* B, int ldb,
+                 const float* bias, const bf16* mask, int ldm, float* Cf, bf16* Cb, int ldc,
+                 int ksplit, cudaStream_t st) {
+  dim3 grid((unsigned)((M + kBM - 1) / kBM), (unsigned)((N + kBN - 1) / kBN), (unsigned)ksplit);
+  k_gemm_bf16<TA, TB, EPI><<<grid, 128, 0, st>>>(M, N, K, A, lda, B, ldb, bias, mask, ldm, Cf,
+                                                  Cb, ldc);
+}
+
+// Features and both hidden layers of n series (rows idx[b], or 0 .. n - 1):
+// 3 launches.
+static void sur_hidden(ebic_surrogate_ctx* s, const uint16_t* seq, const int32_t* len,
+                       int32_t stride, const int32_t* idx, int32_t n, const ActView& a,
+                       cudaStream_t st) {
+  const float* P = s->par.as<float>();
+  k_features<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(seq, len, stride, idx, n, s->C,
+                                                      P + s->o_emb, s->cmean.as<float>(),
+                                                      s->csd.as<float>(), s->len_scale, a.x);
+  gemm<false, false, EPI_BIAS_RELU_BF16>(n, kH, kF, a.x, kF, s->w1b.as<bf16>(), kH, P + s->o_b1,
+                                         nullptr, 0, nullptr, a.h1, kH, 1, st);
+  gemm<false, false, EPI_BIAS_RELU_BF16>(n, kH, kH, a.h1, kH, s->w2b.as<bf16>(), kH, P + s->o_b2,
+                                         nullptr, 0, nullptr, a.h2, kH, 1, st);
+}
+
+ebic_status sur_forward_scores(ebic_surrogate_ctx* s, const uint16_t* seq, const int32_t* len,
+                               int32_t stride, int32_t n, void* act, float* y, cudaStream_t st,
+                               int* launches) {
+  if (n <= 0) {
+    if (launches) *launches = 0;
+    return EBIC_OK;
+  }
+  const ActView a = act_view(act, n);
+  sur_hidden(s, seq, len, stride, nullptr, n, a, st);
+  const float* P = s->par.as<float>();
+  k_out<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(a.h2, P + s->o_w3, P + s->o_b3, n, y, nullptr,
+                                                 nullptr, nullptr, nullptr);
+  if (launches) *launches = 4;
+  EBIC_CUDA_TRY(cudaGetLastError());
+  return EBIC_OK;
+}
+
+// One training step on batch rows idx (device; nullptr: rows 0 .. B - 1);
+// gradients are left in s->grad.
+static ebic_status sur_step(ebic_surrogate_ctx* s, const uint16_t* seq, const int32_t* len,
+                            int32_t stride, const float* t, const int32_t* idx, int32_t B,
+                            float lr, bool update, cudaStream_t st) {
+  EBIC_TRY(sur_reserve(s, B));
+  const ActView a = act_view(s->act.ptr, B);
+  sur_hidden(s, seq, len, stride, idx, B, a, st);
+  float* P = s->par.as<float>();
+  float* G = s->grad.as<float>();
+  EBIC_CUDA_TRY(cudaMemsetAsync(G, 0, (size_t)s->n_par * sizeof(float), st));
+  EBIC_CUDA_TRY(cudaMemsetAsync(s->loss.ptr, 0, sizeof(float), st));
+  const unsigned wb = (unsigned)((B + 7) / 8);
+  k_out<<<wb, 256, 0, st>>>(a.h2, P + s->o_w3, P + s->o_b3, B, s->y.as<float>(), t, idx,
+                            s->dy.as<float>(), s->loss.as<float>());
+  // output layer
+  k_colsum<<<(kH + 31) / 32, 256, 0, st>>>(a.h2, nullptr, B, kH, s->dy.as<float>(), G + s->o_w3);
+  k_colsum<<<1, 256, 0, st>>>(nullptr, s->dy.as<float>(), B, 1, nullptr, G + s->o_b3);
+  const long long nb = (long long)B * kH;
+  k_dh2<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(s->dy.as<float>(), P + s->o_w3, a.h2, B,
+                                                      s->dh2.as<bf16>());
+  // layer 2: dW2 = h1^T dh2, db2, dh1 = (dh2 W2^T) [h1 > 0]
+  const int ks = std::max(1, std::min(32, B / 256));
+  gemm<true, false, EPI_F32_ADD>(kH, kH, B, a.h1, kH, s->dh2.as<bf16>(), kH, nullptr, nullptr, 0,
+                                 G + s->o_w2, nullptr, kH, ks, st);
+  k_colsum<<<(kH + 31) / 32, 256, 0, st>>>(s->dh2.as<bf16>(), nullptr, B, kH, nullptr,
+                                           G + s->o_b2);
+  gemm<false, true, EPI_MASK_BF16>(B, kH, kH, s->dh2.as<bf16>(), kH, s->w2b.as<bf16>(), kH,
+                                   nullptr, a.h1, kH, nullptr, s->dh1.as<bf16>(), kH, 1, st);
+  // layer 1: dW1 = x^T dh1, db1, dx = dh1 W1^T, then the embedding rows
+  gemm<true, false, EPI_F32_ADD>(kF, kH, B, a.x, kF, s->dh1.as<bf16>(), kH, nullptr, nullptr, 0,
+                                 G + s->o_w1, nullptr, kH, ks, st);
+  k_colsum<<<(kH + 31) / 32, 256, 0, st>>>(s->dh1.as<bf16>(), nullptr, B, kH, nullptr,
+                                           G + s->o_b1);
+  gemm<false, true, EPI_F32>(B, kF, kH, s->dh1.as<bf16>(), kH, s->w1b.as<bf16>(), kH, nullptr,
+                             nullptr, 0, s->dx.as<float>(), nullptr, kF, 1, st);
+  k_emb_scatter<<<wb, 256, 0, st>>>(seq, len, stride, idx, B, s->C, s->dx.as<float>(),
+                                    G + s->o_emb);
+  count_launches(14);
+  if (update) {
+    s->steps_done += 1;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = (float)(1.0 - std::pow(0.9, (double)s->steps_done));
+    const float c2 = (float)(1.0 - std::pow(0.999, (double)s->steps_done));
+    struct Seg {
+      long long o, n;
+      bf16* copy;
+    } segs[] = {{s->o_emb, s->o_w1 - s->o_emb, nullptr},
+                {s->o_w1, (long long)kF * kH, s->w1b.as<bf16>()},
+                {s->o_b1, kH, nullptr},
+                {s->o_w2, (long long)kH * kH, s->w2b.as<bf16>()},
+                {s->o_b2, kH + kH + 1, nullptr}};   // b2 | w3 | b3 are contiguous
+    for (const Seg& g : segs) {
+      k_adam<<<(unsigned)((g.n + 255) / 256), 256, 0, st>>>(
+          P + g.o, G + g.o, s->mom.as<float>() + g.o, s->vel.as<float>() + g.o, g.n, lr, b1, b2,
+          1e-8f, c1, c2, g.copy);
+    }
+    count_launches(5);
+  }
+  EBIC_CUDA_TRY(cudaGetLastError());
+  return EBIC_OK;
+}
+
+static ebic_status refresh_copies(ebic_surrogate_ctx* s, cudaStream_t st) {
+  const float* P = s->par.as<float>();
+  k_to_bf16<<<(kF * kH + 255) / 256, 256, 0, st>>>(P + s->o_w1, s->w1b.as<bf16>(),
+                                                   (long long)kF * kH);
+  k_to_bf16<<<(kH * kH + 255) / 256, 256, 0, st>>>(P + s->o_w2, s->w2b.as<bf16>(),
+                                                   (long long)kH * kH);
+  count_launches(2);
+  EBIC_CUDA_TRY(cudaGetLastError());
+  return EBIC_OK;
+}
+
+// Deterministic initial weights: Box-Muller normals on a splitmix64 stream.
+static void init_weights(ebic_surrogate_ctx* s, std::vector<float>& p) {
+  uint64_t z = s->seed ^ 0x9E3779B97F4A7C15ull;
+  auto unif = [&]() {
+    z += 0x9E3779B97F4A7C15ull;
+    uint64_t q = z;
+    q = (q ^ (q >> 30)) * 0xBF58476D1CE4E5B9ull;
+    q = (q ^ (q >> 27)) * 0x94D049BB133111EBull;
+    q ^= q >> 31;
+    return ((double)(q >> 11) + 0.5) * 0x1p-53;
+  };
+  auto nrm = [&]() {
+    const double u1 = unif(), u2 = unif();
+    return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+  };
+  p.assign((size_t)s->n_par, 0.f);
+  for (long long i = 0; i < (long long)s->C * kEmb; ++i) p[(size_t)(s->o_emb + i)] = (float)(0.1 * nrm());
+  for (int r = 0; r < 67; ++r)
+    for (int c = 0; c < kH; ++c)
+      p[(size_t)(s->o_w1 + (long long)r * kH + c)] = (float)(nrm() * std::sqrt(2.0 / 67));
+  for (long long i = 0; i < (long long)kH * kH; ++i)
+    p[(size_t)(s->o_w2 + i)] = (float)(nrm() * std::sqrt(2.0 / kH));
+  for (int i = 0; i < kH; ++i) p[(size_t)(s->o_w3 + i)] = (float)(nrm() * std::sqrt(1.0 / kH));
+}
+
+static void sur_release(ebic_surrogate_ctx* s) {
+  if (s->stream) cudaStreamSynchronize(s->stream);
+  for (DevBuf* b : {&s->par, &s->grad, &s->mom, &s->vel, &s->w1b, &s->w2b, &s->cmean, &s->csd,
+                    &s->act, &s->dh1, &s->dh2, &s->dx, &s->y, &s->dy, &s->idx, &s->loss,
+                    &s->tgt, &s->tmp, &s->log_seq, &s->log_len, &s->log_fit})
+    b->release();
+  if (s->stream) cudaStreamDestroy(s->stream);
+  s->stream = nullptr;
+}
+
+static ebic_status sur_create(ebic_ctx* h, int32_t len_scale, uint64_t seed,
+                              ebic_surrogate_ctx* s) {
+  s->device = h->device;
+  s->C = h->C;
+  s->h = h;
+  s->seed = seed;
+  s->len_scale = (float)len_scale;
+  EBIC_CUDA_TRY(cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking));
+  s->o_emb = 0;
+  s->o_w1 = s->o_emb + (long long)s->C * kEmb;
+  s->o_b1 = s->o_w1 + (long long)kF * kH;
+  s->o_w2 = s->o_b1 + kH;
+  s->o_b2 = s->o_w2 + (long long)kH * kH;
+  s->o_w3 = s->o_b2 + kH;
+  s->o_b3 = s->o_w3 + kH;
+  s->n_par = s->o_b3 + 1;
+  const size_t pb = (size_t)s->n_par * sizeof(float);
+  EBIC_TRY(s->par.reserve(pb));
+  EBIC_TRY(s->grad.reserve(pb));
+  EBIC_TRY(s->mom.reserve_zeroed(pb, s->stream));
+  EBIC_TRY(s->vel.reserve_zeroed(pb, s->stream));
+  EBIC_TRY(s->w1b.reserve((size_t)kF * kH * sizeof(bf16)));
+  EBIC_TRY(s->w2b.reserve((size_t)kH * kH * sizeof(bf16)));
+  EBIC_TRY(s->cmean.reserve((size_t)s->C * sizeof(float)));
+  EBIC_TRY(s->csd.reserve((size_t)s->C * sizeof(float)));
+  EBIC_TRY(s->loss.reserve(sizeof(float)));
+  EBIC_TRY(s->tmp.reserve(2 * sizeof(double)));
+  std::vector<float> p;
+  init_weights(s, p);
+  EBIC_CUDA_TRY(cudaMemcpyAsync(s->par.ptr, p.data(), pb, cudaMemcpyHostToDevice, s->stream));
+  EBIC_TRY(refresh_copies(s, s->stream));
+  k_colstats<<<(unsigned)s->C, 256, 0, s->stream>>>(h->A_c, h->R, h->R_pad, s->cmean.as<float>(),
+                                                    s->csd.as<float>());
+  count_launches(1);
+  EBIC_CUDA_TRY(cudaGetLastError());
+  EBIC_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return EBIC_OK;
+}
+
+static ebic_status sur_train(ebic_surrogate_ctx* s, const uint16_t* seq, const int32_t* len,
+                             int32_t stride, const double* fit, long long n, int32_t steps,
+                             int32_t batch, float lr, float* out_loss) {
+  cudaStream_t st = s->stream;
+  // standardised log1p targets over the whole set
+  EBIC_TRY(s->tgt.reserve((size_t)n * sizeof(float)));
+  EBIC_CUDA_TRY(cudaMemsetAsync(s->tmp.ptr, 0, 2 * sizeof(double), st));
+  k_sum_log1p<<<456, 256, 0, st>>>(fit, n, s->tmp.as<double>());
+  double m2[2];
+  EBIC_CUDA_TRY(cudaMemcpyAsync(m2, s->tmp.ptr, sizeof(m2), cudaMemcpyDeviceToHost, st));
+  EBIC_CUDA_TRY(cudaStreamSynchronize(st));
+  const double mean = m2[0] / (double)n;
+  const double var = m2[1] / (double)n - mean * mean;
+  s->t_mean = (float)mean;
+  s->t_sd = (float)std::sqrt(var > 1e-12 ? var : 1.0);
+  k_targets<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(fit, n, s->t_mean, s->t_sd,
+                                                         s->tgt.as<float>());
+  count_launches(2);
+  EBIC_TRY(sur_reserve(s, batch));
+  for (int32_t i = 0; i < steps; ++i) {
+    k_sample<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>(
+        s->seed, (uint32_t)(s->steps_done + 1), n, batch, s->idx.as<int32_t>());
+    count_launches(1);
+    EBIC_TRY(sur_step(s, seq, len, stride, s->tgt.as<float>(), s->idx.as<int32_t>(), batch, lr,
+                      true, st));
+  }
+  float loss = 0.f;
+  if (out_loss && steps > 0)
+    EBIC_CUDA_TRY(cudaMemcpyAsync(&loss, s->loss.ptr, sizeof(float), cudaMemcpyDeviceToHost, st));
+  EBIC_CUDA_TRY(cudaStreamSynchronize(st));
+  if (out_loss) *out_loss = loss;
+  return EBIC_OK;
+}
+
+static ebic_status sur_log(ebic_surrogate_ctx* s, ebic_ctx* h) {
+  const uint16_t* seq = nullptr;
+  const int32_t* len = nullptr;
+  const double* fit = nullptr;
+  long long n = 0;
+  int32_t stride = 0;
+  EBIC_TRY(ea_archive(h, &seq, &len, &fit, &n, &stride));
+  if (n == 0) return EBIC_OK;
+  const long long need = s->log_n + n;
+  if (need > s->log_cap) {
+    long long cap = std::max<long long>(need, 2 * s->log_cap);
+    DevBuf nseq, nlen, nfit;
+    ebic_status rs = nseq.reserve((size_t)cap * kLogStride * sizeof(uint16_t));
+    if (rs == EBIC_OK) rs = nlen.reserve((size_t)cap * sizeof(int32_t));
+    if (rs == EBIC_OK) rs = nfit.reserve((size_t)cap * sizeof(double));
+    if (rs != EBIC_OK) {
+      nseq.release();
+      nlen.release();
+      nfit.release();
+      return rs;
+    }
+    if (s->log_n) {
+      EBIC_CUDA_TRY(cudaMemcpyAsync(nseq.ptr, s->log_seq.ptr,
+                                    (size_t)s->log_n * kLogStride * sizeof(uint16_t),
+                                    cudaMemcpyDeviceToDevice, s->stream));
+      EBIC_CUDA_TRY(cudaMemcpyAsync(nlen.ptr, s->log_len.ptr, (size_t)s->log_n * sizeof(int32_t),
+                                    cudaMemcpyDeviceToDevice, s->stream));
+      EBIC_CUDA_TRY(cudaMemcpyAsync(nfit.ptr, s->log_fit.ptr, (size_t)s->log_n * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, s->stream));
+      EBIC_CUDA_TRY(cudaStreamSynchronize(s->stream));
+    }
+    s->log_seq.release();
+    s->log_len.release();
+    s->log_fit.release();
+    s->log_seq = nseq;
+    s->log_len = nlen;
+    s->log_fit = nfit;
+    nseq.ptr = nlen.ptr = nfit.ptr = nullptr;
+    s->log_cap = cap;
+  }
+  uint16_t* dseq = s->log_seq.as<uint16_t>() + (size_t)s->log_n * kLogStride;
+  EBIC_CUDA_TRY(cudaMemcpy2DAsync(dseq, kLogStride * sizeof(uint16_t), seq,
+                                  (size_t)stride * sizeof(uint16_t),
+                                  (size_t)stride * sizeof(uint16_t), (size_t)n,
+                                  cudaMemcpyDeviceToDevice, s->stream));
+  EBIC_CUDA_TRY(cudaMemcpyAsync(s->log_len.as<int32_t>() + s->log_n, len, (size_t)n * sizeof(int32_t),
+                                cudaMemcpyDeviceToDevice, s->stream));
+  EBIC_CUDA_TRY(cudaMemcpyAsync(s->log_fit.as<double>() + s->log_n, fit, (size_t)n * sizeof(double),
+                                cudaMemcpyDeviceToDevice, s->stream));
+  EBIC_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  s->log_n += n;
+  return EBIC_OK;
+}
+
+}  // namespace ebic
+
+extern "C" {
+
+ebic_status ebic_surrogate_create(ebic_handle h, int32_t len_scale, uint64_t seed,
+                                  ebic_surrogate* out) {
+  if (!h || !out || len_scale < 1) return fail(EBIC_ERR_ARG, "bad surrogate arguments");
+  ebic_surrogate_ctx* s = new ebic_surrogate_ctx();
+  const ebic_status st = sur_create(h, len_scale, seed, s);
+  if (st != EBIC_OK) {
+    sur_release(s);
+    delete s;
+    return st;
+  }
+  *out = s;
+  return EBIC_OK;
+}
+
+ebic_status ebic_surrogate_free(ebic_surrogate s) {
+  if (!s) return EBIC_OK;
+  if (s->attached > 0)
+    return fail(EBIC_ERR_STATE, "the surrogate is screening %d run(s); detach it first",
+                s->attached);
+  sur_release(s);
+  delete s;
+  return EBIC_OK;
+}
+
+ebic_status ebic_surrogate_params(ebic_surrogate s, float* host_params, int64_t* n_params,
+                                  int32_t write) {
+  if (!s || !n_params) return fail(EBIC_ERR_ARG, "null pointer");
+  const long long n = s->n_par;
+  if (host_params) {
+    if (*n_params < n)
+      return fail(EBIC_ERR_ARG, "buffer holds %lld parameters, %lld needed", (long long)*n_params, n);
+    if (write) {
+      EBIC_CUDA_TRY(cudaMemcpyAsync(s->par.ptr, host_params, (size_t)n * sizeof(float),
+                                    cudaMemcpyHostToDevice, s->stream));
+      EBIC_TRY(refresh_copies(s, s->stream));
+    } else {
+      EBIC_CUDA_TRY(cudaMemcpyAsync(host_params, s->par.ptr, (size_t)n * sizeof(float),
+                                    cudaMemcpyDeviceToHost, s->stream));
+    }
+    EBIC_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  }
+  *n_params = n;
+  return EBIC_OK;
+}
+
+ebic_status ebic_surrogate_grads(ebic_surrogate s, float* host_grads, int64_t n) {
+  if (!s || !host_grads || n < s->n_par) return fail(EBIC_ERR_ARG, "bad gradient buffer");
+  EBIC_CUDA_TRY(cudaMemcpyAsync(host_grads, s->grad.ptr, (size_t)s->n_par * sizeof(float),
+                                cudaMemcpyDeviceToHost, s->stream));
+  EBIC_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return EBIC_OK;
+}
+
+ebic_status ebic_surrogate_colstats(ebic_surrogate s, float* host_mean, float* host_sd) {
+  if (!s || !host_mean || !host_sd) return fail(EBIC_ERR_ARG, "null pointer");
+  EBIC_CUDA_TRY(cudaMemcpyAsync(host_mean, s->cmean.ptr, (size_t)s->C * sizeof(float),
+                                cudaMemcpyDeviceToHost, s->stream));
+  EBIC_CUDA_TRY(cudaMemcpyAsync(host_sd, s->csd.ptr, (size_t)s->C * sizeof(float),
+                                cudaMemcpyDeviceToHost, s->stream));
+  EBIC_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  return EBIC_OK;
+}
+
+ebic_status ebic_surrogate_step(ebic_surrogate s, const uint16_t* d_seq, const int32_t* d_len,
+                                int32_t stride, const float* d_target, const int32_t* d_idx,
+                                int32_t batch, float lr, int32_t update, float* out_loss) {
+  if (!s || !d_seq || !d_len || !d_target || batch < 1 || stride < 1)
+    return fail(EBIC_ERR_ARG, "bad step arguments");
+  const cudaStream_t st = s->stream;
+  EBIC_TRY(sur_step(s, d_seq, d_len, stride, d_target, d_idx, batch, lr, update != 0, st));
+  float loss = 0.f;
+  EBIC_CUDA_TRY(cudaMemcpyAsync(&loss, s->loss.ptr, sizeof(float), cudaMemcpyDeviceToHost, st));
+  EBIC_CUDA_TRY(cudaStreamSynchronize(st));
+  if (out_loss) *out_loss = loss;
+  return EBIC_OK;
+}
+
+ebic_status ebic_surrogate_log(ebic_surrogate s, ebic_handle h, int64_t* out_total) {
+  if (!s || !h) return fail(EBIC_ERR_ARG, "null pointer");
+  if (h->C != s->C) return fail(EBIC_ERR_ARG, "the run's matrix has %d columns, the surrogate %d", h->C, s->C);
+  EBIC_TRY(sur_log(s, h));
+  if (out_total) *out_total = s->log_n;
+  return EBIC_OK;
+}
+
+ebic_status ebic_surrogate_train(ebic_surrogate s, const uint16_t* d_seq, const int32_t* d_len,
+                                 int32_t stride, const double* d_fitness, int64_t n,
+                                 int32_t steps, int32_t batch, float lr, float* out_loss) {
+  if (!s || steps < 0 || batch < 1 || batch > (1 << 24))
+    return fail(EBIC_ERR_ARG, "bad training arguments");
+  if (!d_seq && !d_len && !d_fitness) {
+    d_seq = s->log_seq.as<uint16_t>();
+    d_len = s->log_len.as<int32_t>();
+    d_fitness = s->log_fit.as<double>();
+    stride = kLogStride;
+    n = s->log_n;
+  }
+  if (!d_seq || !d_len || !d_fitness || n < 2 || n > (1ll << 31) - 1 || stride < 1)
+    return fail(EBIC_ERR_ARG, "training needs at least 2 pairs (%lld given)", (long long)n);
+  return sur_train(s, d_seq, d_len, stride, d_fitness, n, steps, batch, lr, out_loss);
+}
+
+ebic_status ebic_surrogate_target_norm(ebic_surrogate s, float* mean, float* sd) {
+  if (!s) return fail(EBIC_ERR_ARG, "null surrogate");
+  if (mean) *mean = s->t_mean;
+  if (sd) *sd = s->t_sd;
+  return EBIC_OK;
+}
+
+ebic_status ebic_surrogate_predict(ebic_surrogate s, const uint16_t* d_seq, const int32_t* d_len,
+                                   int32_t stride, int64_t n, float* d_out, void* stream) {
+  if (!s || !d_seq || !d_len || !d_out || n < 0 || n > (1ll << 31) - 1 || stride < 1)
+    return fail(EBIC_ERR_ARG, "bad prediction arguments");
+  if (n == 0) return EBIC_OK;
+  const cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : s->stream;
+  const int32_t chunk = 1 << 16;
+  const int32_t rows = (int32_t)std::min<int64_t>(chunk, n);
+  if (stream) EBIC_CUDA_TRY(cudaStreamSynchronize(s->stream));
+  EBIC_TRY(sur_reserve(s, rows));
+  for (int64_t b0 = 0; b0 < n; b0 += chunk) {
+    const int32_t m = (int32_t)std::min<int64_t>(chunk, n - b0);
+    EBIC_TRY(sur_forward_scores(s, d_seq + (size_t)b0 * stride, d_len + b0, stride, m,
+                                s->act.ptr, d_out + b0, st, nullptr));
+    count_launches(4);
+  }
+  if (!stream) EBIC_CUDA_TRY(cudaStreamSynchronize(st));
+  return EBIC_OK;
+}
+
+}  // extern "C"

@@ -31,7 +31,9 @@ def assert_bits_equal(got, want, what):
     want = np.asarray(want)
     assert got.shape == want.shape, (what, got.shape, want.shape)
     if got.dtype.kind == "f":
-        same = got.view(np.uint64) == want.view(np.uint64)
+        assert got.dtype == want.dtype, (what, got.dtype, want.dtype)
+        u = np.dtype(f"u{got.dtype.itemsize}")
+        same = got.view(u) == want.view(u)
     else:
         same = got == want
     if not same.all():

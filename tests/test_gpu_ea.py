@@ -24,6 +24,7 @@ def built():
 
 def _device_params(kw):
     d = dict(kw)
+    d.pop("oversample", None)
     mode = d.pop("fitness_support", 0)
     p = eb.ebic_default_params(**d)
     p.support_mode = mode
@@ -31,11 +32,17 @@ def _device_params(kw):
 
 
 def run_both(A, gens_to_check=None, **kw):
+    """Runs the oracle and the device loop with the same parameters and compares
+    them generation by generation.  oversample > 1 screens offspring with
+    pseudo scores on both sides."""
     kw = {**BASE, **kw}
     ref = oracle.run(A, trace=True, **kw)
     h = eb.ebic_load_matrix(A)
     try:
         p = _device_params(kw)
+        V = kw.get("oversample", 1)
+        if V > 1:
+            eb.ebic_run_screen(h, None, V, eb.SCREEN_PSEUDO)
         eb.ebic_run_init(h, p)
         P, T, L = kw["pop_size"], kw["toprank_size"], kw["len_max"]
         done = ref["stats"]["generations_done"]
@@ -163,3 +170,45 @@ def test_expression_shape_three_generations():
     prob = synth.matrix_expression(seed=0)
     run_both(prob.A, gens_to_check={0, 3}, pop_size=4096, len_min=3, len_max=30, sigma=50,
              iterations=3)
+
+
+# ---------------------------------------------------------------------------
+# offspring screening with pseudo scores: the candidate generation, the pick
+# and the record completion against the oracle, bit for bit
+@pytest.mark.parametrize("variant", [
+    dict(oversample=2), dict(oversample=4, tournament_k=1), dict(oversample=8, tournament_k=3),
+    dict(oversample=16, p_crossover=1.0), dict(oversample=3, p_crossover=0.0),
+    dict(oversample=5, tournament_k=4, fitness_support=1)])
+def test_pseudo_screening_matches_oracle(variant):
+    prob = synth.matrix_tiny(seed=3)
+    run_both(prob.A, iterations=8, **variant)
+
+
+def test_pseudo_screening_paper_shape():
+    prob = synth.matrix_paper(seed=1)
+    run_both(prob.A, gens_to_check={0, 1, 5, 20}, pop_size=600, len_min=3, len_max=20,
+             sigma=25, iterations=20, oversample=8)
+
+
+def test_pseudo_screening_changes_the_run_but_not_step1():
+    prob = synth.matrix_tiny(seed=4)
+    plain = oracle.run(prob.A, trace=True, **{**BASE, "iterations": 3})
+    scr = oracle.run(prob.A, trace=True, **{**BASE, "iterations": 3, "oversample": 4})
+    assert plain["trace_pop"][0]["seqs"] == scr["trace_pop"][0]["seqs"]
+    assert plain["trace_pop"][3]["seqs"] != scr["trace_pop"][3]["seqs"]
+
+
+def test_screen_argument_errors():
+    prob = synth.matrix_tiny(seed=0)
+    h = eb.ebic_load_matrix(prob.A)
+    try:
+        for bad in [dict(oversample=0, mode=eb.SCREEN_PSEUDO), dict(oversample=17, mode=eb.SCREEN_PSEUDO),
+                    dict(oversample=4, mode=7), dict(oversample=4, mode=eb.SCREEN_SURROGATE)]:
+            with pytest.raises(eb.EbicError) as e:
+                eb.ebic_run_screen(h, None, **bad)
+            assert e.value.status == 1
+        # screening off again: the plain trajectory
+        eb.ebic_run_screen(h, None, 4, eb.SCREEN_PSEUDO)
+        eb.ebic_run_screen(h, None, 1, eb.SCREEN_OFF)
+    finally:
+        eb.ebic_free(h)
