@@ -17,6 +17,11 @@
 //   Philox-4x32-10   -- Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
 //                       as easy as 1, 2, 3", SC'11 (the counter-based generator
 //                       used for every random draw of the EA)
+//   offspring screening with pseudo scores (make_child, oversample > 1) --
+//                       not in the paper: the test form of the learned
+//                       pre-screen's candidate generation and pick; parity
+//                       unpinned beyond its oversample = 1 case, which is the
+//                       plain algorithm
 //
 // Where the paper is silent the reading is stated next to the code.  Build
 // flags: -O2 -fno-fast-math -ffp-contract=off (IEEE binary32/binary64,
