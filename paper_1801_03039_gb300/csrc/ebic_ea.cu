@@ -83,20 +83,30 @@ struct EaDev {
 
 constexpr int kMaxLen = EBIC_MAX_EA_LEN;
 
+// Words of the column bitsets kept in attempt records: 4 for up to 128
+// columns, 8 for up to 256, none beyond (the builder's generic path).
+__host__ __device__ inline int bit_words(int WC) { return WC <= 4 ? 4 : (WC <= 8 ? 8 : 0); }
+
 // Layout of one attempt record (byte offsets; 8-byte fields first, size a
 // multiple of 16 so that records can be bulk-copied).  ne = 2k entrant slots
 // (first tournament, then second), nc = k * k candidate children (winner
-// positions ta * k + tb), S = series stride.
+// positions ta * k + tb), S = series stride, nw = bitset words (ebit / cbit:
+// the column sets of the entrants / children as bitsets).
 struct RecLayout {
-  int chash, ef, ent, cross, elnf, eL, cL, ctabu, ecols, ccols, bytes;
+  int chash, ef, ent, cross, elnf, eL, cL, ctabu, ebit, cbit, ecols, ccols, bytes, nw;
 };
 
-__host__ __device__ inline RecLayout rec_layout(int k, int S, bool init) {
+__host__ __device__ inline RecLayout rec_layout(int k, int S, bool init, int nw) {
   const int ne = init ? 0 : 2 * k, nc = init ? 1 : k * k;
+  if (init) nw = 0;
   RecLayout l{};
   int o = 0;
+  l.nw = nw;
   l.chash = o; o += nc * 8;
   l.ef = o;    o += ne * 8;
+  o = (o + 15) & ~15;                 // bitsets: 16-byte aligned for vector loads
+  l.ebit = o;  o += ne * nw * 4;
+  l.cbit = o;  o += nc * nw * 4;
   l.ent = o;   o += 8 * 4;
   l.cross = o; o += 4;
   l.elnf = o;  o += ne * 4;
@@ -107,6 +117,12 @@ __host__ __device__ inline RecLayout rec_layout(int k, int S, bool init) {
   l.ccols = o; o += nc * S * 2;
   l.bytes = (o + 15) & ~15;
   return l;
+}
+
+// The column set of a series as nw bitset words.
+__device__ __forceinline__ void write_bits(uint32_t* out, int nw, const uint16_t* s, int L) {
+  for (int w = 0; w < nw; ++w) out[w] = 0u;
+  for (int i = 0; i < L; ++i) out[s[i] >> 5] |= 1u << (s[i] & 31);
 }
 
 // ---------------------------------------------------------------------------
@@ -276,7 +292,7 @@ __global__ void __launch_bounds__(128) k_spec(EaDev d) {
   const int v = SCREEN ? (int)(tid % V) : 0;
   const long long jc = SCREEN ? tid / V : tid;
   const int j = (int)(jc / nc), c = (int)(jc % nc);
-  const RecLayout l = rec_layout(d.k, d.S, INIT);
+  const RecLayout l = rec_layout(d.k, d.S, INIT, bit_words(d.WC));
   char* rec = d.rec + (size_t)j * d.rec_bytes;
   Draws r(d.seed, (uint32_t)g, (uint32_t)j);
   uint16_t x[kMaxLen];
@@ -303,6 +319,7 @@ __global__ void __launch_bounds__(128) k_spec(EaDev d) {
       uint16_t* ec = reinterpret_cast<uint16_t*>(rec + l.ecols) + (size_t)e * d.S;
       const uint16_t* src = d.seq + (size_t)er * d.S;
       for (int i = 0; i < eL; ++i) ec[i] = src[i];
+      if (l.nw) write_bits(reinterpret_cast<uint32_t*>(rec + l.ebit) + (size_t)e * l.nw, l.nw, src, eL);
     }
     if (c == 0 && v == 0) reinterpret_cast<int32_t*>(rec + l.cross)[0] = cross ? 1 : 0;
     const int base = 2 * k + 1 + 5 * v;
@@ -341,6 +358,7 @@ __global__ void __launch_bounds__(128) k_spec(EaDev d) {
   uint16_t* out = reinterpret_cast<uint16_t*>(rec + l.ccols) + (size_t)c * d.S;
   for (int i = 0; i < L; ++i) out[i] = x[i];
   reinterpret_cast<int32_t*>(rec + l.cL)[c] = L;
+  if (l.nw) write_bits(reinterpret_cast<uint32_t*>(rec + l.cbit) + (size_t)c * l.nw, l.nw, x, L);
   const unsigned long long h = seq_hash(x, L);
   reinterpret_cast<unsigned long long*>(rec + l.chash)[c] = h;
   reinterpret_cast<int32_t*>(rec + l.ctabu)[c] = INIT ? 0 : (tabu_contains(d, h, x, L) ? 1 : 0);
@@ -408,11 +426,12 @@ __global__ void __launch_bounds__(128) k_pick(EaDev d) {
   const long long row = jc * d.V + chosen;
   const int L = d.var_len[row];
   const uint16_t* x = d.var_seq + (size_t)row * d.S;
-  const RecLayout l = rec_layout(d.k, d.S, false);
+  const RecLayout l = rec_layout(d.k, d.S, false, bit_words(d.WC));
   char* rec = d.rec + (size_t)j * d.rec_bytes;
   uint16_t* out = reinterpret_cast<uint16_t*>(rec + l.ccols) + (size_t)c * d.S;
   for (int i = 0; i < L; ++i) out[i] = x[i];
   reinterpret_cast<int32_t*>(rec + l.cL)[c] = L;
+  if (l.nw) write_bits(reinterpret_cast<uint32_t*>(rec + l.cbit) + (size_t)c * l.nw, l.nw, x, L);
   reinterpret_cast<unsigned long long*>(rec + l.chash)[c] = chosen_h;
   reinterpret_cast<int32_t*>(rec + l.ctabu)[c] = hit ? 1 : 0;
 }
@@ -433,105 +452,318 @@ __global__ void __launch_bounds__(128) k_pick(EaDev d) {
 // path.
 struct Entrant {
   float lnf;
+  float cl;          // log(base) / L as float
   int32_t S, L, idx;
   const double* f;   // the entrant's binary64 fitness (shared memory)
 };
 
-// Bit 0 of the result: x beats y.  Bit 1: the exact path decided.
-__device__ __forceinline__ int beats(const Entrant& x, const Entrant& y, const EaDev& d,
-                                     const float* cL) {
+// Bit 0 of the result: x beats y.  Bit 1: the exact path decided.  The float
+// decision is formed with selects; only an undecided comparison branches to
+// the exact path.
+__device__ __forceinline__ int beats(const Entrant& x, const Entrant& y, const EaDev& d) {
   if (x.idx == y.idx) return 0;
   const bool zx = x.lnf == -INFINITY, zy = y.lnf == -INFINITY;
-  if (zx && zy) return x.idx < y.idx ? 1 : 0;
-  const float cx = (float)x.S * cL[x.L];
-  const float cy = (float)y.S * cL[y.L];
-  const bool safe_x = zx || (cx < 700.f && x.lnf - cx > -700.f);
-  const bool safe_y = zy || (cy < 700.f && y.lnf - cy > -700.f);
-  if (safe_x && safe_y) {
-    if (zx) return 0;
-    if (zy) return 1;
-    const float gx = x.lnf - cx, gy = y.lnf - cy;
-    const float margin = 0x1p-16f * (fabsf(x.lnf) + fabsf(y.lnf) + cx + cy + 1.f);
-    if (gx - gy > margin) return 1;
-    if (gy - gx > margin) return 0;
+  const float cx = (float)x.S * x.cl;
+  const float cy = (float)y.S * y.cl;
+  const float gx = x.lnf - cx, gy = y.lnf - cy;
+  const bool safe_x = zx || (cx < 700.f && gx > -700.f);
+  const bool safe_y = zy || (cy < 700.f && gy > -700.f);
+  const float diff = gx - gy;
+  const float margin = 0x1p-16f * (fabsf(x.lnf) + fabsf(y.lnf) + cx + cy + 1.f);
+  const bool decided = (zx && zy) || (zx && safe_y) || (zy && safe_x) ||
+                       (!zx && !zy && safe_x && safe_y && fabsf(diff) > margin);
+  if (decided) {
+    const bool win = (zx && zy) ? x.idx < y.idx : (zx ? false : (zy ? true : diff > 0.f));
+    return win ? 1 : 0;
   }
   const double px = __ddiv_rn(*x.f, d.pow_tab[d.pow_off[x.L] + x.S]);
   const double py = __ddiv_rn(*y.f, d.pow_tab[d.pow_off[y.L] + y.S]);
   return 2 | ((px > py || (px == py && x.idx < y.idx)) ? 1 : 0);
 }
 
-// Winner position of one tournament (entrant slots e0 .. e0 + k - 1 of the
-// record; identities ent[0 .. k)), lane-local.  Returns the position of the
-// first entrant with the winning identity; *exact counts exact decisions.
-__device__ __forceinline__ int tournament_lane(const EaDev& d, const float* cL, int k, int e0,
-                                               const int32_t* ent, const float* elnf,
-                                               const int32_t* eL, const double* ef,
-                                               const uint16_t* ecols, int S,
-                                               const uint32_t* pen, int* exact) {
-  Entrant best;
-  int best_t = 0;
-  for (int t = 0; t < k; ++t) {
-    const int e = e0 + t;
-    Entrant x;
-    x.lnf = elnf[e];
-    x.L = eL[e];
-    x.idx = ent[t];
-    x.f = ef + e;
-    const uint16_t* cs = ecols + (size_t)e * S;
-    uint32_t s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-    int c = 0;
-    for (; c + 4 <= x.L; c += 4) {
-      s0 += pen[cs[c]];
-      s1 += pen[cs[c + 1]];
-      s2 += pen[cs[c + 2]];
-      s3 += pen[cs[c + 3]];
-    }
-    for (; c < x.L; ++c) s0 += pen[cs[c]];
-    x.S = (int32_t)(s0 + s1 + s2 + s3);
-    if (t == 0) {
-      best = x;
-      continue;
-    }
-    const int r = beats(x, best, d, cL);
-    *exact += r >> 1;
-    if (r & 1) {
-      best = x;
-      best_t = t;
-    }
-  }
-  for (int t = 0; t < best_t; ++t)
-    if (ent[t] == best.idx) return t;
-  return best_t;
-}
-
-
 // Lane-local tournament decisions for tournament size K (1 or 2): entrant
 // slots 0 .. K - 1 form the first tournament, K .. 2K - 1 the second (when the
 // attempt crosses over).  Returns the child index ta * K + tb; *nex counts
 // exact-path comparisons.
 template <int K>
-__device__ __forceinline__ int decide_small(const EaDev& d, const float* cL, int cr,
-                                            const float (&ln)[4], const int32_t (&Sx)[4],
-                                            const int32_t (&Lx)[4], const int32_t (&id)[4],
-                                            const double* ef, int* nex) {
+__device__ __forceinline__ int decide_small(const EaDev& d, int cr, const float (&ln)[2 * K],
+                                            const float (&cl)[2 * K],
+                                            const int32_t (&Sx)[2 * K],
+                                            const int32_t (&Lx)[2 * K],
+                                            const int32_t (&id)[2 * K], const double* ef,
+                                            int* nex) {
   int ta = 0, tb = 0;
   if (K == 2) {
     {
-      const Entrant x{ln[1], Sx[1], Lx[1], id[1], ef + 1};
-      const Entrant y{ln[0], Sx[0], Lx[0], id[0], ef + 0};
-      const int r = beats(x, y, d, cL);
+      const Entrant x{ln[1], cl[1], Sx[1], Lx[1], id[1], ef + 1};
+      const Entrant y{ln[0], cl[0], Sx[0], Lx[0], id[0], ef + 0};
+      const int r = beats(x, y, d);
       *nex += r >> 1;
       if ((r & 1) && id[1] != id[0]) ta = 1;
     }
     if (cr) {
-      const Entrant x{ln[3], Sx[3], Lx[3], id[3], ef + 3};
-      const Entrant y{ln[2], Sx[2], Lx[2], id[2], ef + 2};
-      const int r = beats(x, y, d, cL);
+      const Entrant x{ln[K + 1], cl[K + 1], Sx[K + 1], Lx[K + 1], id[K + 1], ef + K + 1};
+      const Entrant y{ln[K], cl[K], Sx[K], Lx[K], id[K], ef + K};
+      const int r = beats(x, y, d);
       *nex += r >> 1;
-      if ((r & 1) && id[3] != id[2]) tb = 1;
+      if ((r & 1) && id[K + 1] != id[K]) tb = 1;
     }
   }
   return ta * K + tb;
+}
+
+// Within-generation duplicate check: open addressing on the 64-bit hash in
+// shared memory; a hash match is confirmed on the columns of the earlier
+// child (warp-wide compare).  Returns true for a duplicate; *slot = the first
+// empty slot after the probe otherwise.
+template <int NCT>   // combos per record when known at compile time (0: runtime nc)
+__device__ __forceinline__ bool gen_duplicate(const EaDev& d, const RecLayout& l,
+                                              const unsigned long long* hkey,
+                                              const int32_t* href, int hmask, int nc_rt, int RB,
+                                              unsigned long long key, const uint16_t* child,
+                                              int L, int lane, int* slot) {
+  const int nc = NCT ? NCT : nc_rt;
+  int sl = (int)(key & (unsigned long long)hmask);
+  for (int probe = 0; probe <= hmask; ++probe) {
+    const unsigned long long kk = hkey[sl];
+    if (kk == 0ull) break;
+    if (kk == key) {
+      const int32_t r = href[sl];
+      const char* orec = d.rec + (size_t)(r / nc) * RB;
+      const int oc = r % nc;
+      const uint16_t* other = reinterpret_cast<const uint16_t*>(orec + l.ccols) + (size_t)oc * d.S;
+      const int oL = reinterpret_cast<const int32_t*>(orec + l.cL)[oc];
+      const bool same =
+          oL == L &&
+          __all_sync(0xffffffffu, lane >= L || other[lane] == child[lane]) &&
+          __all_sync(0xffffffffu, lane + 32 >= L || other[lane + 32] == child[lane + 32]);
+      if (same) return true;
+    }
+    sl = (sl + 1) & hmask;
+  }
+  *slot = sl;
+  return false;
+}
+
+// Float part of one tournament comparison (see beats) with the constants of
+// the pair precomputed once per sub-chunk.  During a sub-chunk a penalty sum
+// can only grow, by at most 31 * L (31 earlier acceptances, each sharing at
+// most L columns with the entrant), so the range checks of beats are settled
+// in advance for the whole interval: a pair that passes them for every sum up
+// to that bound compares in float; one that does not always takes the exact
+// path.  Pairs whose outcome does not depend on the sums (the same individual
+// twice, a zero fitness on either side) are decided once.
+struct PairConst {
+  float lx, ly, clx, cly, base;   // base = 2^-16 (|lx| + |ly| + 1)
+  int fixed;                      // -1: depends on the sums; else the outcome
+  bool exact_always, xlow;        // xlow: idx_x < idx_y
+};
+
+__device__ __forceinline__ PairConst pair_const(float lx, float ly, float clx, float cly,
+                                                int32_t ix, int32_t iy, int32_t Sx, int32_t Sy,
+                                                int32_t Lx, int32_t Ly) {
+  PairConst p;
+  p.lx = lx;
+  p.ly = ly;
+  p.clx = clx;
+  p.cly = cly;
+  p.xlow = ix < iy;
+  const bool zx = lx == -INFINITY, zy = ly == -INFINITY;
+  p.base = (zx || zy) ? 0.f : 0x1p-16f * (fabsf(lx) + fabsf(ly) + 1.f);
+  // the range checks at the largest sums the sub-chunk can reach (the checks
+  // are monotone in the sum)
+  const float cxm = (float)(Sx + 31 * Lx) * clx, cym = (float)(Sy + 31 * Ly) * cly;
+  const bool safe_x = zx || (cxm < 700.f && lx - cxm > -700.f);
+  const bool safe_y = zy || (cym < 700.f && ly - cym > -700.f);
+  p.fixed = -1;
+  p.exact_always = false;
+  if (ix == iy) p.fixed = 0;
+  else if (zx && zy) p.fixed = p.xlow ? 1 : 0;
+  else if (!(safe_x && safe_y)) p.exact_always = true;
+  else if (zx) p.fixed = 0;
+  else if (zy) p.fixed = 1;
+  return p;
+}
+
+// 1 / 0 when decided in float, -1 when the exact path must decide.
+__device__ __forceinline__ int pair_fast(const PairConst& p, int32_t Sx, int32_t Sy) {
+  const float cx = (float)Sx * p.clx, cy = (float)Sy * p.cly;
+  const float diff = (p.lx - cx) - (p.ly - cy);
+  const float margin = p.base + 0x1p-16f * (cx + cy);
+  int r = fabsf(diff) > margin ? (diff > 0.f ? 1 : 0) : -1;
+  r = p.exact_always ? -1 : r;
+  return p.fixed >= 0 ? p.fixed : r;
+}
+
+// Exact binary64 comparison (the definition; see beats) for an undecided pair.
+__device__ __noinline__ int pair_exact(const EaDev& d, const double* fx, const double* fy,
+                                       int32_t Lx, int32_t Ly, int32_t Sx, int32_t Sy,
+                                       bool xlow) {
+  const double px = __ddiv_rn(*fx, d.pow_tab[d.pow_off[Lx] + Sx]);
+  const double py = __ddiv_rn(*fy, d.pow_tab[d.pow_off[Ly] + Sy]);
+  return (px > py || (px == py && xlow)) ? 1 : 0;
+}
+
+// The Step 3 consumer for tournaments of K <= 2 entrants and NW-word column
+// bitsets, run by one warp on one chunk of records in shared memory.  The 32
+// attempts of a sub-chunk (one per lane) are prepared in parallel: penalty
+// sums, the constants of both tournaments, entrant bitsets, outcomes.  The
+// scan then takes them in order.  For attempt b every later lane computes,
+// before the duplicate check of b is known, the penalty sums it would have if
+// b's child were accepted (sum += |entrant & child| from the bitsets) and the
+// outcome those sums give; the acceptance commits them.  Penalty counts are
+// brought up to date once per 32 attempts.  With K = 1 there is no
+// comparison, so no sums are tracked.
+template <int K, int NW>
+__device__ __forceinline__ void build_fast(const EaDev& d, const RecLayout& l, const char* cur,
+                                           int cnt, int j0, uint32_t* pen, const float* cLf,
+                                           unsigned long long* hkey, int32_t* href,
+                                           long long base, int hmask, int RB, int lane, int& n,
+                                           int& hits, int& stopped, long long& attempts,
+                                           long long& exact) {
+  constexpr int NE = 2 * K, NC = K * K, NV = NW / 4;
+  const int S = d.S;
+  for (int sb = 0; sb < cnt && n < d.P && !stopped; sb += 32) {
+    const int a = sb + lane;
+    const bool have = a < cnt;
+    const char* ra = cur + (size_t)(have ? a : sb) * RB;
+    const int cr = have ? *reinterpret_cast<const int32_t*>(ra + l.cross) : 0;
+    int32_t Sx[NE], Lx[NE];
+    uint4 bits[NE][NV];
+    PairConst pc[2];
+    const double* efa = reinterpret_cast<const double*>(ra + l.ef);
+    int dec = 0, nex = 0;
+    if (K == 2) {
+      float ln[NE], cl[NE];
+      int32_t id[NE];
+#pragma unroll
+      for (int e = 0; e < NE; ++e) {
+        ln[e] = 0.f;
+        cl[e] = 0.f;
+        Sx[e] = Lx[e] = id[e] = 0;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) bits[e][v] = make_uint4(0u, 0u, 0u, 0u);
+        if (have && (e < K || cr)) {
+          ln[e] = reinterpret_cast<const float*>(ra + l.elnf)[e];
+          Lx[e] = reinterpret_cast<const int32_t*>(ra + l.eL)[e];
+          cl[e] = cLf[Lx[e]];
+          id[e] = reinterpret_cast<const int32_t*>(ra + l.ent)[e < K ? e : 4 + (e - K)];
+          const uint4* eb = reinterpret_cast<const uint4*>(ra + l.ebit) + e * NV;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) bits[e][v] = eb[v];
+          const uint16_t* cs = reinterpret_cast<const uint16_t*>(ra + l.ecols) + (size_t)e * S;
+          uint32_t s0 = 0, s1 = 0;
+          int c = 0;
+          for (; c + 2 <= Lx[e]; c += 2) {
+            s0 += pen[cs[c]];
+            s1 += pen[cs[c + 1]];
+          }
+          if (c < Lx[e]) s0 += pen[cs[c]];
+          Sx[e] = (int32_t)(s0 + s1);
+        }
+      }
+      pc[0] = pair_const(ln[1], ln[0], cl[1], cl[0], id[1], id[0], Sx[1], Sx[0], Lx[1], Lx[0]);
+      pc[1] = pair_const(ln[3], ln[2], cl[3], cl[2], id[3], id[2], Sx[3], Sx[2], Lx[3], Lx[2]);
+    }
+    // outcome (ta * K + tb) of this lane's attempt for penalty sums s[]
+    auto decide = [&](const int32_t (&sx)[NE], int* ne) -> int {
+      if (K == 1 || !have) return 0;
+      int ta = pair_fast(pc[0], sx[1], sx[0]);
+      if (ta < 0) {
+        ta = pair_exact(d, efa + 1, efa + 0, Lx[1], Lx[0], sx[1], sx[0], pc[0].xlow);
+        ++*ne;
+      }
+      int tb = 0;
+      if (cr) {
+        tb = pair_fast(pc[1], sx[3], sx[2]);
+        if (tb < 0) {
+          tb = pair_exact(d, efa + 3, efa + 2, Lx[3], Lx[2], sx[3], sx[2], pc[1].xlow);
+          ++*ne;
+        }
+      }
+      return ta * K + tb;
+    };
+    dec = decide(Sx, &nex);
+    bool mine = false;
+    int my_combo = 0, my_slot = 0, done = 0;
+    for (int b = 0; b < 32 && sb + b < cnt; ++b) {
+      if (n >= d.P) break;
+      const int combo = __shfl_sync(0xffffffffu, dec, b);
+      const char* rb = cur + (size_t)(sb + b) * RB;
+      ++done;
+      const int L = reinterpret_cast<const int32_t*>(rb + l.cL)[combo];
+      const unsigned long long key = reinterpret_cast<const unsigned long long*>(rb + l.chash)[combo];
+      const int tabu = reinterpret_cast<const int32_t*>(rb + l.ctabu)[combo];
+      int slot = (int)(key & (unsigned long long)hmask);
+      const unsigned long long kk = hkey[slot];
+      // speculative: sums and outcome of the later lanes if b's child is accepted
+      int32_t Sy[NE];
+      int dec2 = dec, nex2 = nex;
+      if (K == 2) {
+        uint4 cw[NV];
+        const uint4* cb = reinterpret_cast<const uint4*>(rb + l.cbit) + combo * NV;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) cw[v] = cb[v];
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+          uint32_t inter = 0;
+#pragma unroll
+          for (int v = 0; v < NV; ++v)
+            inter += __popc(bits[e][v].x & cw[v].x) + __popc(bits[e][v].y & cw[v].y) +
+                     __popc(bits[e][v].z & cw[v].z) + __popc(bits[e][v].w & cw[v].w);
+          Sy[e] = Sx[e] + (int32_t)inter;
+        }
+        nex2 = 0;
+        dec2 = decide(Sy, &nex2);
+      }
+      const uint16_t* child = reinterpret_cast<const uint16_t*>(rb + l.ccols) + (size_t)combo * S;
+      bool dup = tabu != 0;
+      if (!dup && kk != 0ull)
+        dup = gen_duplicate<NC>(d, l, hkey, href, hmask, NC, RB, key, child, L, lane, &slot);
+      if (dup) {
+        if (++hits > d.P) {
+          stopped = 1;
+          break;
+        }
+        continue;
+      }
+      const int32_t rec_id = (int32_t)((j0 + sb + b) * NC + combo);
+      if (lane == 0) {
+        hkey[slot] = key;
+        href[slot] = rec_id;
+      }
+      mine = mine || lane == b;
+      my_combo = lane == b ? combo : my_combo;
+      my_slot = lane == b ? n : my_slot;
+      if (K == 2) {
+        const bool later = lane > b;
+#pragma unroll
+        for (int e = 0; e < NE; ++e) Sx[e] = later ? Sy[e] : Sx[e];
+        dec = later ? dec2 : dec;
+        nex = later ? nex2 : nex;
+      }
+      ++n;
+    }
+    attempts += done;
+    // exact-path decisions among the attempts taken; then each accepted child
+    // goes, from shared memory, into its archive slot and the penalty counts
+    int ex = lane < done ? nex : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ex += __shfl_xor_sync(0xffffffffu, ex, o);
+    exact += ex;
+    if (mine) {
+      const uint16_t* ch = reinterpret_cast<const uint16_t*>(ra + l.ccols) + (size_t)my_combo * S;
+      const int Lc = reinterpret_cast<const int32_t*>(ra + l.cL)[my_combo];
+      uint16_t* dst = d.seq + (size_t)(base + my_slot) * S;
+      for (int c = 0; c < Lc; ++c) {
+        const uint16_t v = ch[c];
+        dst[c] = v;
+        atomicAdd(&pen[v], 1u);
+      }
+      d.len[base + my_slot] = Lc;
+    }
+    __syncwarp();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -542,9 +774,10 @@ __device__ __forceinline__ int decide_small(const EaDev& d, const float* cL, int
 // copies into a double buffer completed through mbarriers, issued by thread 0
 // two chunks ahead.  Every wait is bounded: on expiry the kernel records
 // stop reason 4, drains its own copies in flight and returns.
-// Accepted children go to the archive, copied by all warps at the end.
+// Accepted children go to the archive straight from the shared-memory records
+// (at acceptance, or once per 32 attempts in the fast path).
 //
-// Shared memory: hkey[H] (u64) | href[H] | acc[P] | pen[C] | cLf[Lmax + 1] |
+// Shared memory: hkey[H] (u64) | href[H] | pen[C] | cLf[Lmax + 1] |
 //                2 record buffers of kB records (128-byte aligned).
 // ---------------------------------------------------------------------------
 constexpr int kBuildThreads = 128;
@@ -594,21 +827,23 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = d.ctl->gen;
   const int H = hmask + 1, k = d.k, nc = INIT ? 1 : k * k, S = d.S;
-  const RecLayout l = rec_layout(k, S, INIT);
+  const RecLayout l = rec_layout(k, S, INIT, bit_words(d.WC));
   const int RB = d.rec_bytes;
   unsigned long long* hkey = smem_u64;
   int32_t* href = reinterpret_cast<int32_t*>(hkey + H);
-  int32_t* acc = href + H;                                 // accepted record per new slot
-  uint32_t* pen = reinterpret_cast<uint32_t*>(acc + d.P);
+  uint32_t* pen = reinterpret_cast<uint32_t*>(href + H);
   float* cLf = reinterpret_cast<float*>(pen + d.C);
-  char* buf0 = reinterpret_cast<char*>(
-      (reinterpret_cast<uintptr_t>(cLf + d.Lmax + 1) + 127) & ~(uintptr_t)127);
-  char* bufs[2] = {buf0, buf0 + (size_t)kB * RB};
+  // 128-byte aligned by an offset from the shared base (integer round trips
+  // through uintptr_t would lose the shared address space)
+  char* const sbase = reinterpret_cast<char*>(smem_u64);
+  char* buf0 = sbase + ((reinterpret_cast<char*>(cLf + d.Lmax + 1) - sbase + 127) & ~(ptrdiff_t)127);
+  // record buffer i at buf0 + i * kB * RB (computed, not looked up, so that the
+  // compiler keeps the shared-memory address space of every record access)
+  const size_t buf_bytes = (size_t)kB * RB;
   __shared__ __align__(8) unsigned long long bars[2];
   __shared__ int s_n, s_done, s_E, s_fail;
-  __shared__ uint32_t cbits[8];          // columns of the child just accepted (fast path)
   // fast path: tournaments of at most 2 entrants, column sets of at most 256 bits
-  const bool fast = d.k <= 2 && d.WC <= 8;
+  const bool fast = d.k <= 2 && l.nw > 0;
 
   const int nchunks = (d.J + kB - 1) / kB;
   if (tid == 0) {
@@ -622,13 +857,13 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
   if (tid == 0) {
     for (; issued < 2 && issued < nchunks; ++issued) {
       const int j0 = issued * kB, cnt = min(kB, d.J - j0);
-      bulk_load(bufs[issued & 1], d.rec + (size_t)j0 * RB, (uint32_t)cnt * RB, &bars[issued & 1]);
+      bulk_load(buf0 + (issued & 1) * buf_bytes, d.rec + (size_t)j0 * RB, (uint32_t)cnt * RB,
+                &bars[issued & 1]);
     }
   }
   for (int i = tid; i < H; i += kBuildThreads) hkey[i] = 0ull;
   for (int i = tid; i < d.C; i += kBuildThreads) pen[i] = 0u;
   for (int i = tid; i <= d.Lmax; i += kBuildThreads) cLf[i] = d.c_over_L[i];
-  if (tid < 8) cbits[tid] = 0u;
   const long long base = (long long)g * d.P;
   if (tid == 0) {
     int E = 0;
@@ -642,16 +877,15 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
   __syncthreads();
   const int E = s_E;
   // Step 2: elites copied in order, each column use counted.
-  for (int i = tid; i < E * S; i += kBuildThreads) {
-    const int e = i / S, c = i % S;
+  for (int e = warp; e < E; e += kBuildThreads / 32) {
     const int32_t src = d.list_ref[e];
     const int L = d.len[src];
-    if (c < L) {
+    for (int c = lane; c < L; c += 32) {
       const uint16_t v = d.seq[(size_t)src * S + c];
       d.seq[(size_t)(base + e) * S + c] = v;
       atomicAdd(&pen[v], 1u);
     }
-    if (c == 0) d.len[base + e] = L;
+    if (lane == 0) d.len[base + e] = L;
   }
   __syncthreads();
 
@@ -659,135 +893,27 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
   long long attempts = 0, exact = 0;
   int chunk = 0;
   for (; chunk < nchunks; ++chunk) {
-    char* cur = bufs[chunk & 1];
+    char* cur = buf0 + (chunk & 1) * buf_bytes;
     if (warp == 0) {
       const bool ok = mbar_wait(&bars[chunk & 1], (uint32_t)((chunk >> 1) & 1));
       const int cnt = min(kB, d.J - chunk * kB);
       if (!ok) {
         stopped = 4;
       } else if (!INIT && fast) {
-        // ---- speculative sub-chunks of 32 attempts, one per lane ----
-        for (int sb = 0; sb < cnt && n < d.P && !stopped; sb += 32) {
-          const int a = sb + lane;
-          const bool have = a < cnt;
-          const char* ra = cur + (size_t)(have ? a : sb) * RB;
-          const int cr = have ? *reinterpret_cast<const int32_t*>(ra + l.cross) : 0;
-          const int nE = have ? (cr ? 2 * k : k) : 0;
-          const double* efa = reinterpret_cast<const double*>(ra + l.ef);
-          float ln[4];
-          int32_t Sx[4], Lx[4], id[4];
-          uint32_t bits[4][8];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            ln[e] = 0.f;
-            Sx[e] = Lx[e] = id[e] = 0;
-#pragma unroll
-            for (int w = 0; w < 8; ++w) bits[e][w] = 0u;
-            if (e < nE) {
-              ln[e] = reinterpret_cast<const float*>(ra + l.elnf)[e];
-              Lx[e] = reinterpret_cast<const int32_t*>(ra + l.eL)[e];
-              id[e] = reinterpret_cast<const int32_t*>(ra + l.ent)[e < k ? e : 4 + (e - k)];
-              const uint16_t* cs = reinterpret_cast<const uint16_t*>(ra + l.ecols) + (size_t)e * S;
-              uint32_t sum = 0;
-              for (int c = 0; c < Lx[e]; ++c) {
-                const uint32_t col = cs[c];
-                sum += pen[col];
-#pragma unroll
-                for (int w = 0; w < 8; ++w)
-                  if ((int)(col >> 5) == w) bits[e][w] |= 1u << (col & 31);
-              }
-              Sx[e] = (int32_t)sum;
-            }
-          }
-          int my_nex = 0;
-          int dec = have ? (k == 2 ? decide_small<2>(d, cLf, cr, ln, Sx, Lx, id, efa, &my_nex)
-                                   : decide_small<1>(d, cLf, cr, ln, Sx, Lx, id, efa, &my_nex))
-                         : 0;
-          bool dirty = false;
-          for (int b = 0; b < 32 && sb + b < cnt; ++b) {
-            if (n >= d.P) break;
-            if (lane == b && dirty) {
-              my_nex = 0;
-              dec = k == 2 ? decide_small<2>(d, cLf, cr, ln, Sx, Lx, id, efa, &my_nex)
-                           : decide_small<1>(d, cLf, cr, ln, Sx, Lx, id, efa, &my_nex);
-            }
-            const int combo = __shfl_sync(0xffffffffu, dec, b);
-            exact += __shfl_sync(0xffffffffu, my_nex, b);
-            const char* rb = cur + (size_t)(sb + b) * RB;
-            const int j = chunk * kB + sb + b;
-            ++attempts;
-            const int L = reinterpret_cast<const int32_t*>(rb + l.cL)[combo];
-            const unsigned long long key = reinterpret_cast<const unsigned long long*>(rb + l.chash)[combo];
-            const uint16_t* child = reinterpret_cast<const uint16_t*>(rb + l.ccols) + (size_t)combo * S;
-            bool dup = reinterpret_cast<const int32_t*>(rb + l.ctabu)[combo] != 0;
-            int slot = (int)(key & (unsigned long long)hmask);
-            if (!dup) {
-              for (int probe = 0; probe <= hmask; ++probe) {
-                const unsigned long long kk = hkey[slot];
-                if (kk == 0ull) break;
-                if (kk == key) {
-                  const int32_t r = href[slot];
-                  const char* orec = d.rec + (size_t)(r / nc) * RB;
-                  const int oc = r % nc;
-                  const uint16_t* other = reinterpret_cast<const uint16_t*>(orec + l.ccols) + (size_t)oc * S;
-                  const int oL = reinterpret_cast<const int32_t*>(orec + l.cL)[oc];
-                  const bool same =
-                      oL == L &&
-                      __all_sync(0xffffffffu, lane >= L || other[lane] == child[lane]) &&
-                      __all_sync(0xffffffffu, lane + 32 >= L || other[lane + 32] == child[lane + 32]);
-                  if (same) {
-                    dup = true;
-                    break;
-                  }
-                }
-                slot = (slot + 1) & hmask;
-              }
-            }
-            if (dup) {
-              if (++hits > d.P) {
-                stopped = 1;
-                break;
-              }
-              continue;
-            }
-            // accept: penalty counts, child bitset, hash set, slot
-            const int c0 = lane < L ? child[lane] : 0;
-            const int c1 = lane + 32 < L ? child[lane + 32] : 0;
-            if (lane < L) {
-              pen[c0] += 1u;
-              atomicOr(&cbits[c0 >> 5], 1u << (c0 & 31));
-            }
-            if (lane + 32 < L) {
-              pen[c1] += 1u;
-              atomicOr(&cbits[c1 >> 5], 1u << (c1 & 31));
-            }
-            if (lane == 0) {
-              hkey[slot] = key;
-              href[slot] = (int32_t)(j * nc + combo);
-              acc[n] = (int32_t)(j * nc + combo);
-            }
-            __syncwarp();
-            // later attempts of this sub-chunk: penalty sums += overlap
-            if (lane > b && have) {
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                if (e < nE) {
-                  uint32_t inter = 0;
-#pragma unroll
-                  for (int w = 0; w < 8; ++w) inter += __popc(bits[e][w] & cbits[w]);
-                  if (inter) {
-                    Sx[e] += (int32_t)inter;
-                    dirty = true;
-                  }
-                }
-              }
-            }
-            __syncwarp();
-            if (lane < L) cbits[c0 >> 5] = 0u;
-            if (lane + 32 < L) cbits[c1 >> 5] = 0u;
-            __syncwarp();
-            ++n;
-          }
+        if (k == 2) {
+          if (l.nw == 4)
+            build_fast<2, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, base, hmask, RB,
+                             lane, n, hits, stopped, attempts, exact);
+          else
+            build_fast<2, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, base, hmask, RB,
+                             lane, n, hits, stopped, attempts, exact);
+        } else {
+          if (l.nw == 4)
+            build_fast<1, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, base, hmask, RB,
+                             lane, n, hits, stopped, attempts, exact);
+          else
+            build_fast<1, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, base, hmask, RB,
+                             lane, n, hits, stopped, attempts, exact);
         }
       } else {
         for (int a = 0; a < kB && n < d.P; ++a) {
@@ -836,12 +962,13 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
                 x.lnf = elnf[e];
                 x.S = (int32_t)__shfl_sync(0xffffffffu, e < 4 ? part0 : part1, (e & 3) * 8);
                 x.L = eL[e];
+                x.cl = cLf[x.L];
                 x.idx = ent[(tour ? 4 : 0) + t];
                 x.f = ef + e;
                 if (t == 0) {
                   best = x;
                 } else {
-                  const int r = beats(x, best, d, cLf);
+                  const int r = beats(x, best, d);
                   nex += r >> 1;
                   if (r & 1) {
                     best = x;
@@ -863,32 +990,9 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
           const int L = reinterpret_cast<const int32_t*>(rc + l.cL)[combo];
           const unsigned long long key = reinterpret_cast<const unsigned long long*>(rc + l.chash)[combo];
           const uint16_t* child = reinterpret_cast<const uint16_t*>(rc + l.ccols) + (size_t)combo * S;
-          bool dup = reinterpret_cast<const int32_t*>(rc + l.ctabu)[combo] != 0;
-          int slot = (int)(key & (unsigned long long)hmask);   // first empty slot after the probe
-          if (!dup) {
-            // within this generation: open addressing on the 64-bit hash; a
-            // hash match is confirmed on the columns of the earlier child
-            for (int probe = 0; probe <= hmask; ++probe) {
-              const unsigned long long kk = hkey[slot];
-              if (kk == 0ull) break;
-              if (kk == key) {
-                const int32_t r = href[slot];
-                const char* orec = d.rec + (size_t)(r / nc) * RB;
-                const int oc = r % nc;
-                const uint16_t* other = reinterpret_cast<const uint16_t*>(orec + l.ccols) + (size_t)oc * S;
-                const int oL = reinterpret_cast<const int32_t*>(orec + l.cL)[oc];
-                const bool same =
-                    oL == L &&
-                    __all_sync(0xffffffffu, lane >= L || other[lane] == child[lane]) &&
-                    __all_sync(0xffffffffu, lane + 32 >= L || other[lane + 32] == child[lane + 32]);
-                if (same) {
-                  dup = true;
-                  break;
-                }
-              }
-              slot = (slot + 1) & hmask;
-            }
-          }
+          int slot = 0;
+          const bool dup = reinterpret_cast<const int32_t*>(rc + l.ctabu)[combo] != 0 ||
+                           gen_duplicate<0>(d, l, hkey, href, hmask, nc, RB, key, child, L, lane, &slot);
           if (dup) {
             if (++hits > d.P) {
               stopped = INIT ? 2 : 1;
@@ -897,12 +1001,19 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
             continue;
           }
           const int32_t rec_id = (int32_t)(j * nc + combo);
-          if (lane < L) pen[child[lane]] += 1u;
-          if (lane + 32 < L) pen[child[lane + 32]] += 1u;
+          uint16_t* dst = d.seq + (size_t)(base + n) * S;
+          if (lane < L) {
+            pen[child[lane]] += 1u;
+            dst[lane] = child[lane];
+          }
+          if (lane + 32 < L) {
+            pen[child[lane + 32]] += 1u;
+            dst[lane + 32] = child[lane + 32];
+          }
           if (lane == 0) {
             hkey[slot] = key;
             href[slot] = rec_id;
-            acc[n] = rec_id;
+            d.len[base + n] = L;
           }
           __syncwarp();
           ++n;
@@ -921,7 +1032,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
     }
     if (tid == 0 && issued < nchunks) {
       const int j0 = issued * kB, cnt = min(kB, d.J - j0);
-      bulk_load(bufs[issued & 1], d.rec + (size_t)j0 * RB, (uint32_t)cnt * RB, &bars[issued & 1]);
+      bulk_load(buf0 + (issued & 1) * buf_bytes, d.rec + (size_t)j0 * RB, (uint32_t)cnt * RB,
+                &bars[issued & 1]);
       ++issued;
     }
   }
@@ -934,17 +1046,6 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
       if (!mbar_wait(&bars[c & 1], (uint32_t)((c >> 1) & 1))) s_fail = 1;
   }
   __syncthreads();
-  n = s_n;
-  // accepted children into the archive, in acceptance order after the elites
-  for (int i = tid; i < (n - E) * S; i += kBuildThreads) {
-    const int slot = E + i / S, c = i % S;
-    const int32_t r = acc[slot];
-    const char* rec = d.rec + (size_t)(r / nc) * RB;
-    const int L = reinterpret_cast<const int32_t*>(rec + l.cL)[r % nc];
-    if (c < L) d.seq[(size_t)(base + slot) * S + c] =
-        reinterpret_cast<const uint16_t*>(rec + l.ccols)[(size_t)(r % nc) * S + c];
-    if (c == 0) d.len[base + slot] = L;
-  }
   if (tid == 0) {
     Ctl* ctl = d.ctl;
     ctl->last_hits = hits;
@@ -1322,7 +1423,7 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
   EBIC_CUDA_TRY(cudaMemsetAsync(st->tkey.ptr, 0, tcap * sizeof(unsigned long long), s));
   EBIC_CUDA_TRY(cudaMemsetAsync(st->dec.ptr, 0, E * sizeof(uint32_t), s));
   // attempt records: sized for the larger (Steps 2-5) layout
-  st->rec_bytes = rec_layout(k, st->S, false).bytes;
+  st->rec_bytes = rec_layout(k, st->S, false, bit_words((h->C + 31) / 32)).bytes;
   EBIC_TRY(st->rec.reserve((size_t)st->J * st->rec_bytes));
   EBIC_TRY(st->list_ref.reserve((size_t)(T + P) * sizeof(int32_t)));
   EBIC_TRY(st->list_f.reserve((size_t)(T + P) * sizeof(double)));
@@ -1431,7 +1532,7 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
 
   // build: wset + accepted + pen + cL, then two record buffers of kB attempts
   const size_t fixed = (size_t)H * (sizeof(unsigned long long) + sizeof(int32_t)) +
-                       (size_t)P * sizeof(int32_t) + (size_t)h->C * sizeof(uint32_t) +
+                       (size_t)h->C * sizeof(uint32_t) +
                        (size_t)(p->len_max + 2) * sizeof(float) + 128;
   st->kB = 64;
   while (st->kB > 2 && fixed + 2 * (size_t)st->kB * st->rec_bytes > 200 * 1024) st->kB >>= 1;
