@@ -604,35 +604,52 @@ __device__ __noinline__ int pair_exact(const EaDev& d, const double* fx, const d
   return (px > py || (px == py && xlow)) ? 1 : 0;
 }
 
+// Equal series test of two children (lane-local).
+__device__ __forceinline__ bool same_cols(const uint16_t* a, const uint16_t* b, int L) {
+  for (int i = 0; i < L; ++i)
+    if (a[i] != b[i]) return false;
+  return true;
+}
+
 // The Step 3 consumer for tournaments of K <= 2 entrants and NW-word column
-// bitsets, run by one warp on one chunk of records in shared memory.  The 32
-// attempts of a sub-chunk (one per lane) are prepared in parallel: penalty
-// sums, the constants of both tournaments, entrant bitsets, outcomes.  The
-// scan then takes them in order.  For attempt b every later lane computes,
-// before the duplicate check of b is known, the penalty sums it would have if
-// b's child were accepted (sum += |entrant & child| from the bitsets) and the
-// outcome those sums give; the acceptance commits them.  Penalty counts are
-// brought up to date once per 32 attempts.  With K = 1 there is no
-// comparison, so no sums are tracked.
+// bitsets, run by one warp on one chunk of records in shared memory, 32
+// attempts (one per lane) at a time.
+//
+// The sequential rule -- each tournament sees the penalty counts left by every
+// earlier acceptance -- is solved as a fixpoint.  Assuming every attempt of
+// the batch is accepted, lane a's penalty sums are its sums at the batch
+// start plus |entrant & child_b| for the chosen child of every earlier lane
+// b; its outcome is the tournament result for those sums.  Starting from the
+// outcomes at the batch start, all lanes recompute their outcomes from the
+// current children of the earlier lanes until none changes (Jacobi
+// iteration).  Lane 0 is final after the first pass and lane k after pass k,
+// so the iteration stops after at most 32 passes, at the unique fixpoint: the
+// outcomes of taking the attempts one by one.  Then duplicates are found in
+// parallel (the record's tabu flag, a probe of this generation's hash set,
+// equal keys among earlier lanes of the batch), and the batch is committed up
+// to the first duplicate, which counts as a hit; the next batch starts after
+// it, from penalty counts that include every acceptance so far.
 template <int K, int NW>
-__device__ __forceinline__ void build_fast(const EaDev& d, const RecLayout& l, const char* cur,
-                                           int cnt, int j0, uint32_t* pen, const float* cLf,
-                                           unsigned long long* hkey, int32_t* href,
-                                           long long base, int hmask, int RB, int lane, int& n,
-                                           int& hits, int& stopped, long long& attempts,
-                                           long long& exact) {
+__device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, const char* cur,
+                                            int cnt, int j0, uint32_t* pen, const float* cLf,
+                                            unsigned long long* hkey, int32_t* href,
+                                            int* s_dec, uint4* s_cw, long long base, int hmask,
+                                            int RB,
+                                            int lane, int& n, int& hits, int& stopped,
+                                            long long& attempts, long long& exact) {
   constexpr int NE = 2 * K, NC = K * K, NV = NW / 4;
   const int S = d.S;
-  for (int sb = 0; sb < cnt && n < d.P && !stopped; sb += 32) {
-    const int a = sb + lane;
-    const bool have = a < cnt;
-    const char* ra = cur + (size_t)(have ? a : sb) * RB;
+  const unsigned FULL = 0xffffffffu;
+  int sb = 0;
+  while (sb < cnt && n < d.P && !stopped) {
+    const int avail = min(32, cnt - sb);
+    const bool have = lane < avail;
+    const char* ra = cur + (size_t)(have ? sb + lane : sb) * RB;
     const int cr = have ? *reinterpret_cast<const int32_t*>(ra + l.cross) : 0;
     int32_t Sx[NE], Lx[NE];
     uint4 bits[NE][NV];
     PairConst pc[2];
     const double* efa = reinterpret_cast<const double*>(ra + l.ef);
-    int dec = 0, nex = 0;
     if (K == 2) {
       float ln[NE], cl[NE];
       int32_t id[NE];
@@ -665,104 +682,195 @@ __device__ __forceinline__ void build_fast(const EaDev& d, const RecLayout& l, c
       pc[0] = pair_const(ln[1], ln[0], cl[1], cl[0], id[1], id[0], Sx[1], Sx[0], Lx[1], Lx[0]);
       pc[1] = pair_const(ln[3], ln[2], cl[3], cl[2], id[3], id[2], Sx[3], Sx[2], Lx[3], Lx[2]);
     }
-    // outcome (ta * K + tb) of this lane's attempt for penalty sums s[]
-    auto decide = [&](const int32_t (&sx)[NE], int* ne) -> int {
+    auto decide = [&](int* ne) -> int {
       if (K == 1 || !have) return 0;
-      int ta = pair_fast(pc[0], sx[1], sx[0]);
+      int ta = pair_fast(pc[0], Sx[1], Sx[0]);
       if (ta < 0) {
-        ta = pair_exact(d, efa + 1, efa + 0, Lx[1], Lx[0], sx[1], sx[0], pc[0].xlow);
+        ta = pair_exact(d, efa + 1, efa + 0, Lx[1], Lx[0], Sx[1], Sx[0], pc[0].xlow);
         ++*ne;
       }
       int tb = 0;
       if (cr) {
-        tb = pair_fast(pc[1], sx[3], sx[2]);
+        tb = pair_fast(pc[1], Sx[3], Sx[2]);
         if (tb < 0) {
-          tb = pair_exact(d, efa + 3, efa + 2, Lx[3], Lx[2], sx[3], sx[2], pc[1].xlow);
+          tb = pair_exact(d, efa + 3, efa + 2, Lx[3], Lx[2], Sx[3], Sx[2], pc[1].xlow);
           ++*ne;
         }
       }
       return ta * K + tb;
     };
-    dec = decide(Sx, &nex);
-    bool mine = false;
-    int my_combo = 0, my_slot = 0, done = 0;
-    for (int b = 0; b < 32 && sb + b < cnt; ++b) {
-      if (n >= d.P) break;
-      const int combo = __shfl_sync(0xffffffffu, dec, b);
-      const char* rb = cur + (size_t)(sb + b) * RB;
-      ++done;
-      const int L = reinterpret_cast<const int32_t*>(rb + l.cL)[combo];
-      const unsigned long long key = reinterpret_cast<const unsigned long long*>(rb + l.chash)[combo];
-      const int tabu = reinterpret_cast<const int32_t*>(rb + l.ctabu)[combo];
-      int slot = (int)(key & (unsigned long long)hmask);
-      const unsigned long long kk = hkey[slot];
-      // speculative: sums and outcome of the later lanes if b's child is accepted
-      int32_t Sy[NE];
-      int dec2 = dec, nex2 = nex;
-      if (K == 2) {
-        uint4 cw[NV];
-        const uint4* cb = reinterpret_cast<const uint4*>(rb + l.cbit) + combo * NV;
+    // overlaps of this lane's entrants with another lane's child bitset
+    auto add_overlap = [&](const uint4 (&w)[NV], int sign) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) cw[v] = cb[v];
+      for (int e = 0; e < NE; ++e) {
+        int inter = 0;
 #pragma unroll
-        for (int e = 0; e < NE; ++e) {
-          uint32_t inter = 0;
+        for (int v = 0; v < NV; ++v)
+          inter += __popc(bits[e][v].x & w[v].x) + __popc(bits[e][v].y & w[v].y) +
+                   __popc(bits[e][v].z & w[v].z) + __popc(bits[e][v].w & w[v].w);
+        Sx[e] += sign * inter;
+      }
+    };
+    int nex = 0;
+    int dec = decide(&nex);
+    uint4 cw[NV];                       // bitset of this lane's current child
+    if (K == 2) {
+      const uint4* cb = reinterpret_cast<const uint4*>(ra + l.cbit) + dec * NV;
 #pragma unroll
-          for (int v = 0; v < NV; ++v)
-            inter += __popc(bits[e][v].x & cw[v].x) + __popc(bits[e][v].y & cw[v].y) +
-                     __popc(bits[e][v].z & cw[v].z) + __popc(bits[e][v].w & cw[v].w);
-          Sy[e] = Sx[e] + (int32_t)inter;
-        }
-        nex2 = 0;
-        dec2 = decide(Sy, &nex2);
-      }
-      const uint16_t* child = reinterpret_cast<const uint16_t*>(rb + l.ccols) + (size_t)combo * S;
-      bool dup = tabu != 0;
-      if (!dup && kk != 0ull)
-        dup = gen_duplicate<NC>(d, l, hkey, href, hmask, NC, RB, key, child, L, lane, &slot);
-      if (dup) {
-        if (++hits > d.P) {
-          stopped = 1;
-          break;
-        }
-        continue;
-      }
-      const int32_t rec_id = (int32_t)((j0 + sb + b) * NC + combo);
-      if (lane == 0) {
-        hkey[slot] = key;
-        href[slot] = rec_id;
-      }
-      mine = mine || lane == b;
-      my_combo = lane == b ? combo : my_combo;
-      my_slot = lane == b ? n : my_slot;
-      if (K == 2) {
-        const bool later = lane > b;
+      for (int v = 0; v < NV; ++v) cw[v] = cb[v];
+      // pass 0: every earlier lane's child, assuming all are accepted (the
+      // children's bitsets broadcast from shared memory)
 #pragma unroll
-        for (int e = 0; e < NE; ++e) Sx[e] = later ? Sy[e] : Sx[e];
-        dec = later ? dec2 : dec;
-        nex = later ? nex2 : nex;
+      for (int v = 0; v < NV; ++v) s_cw[lane * NV + v] = cw[v];
+      __syncwarp();
+#pragma unroll 4
+      for (int b = 0; b < 31; ++b) {
+        if (b + 1 >= avail) break;
+        uint4 w[NV];
+#pragma unroll
+        for (int v = 0; v < NV; ++v) w[v] = s_cw[b * NV + v];
+        if (lane > b) add_overlap(w, 1);
       }
-      ++n;
+      __syncwarp();
     }
-    attempts += done;
-    // exact-path decisions among the attempts taken; then each accepted child
-    // goes, from shared memory, into its archive slot and the penalty counts
-    int ex = lane < done ? nex : 0;
+    // lanes below `first` are settled (committed, or excluded as hits)
+    int first = 0;
+    bool done_batch = false;
+    while (!done_batch) {
+      if (K == 2) {
+        // Jacobi passes until no outcome changes (at most 32 passes)
+        for (int pass = 0; pass < 33; ++pass) {
+          int nx = 0;
+          const int nd = decide(&nx);
+          unsigned changed = __ballot_sync(FULL, have && lane >= first && nd != dec);
+          if (!changed) break;
+          uint4 nw[NV];
+          const uint4* nb = reinterpret_cast<const uint4*>(ra + l.cbit) + nd * NV;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ex += __shfl_xor_sync(0xffffffffu, ex, o);
-    exact += ex;
-    if (mine) {
-      const uint16_t* ch = reinterpret_cast<const uint16_t*>(ra + l.ccols) + (size_t)my_combo * S;
-      const int Lc = reinterpret_cast<const int32_t*>(ra + l.cL)[my_combo];
-      uint16_t* dst = d.seq + (size_t)(base + my_slot) * S;
-      for (int c = 0; c < Lc; ++c) {
-        const uint16_t v = ch[c];
-        dst[c] = v;
-        atomicAdd(&pen[v], 1u);
+          for (int v = 0; v < NV; ++v) nw[v] = nb[v];
+          while (changed) {
+            const int b = __ffs(changed) - 1;
+            changed &= changed - 1;
+            uint4 wo[NV], wn[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              wo[v].x = __shfl_sync(FULL, cw[v].x, b);
+              wo[v].y = __shfl_sync(FULL, cw[v].y, b);
+              wo[v].z = __shfl_sync(FULL, cw[v].z, b);
+              wo[v].w = __shfl_sync(FULL, cw[v].w, b);
+              wn[v].x = __shfl_sync(FULL, nw[v].x, b);
+              wn[v].y = __shfl_sync(FULL, nw[v].y, b);
+              wn[v].z = __shfl_sync(FULL, nw[v].z, b);
+              wn[v].w = __shfl_sync(FULL, nw[v].w, b);
+            }
+            if (lane > b) {
+              add_overlap(wo, -1);
+              add_overlap(wn, 1);
+            }
+          }
+          if (lane >= first) {
+            dec = nd;
+            nex = nx;
+#pragma unroll
+            for (int v = 0; v < NV; ++v) cw[v] = nw[v];
+          }
+        }
       }
-      d.len[base + my_slot] = Lc;
+      // duplicates: tabu flag, this generation's hash set (which holds every
+      // child committed so far), equal keys among unsettled earlier lanes
+      const bool live = have && lane >= first;
+      const unsigned long long key =
+          have ? reinterpret_cast<const unsigned long long*>(ra + l.chash)[dec] : 0ull;
+      const int L = have ? reinterpret_cast<const int32_t*>(ra + l.cL)[dec] : 0;
+      const uint16_t* child = reinterpret_cast<const uint16_t*>(ra + l.ccols) + (size_t)dec * S;
+      bool dup = live && reinterpret_cast<const int32_t*>(ra + l.ctabu)[dec] != 0;
+      if (live && !dup) {
+        int sl = (int)(key & (unsigned long long)hmask);
+        for (int probe = 0; probe <= hmask; ++probe) {
+          const unsigned long long kk = hkey[sl];
+          if (kk == 0ull) break;
+          if (kk == key) {
+            const int32_t r = href[sl];
+            const char* orec = d.rec + (size_t)(r / NC) * RB;
+            const int oc = r % NC;
+            if (reinterpret_cast<const int32_t*>(orec + l.cL)[oc] == L &&
+                same_cols(reinterpret_cast<const uint16_t*>(orec + l.ccols) + (size_t)oc * S,
+                          child, L)) {
+              dup = true;
+              break;
+            }
+          }
+          sl = (sl + 1) & hmask;
+        }
+      }
+      s_dec[lane] = dec;
+      __syncwarp();
+      unsigned twins = __match_any_sync(FULL, key) & ((1u << lane) - 1u) & ~((1u << first) - 1u);
+      if (!live) twins = 0u;
+      while (twins && !dup) {
+        const int b = __ffs(twins) - 1;
+        twins &= twins - 1;
+        const char* rbb = cur + (size_t)(sb + b) * RB;
+        const int db = s_dec[b];
+        if (reinterpret_cast<const int32_t*>(rbb + l.cL)[db] == L &&
+            same_cols(reinterpret_cast<const uint16_t*>(rbb + l.ccols) + (size_t)db * S, child, L))
+          dup = true;
+      }
+      __syncwarp();
+      // commit lanes first .. first_dup - 1, as far as the population needs
+      const unsigned dupmask = __ballot_sync(FULL, dup);
+      const int first_dup = dupmask ? __ffs(dupmask) - 1 : avail;
+      const int need = d.P - n;
+      const int nacc = min(first_dup - first, need);
+      const bool hit = first_dup < avail && first_dup - first < need;
+      const int processed = nacc + (hit ? 1 : 0);
+      const int k = lane - first;
+      if (k >= 0 && k < nacc) {
+        const int32_t rec_id = (int32_t)((j0 + sb + lane) * NC + dec);
+        int sl = (int)(key & (unsigned long long)hmask);
+        for (int probe = 0; probe <= hmask; ++probe) {
+          if (atomicCAS(&hkey[sl], 0ull, key) == 0ull) {
+            href[sl] = rec_id;
+            break;
+          }
+          sl = (sl + 1) & hmask;
+        }
+        uint16_t* dst = d.seq + (size_t)(base + n + k) * S;
+        for (int c = 0; c < L; ++c) {
+          const uint16_t v = child[c];
+          dst[c] = v;
+          atomicAdd(&pen[v], 1u);
+        }
+        d.len[base + n + k] = L;
+      }
+      int ex = (k >= 0 && k < processed) ? nex : 0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ex += __shfl_xor_sync(FULL, ex, o);
+      exact += ex;
+      attempts += processed;
+      n += nacc;
+      if (hit && ++hits > d.P) stopped = 1;
+      if (hit && !stopped && n < d.P && first_dup + 1 < avail) {
+        // the hit's child is not accepted: take it out of the later lanes'
+        // sums and go on with the rest of the batch
+        if (K == 2) {
+          uint4 wo[NV];
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            wo[v].x = __shfl_sync(FULL, cw[v].x, first_dup);
+            wo[v].y = __shfl_sync(FULL, cw[v].y, first_dup);
+            wo[v].z = __shfl_sync(FULL, cw[v].z, first_dup);
+            wo[v].w = __shfl_sync(FULL, cw[v].w, first_dup);
+          }
+          if (lane > first_dup) add_overlap(wo, -1);
+        }
+        first = first_dup + 1;
+      } else {
+        sb += first + processed;
+        done_batch = true;
+      }
+      __syncwarp();
     }
-    __syncwarp();
   }
 }
 
@@ -842,6 +950,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
   const size_t buf_bytes = (size_t)kB * RB;
   __shared__ __align__(8) unsigned long long bars[2];
   __shared__ int s_n, s_done, s_E, s_fail;
+  __shared__ int s_dec[32];              // outcomes of the batch's lanes (fast path)
+  __shared__ uint4 s_cw[32 * 2];         // their children's bitsets (fast path)
   // fast path: tournaments of at most 2 entrants, column sets of at most 256 bits
   const bool fast = d.k <= 2 && l.nw > 0;
 
@@ -902,17 +1012,21 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
       } else if (!INIT && fast) {
         if (k == 2) {
           if (l.nw == 4)
-            build_fast<2, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, base, hmask, RB,
+            build_batch<2, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, base,
+                              hmask, RB,
                              lane, n, hits, stopped, attempts, exact);
           else
-            build_fast<2, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, base, hmask, RB,
+            build_batch<2, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, base,
+                              hmask, RB,
                              lane, n, hits, stopped, attempts, exact);
         } else {
           if (l.nw == 4)
-            build_fast<1, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, base, hmask, RB,
+            build_batch<1, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, base,
+                              hmask, RB,
                              lane, n, hits, stopped, attempts, exact);
           else
-            build_fast<1, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, base, hmask, RB,
+            build_batch<1, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, base,
+                              hmask, RB,
                              lane, n, hits, stopped, attempts, exact);
         }
       } else {
@@ -1251,6 +1365,220 @@ __global__ void __launch_bounds__(kRankThreads) k_rank(EaDev d, int Pp) {
 }
 
 // ---------------------------------------------------------------------------
+// k_rank_warp: the same Step 5 for column sets of at most NW * 32 columns.
+// The whole CTA sorts (as k_rank) and then prefetches, in visiting order, each
+// individual's fitness, length and column bitset, and the bitsets of the
+// listed records, into shared memory.  The visit itself -- sequential by
+// definition -- is run by warp 0 alone from shared memory: overlaps are
+// popcounts of bitset intersections, |a & b| > tau * min(|a|, |b|) is an
+// integer test against floor(tau * m) (the binary64 product, as in k_rank),
+// and evictions and the insertion are stable warp-wide compactions and
+// shifts, with no CTA barrier per individual.
+//
+// Shared memory: skey[Pp] (u64) | sidx[Pp] | pf[P] (f64) | pL[P] | pbits[P][NW] |
+//                lf[cap] (f64) | lr[cap] | lL[cap] | lbits[cap][NW] | thr[Lmax + 1]
+// ---------------------------------------------------------------------------
+constexpr int kRankWarpThreads = 512;   // register room for the deciding warp
+
+template <int NW>
+__global__ void __launch_bounds__(kRankWarpThreads) k_rank_warp(EaDev d, int Pp) {
+  extern __shared__ unsigned long long smem_u64[];
+  if (*(volatile int32_t*)&d.ctl->stop) return;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int g = d.ctl->gen;
+  const long long base = (long long)g * d.P;
+  const int cap = d.T + d.P, P = d.P;
+  unsigned long long* skey = smem_u64;
+  int32_t* sidx = reinterpret_cast<int32_t*>(skey + Pp);
+  double* pf = reinterpret_cast<double*>(sidx + Pp + (Pp & 1));
+  double* lf = pf + P;
+  int32_t* pL = reinterpret_cast<int32_t*>(lf + cap);
+  int32_t* lr = pL + P;
+  int32_t* lL = lr + cap;
+  int32_t* thr = lL + cap;
+  uint32_t* pbits = reinterpret_cast<uint32_t*>(thr + ((d.Lmax + 1 + 3) & ~3));
+  uint32_t* lbits = pbits + (size_t)P * NW;
+
+  for (int i = tid; i < Pp; i += kRankWarpThreads) {
+    if (i < P) {
+      skey[i] = ~(unsigned long long)__double_as_longlong(d.fit[base + i]);
+      sidx[i] = i;
+    } else {
+      skey[i] = ~0ull;
+      sidx[i] = 0x7fffffff;
+    }
+  }
+  for (int m = tid; m <= d.Lmax; m += kRankWarpThreads) thr[m] = (int32_t)floor(d.tau * (double)m);
+  int n = d.ctl->n_top;
+  // the listed records: reference, fitness, length, bitset
+  for (int t = tid; t < n; t += kRankWarpThreads) {
+    const int32_t r = d.list_ref[t];
+    lr[t] = r;
+    lf[t] = d.list_f[t];
+    const int L = d.len[r];
+    lL[t] = L;
+    uint32_t* b = lbits + (size_t)t * NW;     // this thread's entry
+#pragma unroll
+    for (int w = 0; w < NW; ++w) b[w] = 0u;
+    const uint16_t* sq = d.seq + (size_t)r * d.S;
+    for (int c = 0; c < L; ++c) b[sq[c] >> 5] |= 1u << (sq[c] & 31);
+  }
+  __syncthreads();
+  for (int size = 2; size <= Pp; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      for (int i = tid; i < Pp; i += kRankWarpThreads) {
+        const int jx = i ^ stride;
+        if (jx > i) {
+          const bool up = (i & size) == 0;
+          const unsigned long long ka = skey[i], kb = skey[jx];
+          const int ia = sidx[i], ib = sidx[jx];
+          const bool a_gt_b = ka > kb || (ka == kb && ia > ib);
+          if (a_gt_b == up) {
+            skey[i] = kb;
+            skey[jx] = ka;
+            sidx[i] = ib;
+            sidx[jx] = ia;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // individuals in visiting order: fitness, length, bitset
+  for (int oi = tid; oi < P; oi += kRankWarpThreads) {
+    const long long xe = base + sidx[oi];
+    pf[oi] = d.fit[xe];
+    const int L = d.len[xe];
+    pL[oi] = L;
+    uint32_t* b = pbits + (size_t)oi * NW;    // this thread's entry
+#pragma unroll
+    for (int w = 0; w < NW; ++w) b[w] = 0u;
+    const uint16_t* sq = d.seq + (size_t)xe * d.S;
+    for (int c = 0; c < L; ++c) b[sq[c] >> 5] |= 1u << (sq[c] & 31);
+  }
+  __syncthreads();
+
+  if (tid < 32) {
+    for (int oi = 0; oi < P; ++oi) {
+      const double xf = pf[oi];
+      const int xL = pL[oi];
+      uint32_t xb[NW];
+#pragma unroll
+      for (int w = 0; w < NW; ++w) xb[w] = pbits[(size_t)oi * NW + w];
+      // records strictly fitter, and overlapping records of higher or equal
+      // fitness (which block x)
+      int above = 0;
+      bool block = false;
+      for (int t0 = 0; t0 < n; t0 += 32) {
+        const int t = t0 + lane;
+        if (t < n) {
+          const double f = lf[t];
+          above += f > xf ? 1 : 0;
+          if (f >= xf) {
+            int inter = 0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) inter += __popc(lbits[(size_t)t * NW + w] & xb[w]);
+            block = block || inter > thr[min(lL[t], xL)];
+          }
+        }
+      }
+      above = __reduce_add_sync(0xffffffffu, (unsigned)above);
+      if (above >= d.T) break;                            // see k_rank
+      if (__any_sync(0xffffffffu, block)) continue;
+      // stable compaction of the records kept (not: overlapping and less fit),
+      // counting those of higher or equal fitness (x goes after them)
+      int m = 0, pos = 0;
+      for (int t0 = 0; t0 < n; t0 += 32) {
+        const int t = t0 + lane;
+        bool keep = false;
+        double f = 0.0;
+        int32_t r = 0, L = 0;
+        uint32_t b[NW];
+        if (t < n) {
+          f = lf[t];
+          r = lr[t];
+          L = lL[t];
+          int inter = 0;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) {
+            b[w] = lbits[(size_t)t * NW + w];
+            inter += __popc(b[w] & xb[w]);
+          }
+          keep = !(inter > thr[min(L, xL)] && f < xf);
+        }
+        const unsigned bal = __ballot_sync(0xffffffffu, keep);
+        const unsigned ge = __ballot_sync(0xffffffffu, keep && f >= xf);
+        __syncwarp();
+        if (keep) {
+          const int dst = m + __popc(bal & ((1u << lane) - 1u));
+          lf[dst] = f;
+          lr[dst] = r;
+          lL[dst] = L;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) lbits[(size_t)dst * NW + w] = b[w];
+        }
+        __syncwarp();
+        m += __popc(bal);
+        pos += __popc(ge);
+      }
+      // shift [pos, m) up by one, from the end, and place x at pos
+      for (int t0 = ((m - 1) & ~31); t0 >= pos - 31 && t0 >= 0; t0 -= 32) {
+        const int t = t0 + lane;
+        const bool mv = t >= pos && t < m;
+        double f = 0.0;
+        int32_t r = 0, L = 0;
+        uint32_t b[NW];
+        if (mv) {
+          f = lf[t];
+          r = lr[t];
+          L = lL[t];
+#pragma unroll
+          for (int w = 0; w < NW; ++w) b[w] = lbits[(size_t)t * NW + w];
+        }
+        __syncwarp();
+        if (mv) {
+          lf[t + 1] = f;
+          lr[t + 1] = r;
+          lL[t + 1] = L;
+#pragma unroll
+          for (int w = 0; w < NW; ++w) lbits[(size_t)(t + 1) * NW + w] = b[w];
+        }
+        __syncwarp();
+      }
+      if (lane == 0) {
+        lf[pos] = xf;
+        lr[pos] = (int32_t)(base + sidx[oi]);
+        lL[pos] = xL;
+      }
+#pragma unroll
+      for (int w = 0; w < NW; ++w)
+        if (lane == w) lbits[(size_t)pos * NW + w] = xb[w];
+      __syncwarp();
+      n = m + 1;
+    }
+    if (n > d.T) n = d.T;
+    for (int i = lane; i < n; i += 32) {
+      d.list_ref[i] = lr[i];
+      d.list_f[i] = lf[i];
+    }
+    if (lane == 0) {
+      Ctl* ctl = d.ctl;
+      ctl->n_top = n;
+      ctl->evals_total += d.P;
+      if (g > 0) ctl->gens_done = g;
+      ctl->gen = g + 1;
+    }
+  }
+}
+
+// Shared bytes of k_rank_warp<NW> for population P (padded Pp), list T.
+static size_t rank_warp_smem(int P, int Pp, int T, int Lmax, int NW) {
+  const size_t cap = (size_t)T + P;
+  return (size_t)Pp * 12 + 4 * (Pp & 1) + ((size_t)P + cap) * 8 + ((size_t)P + 2 * cap) * 4 +
+         (size_t)((Lmax + 1 + 3) & ~3) * 4 + ((size_t)P + cap) * NW * 4;
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 struct EaState {
@@ -1266,6 +1594,7 @@ struct EaState {
   DevBuf ctl, gather;
   HostBuf h_ctl, h_gather;
   size_t smem_build = 0, smem_rank = 0;
+  int32_t rank_nw = 0;           // k_rank_warp<rank_nw> (0: k_rank)
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   EaDev dev{};
@@ -1352,6 +1681,15 @@ static ebic_status launch_records(EaState* st, cudaStream_t s, int* n) {
   return EBIC_OK;
 }
 
+static void launch_rank(const EaState* st, cudaStream_t s) {
+  if (st->rank_nw == 4)
+    k_rank_warp<4><<<1, kRankWarpThreads, st->smem_rank, s>>>(st->dev, st->Pp);
+  else if (st->rank_nw == 8)
+    k_rank_warp<8><<<1, kRankWarpThreads, st->smem_rank, s>>>(st->dev, st->Pp);
+  else
+    k_rank<<<1, kRankThreads, st->smem_rank, s>>>(st->dev, st->Pp);
+}
+
 static ebic_status launch_generation(ebic_ctx* h, EaState* st, bool init, cudaStream_t s) {
   const EaDev& d = st->dev;
   if (init) {
@@ -1367,7 +1705,7 @@ static ebic_status launch_generation(ebic_ctx* h, EaState* st, bool init, cudaSt
   k_tabu_insert<<<(unsigned)((st->p.pop_size + 255) / 256), 256, 0, s>>>(d);
   EBIC_CUDA_TRY(cudaGetLastError());
   EBIC_TRY(eval_archive(h, st->apop, st->eargs, s));
-  k_rank<<<1, kRankThreads, st->smem_rank, s>>>(d, st->Pp);
+  launch_rank(st, s);
   EBIC_CUDA_TRY(cudaGetLastError());
   return EBIC_OK;
 }
@@ -1541,6 +1879,16 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
   st->smem_rank = (size_t)st->Pp * (sizeof(unsigned long long) + sizeof(int32_t)) +
                   cap * (2 * sizeof(double) + 2 * sizeof(int32_t)) + ((cap + 15) & ~(size_t)15) +
                   (size_t)st->WC * sizeof(uint32_t);
+  // Step 5 by one warp from shared bitsets when the columns and sizes allow
+  st->rank_nw = 0;
+  const int rnw = bit_words(st->WC);
+  if (rnw) {
+    const size_t need = rank_warp_smem(P, st->Pp, T, p->len_max, rnw);
+    if (need <= 200 * 1024) {
+      st->rank_nw = rnw;
+      st->smem_rank = need;
+    }
+  }
   if (st->smem_build > 220 * 1024 || st->smem_rank > 220 * 1024)
     return fail(EBIC_ERR_ARG, "population / top-rank sizes need more shared memory than a CTA has "
                               "(build %zu B, rank %zu B)", st->smem_build, st->smem_rank);
@@ -1548,8 +1896,15 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
                                      (int)st->smem_build));
   EBIC_CUDA_TRY(cudaFuncSetAttribute(k_build<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)st->smem_build));
-  EBIC_CUDA_TRY(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)st->smem_rank));
+  if (st->rank_nw == 4)
+    EBIC_CUDA_TRY(cudaFuncSetAttribute(k_rank_warp<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)st->smem_rank));
+  else if (st->rank_nw == 8)
+    EBIC_CUDA_TRY(cudaFuncSetAttribute(k_rank_warp<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)st->smem_rank));
+  else
+    EBIC_CUDA_TRY(cudaFuncSetAttribute(k_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)st->smem_rank));
 
   // The pair table pays for itself over a run; build it when it fits.
   if (h->path != EBIC_PATH_GATHER && !h->LT) {
@@ -1574,7 +1929,7 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
     float us = 0.f;
     EBIC_TRY(autotune_archive(h, st->apop, a, s, &us));
   }
-  k_rank<<<1, kRankThreads, st->smem_rank, s>>>(dd, st->Pp);
+  launch_rank(st, s);
   count_launches(1);
   EBIC_CUDA_TRY(cudaGetLastError());
 
@@ -1692,7 +2047,7 @@ static ebic_status run_step_profiled(ebic_ctx* h, float* us) {
   ebic_status es = eval_archive(h, st->apop, st->eargs, s);
   h->tuning = user;
   cudaEventRecord(ev[4], s);
-  k_rank<<<1, kRankThreads, st->smem_rank, s>>>(d, st->Pp);
+  launch_rank(st, s);
   cudaEventRecord(ev[5], s);
   count_launches((uint64_t)(3 + nrec));
   cudaError_t e = cudaEventSynchronize(ev[5]);

@@ -212,3 +212,19 @@ def test_screen_argument_errors():
         eb.ebic_run_screen(h, None, 1, eb.SCREEN_OFF)
     finally:
         eb.ebic_free(h)
+
+
+def test_wide_matrix_generic_paths():
+    """More than 256 columns: the builder's generic consumer and the CTA-wide
+    Step 5 (the bitset paths need at most 256 columns)."""
+    rng = np.random.default_rng(7)
+    A = rng.standard_normal((300, 300)).astype(np.float32)
+    run_both(A, iterations=6, len_max=8)
+
+
+@pytest.mark.parametrize("P,T", [(37, 3), (300, 250), (1024, 1)])
+def test_population_and_list_sizes(P, T):
+    """Populations that are not powers of two, lists shorter and longer than
+    a warp's chunk, a list of one."""
+    prob = synth.matrix_tiny(seed=5)
+    run_both(prob.A, iterations=5, pop_size=P, toprank_size=T, len_max=6)
