@@ -604,6 +604,30 @@ __device__ __noinline__ int pair_exact(const EaDev& d, const double* fx, const d
   return (px > py || (px == py && xlow)) ? 1 : 0;
 }
 
+// Carry-save adder: a + b + c = 2 h + l, bit by bit.
+__device__ __forceinline__ void csa(uint32_t& h, uint32_t& l, uint32_t a, uint32_t b, uint32_t c) {
+  const uint32_t u = a ^ b;
+  h = (a & b) | (u & c);
+  l = u ^ c;
+}
+
+// Harley-Seal accumulation of eight words into bit-sliced counters: keeps
+// ones + 2 twos + 4 fours + 8 eights (ones, twos, fours counted bit by bit)
+// equal to the number of set bits added so far, with one popcount per eight
+// words instead of eight.
+__device__ __forceinline__ void hs8(const uint32_t (&v)[8], uint32_t& ones, uint32_t& twos,
+                                    uint32_t& fours, int& eights) {
+  uint32_t c1, s1, c2, s2, c3, s3, c4, d1, e1, d2, f1;
+  csa(c1, s1, v[0], v[1], v[2]);
+  csa(c2, s2, v[3], v[4], v[5]);
+  csa(c3, s3, s1, s2, v[6]);
+  csa(c4, ones, ones, s3, v[7]);
+  csa(d1, e1, c1, c2, c3);
+  csa(d2, twos, twos, e1, c4);
+  csa(f1, fours, fours, d1, d2);
+  eights += __popc(f1);
+}
+
 // Equal series test of two children (lane-local).
 __device__ __forceinline__ bool same_cols(const uint16_t* a, const uint16_t* b, int L) {
   for (int i = 0; i < L; ++i)
@@ -723,14 +747,43 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
 #pragma unroll
       for (int v = 0; v < NV; ++v) s_cw[lane * NV + v] = cw[v];
       __syncwarp();
-#pragma unroll 4
-      for (int b = 0; b < 31; ++b) {
-        if (b + 1 >= avail) break;
-        uint4 w[NV];
+      // children b < avail - 1, two at a time; child b counts for lanes > b
+      uint32_t h1[NE], h2[NE], h4[NE];
+      int h8[NE];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) w[v] = s_cw[b * NV + v];
-        if (lane > b) add_overlap(w, 1);
+      for (int e = 0; e < NE; ++e) {
+        h1[e] = h2[e] = h4[e] = 0u;
+        h8[e] = 0;
       }
+      for (int b = 0; b + 1 < avail; b += 2) {
+        uint32_t m[2][NW];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+          const bool on = lane > b + i;
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const uint4 w = s_cw[(b + i) * NV + v];
+            m[i][4 * v + 0] = on ? w.x : 0u;
+            m[i][4 * v + 1] = on ? w.y : 0u;
+            m[i][4 * v + 2] = on ? w.z : 0u;
+            m[i][4 * v + 3] = on ? w.w : 0u;
+          }
+        }
+#pragma unroll
+        for (int e = 0; e < NE; ++e) {
+#pragma unroll
+          for (int v = 0; v < NV; ++v) {
+            const uint32_t x[8] = {bits[e][v].x & m[0][4 * v], bits[e][v].y & m[0][4 * v + 1],
+                                   bits[e][v].z & m[0][4 * v + 2], bits[e][v].w & m[0][4 * v + 3],
+                                   bits[e][v].x & m[1][4 * v], bits[e][v].y & m[1][4 * v + 1],
+                                   bits[e][v].z & m[1][4 * v + 2], bits[e][v].w & m[1][4 * v + 3]};
+            hs8(x, h1[e], h2[e], h4[e], h8[e]);
+          }
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < NE; ++e)
+        Sx[e] += 8 * h8[e] + 4 * __popc(h4[e]) + 2 * __popc(h2[e]) + __popc(h1[e]);
       __syncwarp();
     }
     // lanes below `first` are settled (committed, or excluded as hits)
