@@ -628,6 +628,78 @@ __device__ __forceinline__ void hs8(const uint32_t (&v)[8], uint32_t& ones, uint
   eights += __popc(f1);
 }
 
+// Named barrier 1 over the builder's CTA: warp 0 and the helper warps meet
+// there twice per batch (job posted, shares done) and once per chunk (release).
+constexpr int kBuildThreads = 128;
+__device__ __forceinline__ void bar_team() {
+  asm volatile("bar.sync 1, %0;" ::"n"(kBuildThreads) : "memory");
+}
+
+// One entrant's share of a batch's overlap pass: for the attempt of lane a
+// (record sb + a of the chunk), sum over earlier lanes b < a of
+// |entrant e & child_b|, the children's bitsets in s_cw (Harley-Seal).
+template <int K, int NV>
+__device__ __forceinline__ int pass0_share(const RecLayout& l, const char* cur, int sb, int avail,
+                                           int e, int lane, int RB, const uint4* s_cw) {
+  constexpr int NW = 4 * NV;
+  const bool have = lane < avail;
+  const char* ra = cur + (size_t)(have ? sb + lane : sb) * RB;
+  const int cr = have ? *reinterpret_cast<const int32_t*>(ra + l.cross) : 0;
+  const bool on = have && (e < K || cr);
+  uint4 bits[NV];
+#pragma unroll
+  for (int v = 0; v < NV; ++v)
+    bits[v] = on ? reinterpret_cast<const uint4*>(ra + l.ebit)[e * NV + v]
+                 : make_uint4(0u, 0u, 0u, 0u);
+  uint32_t h1 = 0u, h2 = 0u, h4 = 0u;
+  int h8 = 0;
+  for (int b = 0; b + 1 < avail; b += 2) {
+    uint32_t m[2][NW];
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      const bool in = lane > b + i;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        const uint4 w = s_cw[(b + i) * NV + v];
+        m[i][4 * v + 0] = in ? w.x : 0u;
+        m[i][4 * v + 1] = in ? w.y : 0u;
+        m[i][4 * v + 2] = in ? w.z : 0u;
+        m[i][4 * v + 3] = in ? w.w : 0u;
+      }
+    }
+#pragma unroll
+    for (int v = 0; v < NV; ++v) {
+      const uint32_t x[8] = {bits[v].x & m[0][4 * v], bits[v].y & m[0][4 * v + 1],
+                             bits[v].z & m[0][4 * v + 2], bits[v].w & m[0][4 * v + 3],
+                             bits[v].x & m[1][4 * v], bits[v].y & m[1][4 * v + 1],
+                             bits[v].z & m[1][4 * v + 2], bits[v].w & m[1][4 * v + 3]};
+      hs8(x, h1, h2, h4, h8);
+    }
+  }
+  return 8 * h8 + 4 * __popc(h4) + 2 * __popc(h2) + __popc(h1);
+}
+
+// Shared words of the builder's team protocol.
+struct Team {
+  int job, sb, avail;
+  int ov[32 * 4];       // entrant e of lane a: ov[4 a + e]
+};
+
+// Helper warps (1 .. 3) during one chunk of the fast path: each batch they
+// compute the overlap share of entrant `warp` for all 32 lanes; a job of 0
+// ends the chunk.
+template <int NV>
+__device__ __forceinline__ void team_helper(const RecLayout& l, const char* cur, int RB,
+                                            int warp, int lane, Team* tm, const uint4* s_cw) {
+  for (;;) {
+    bar_team();
+    if (*(volatile int*)&tm->job == 0) break;
+    const int sb = tm->sb, avail = tm->avail;
+    tm->ov[4 * lane + warp] = pass0_share<2, NV>(l, cur, sb, avail, warp, lane, RB, s_cw);
+    bar_team();
+  }
+}
+
 // Equal series test of two children (lane-local).
 __device__ __forceinline__ bool same_cols(const uint16_t* a, const uint16_t* b, int L) {
   for (int i = 0; i < L; ++i)
@@ -657,8 +729,8 @@ template <int K, int NW>
 __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, const char* cur,
                                             int cnt, int j0, uint32_t* pen, const float* cLf,
                                             unsigned long long* hkey, int32_t* href,
-                                            int* s_dec, uint4* s_cw, long long base, int hmask,
-                                            int RB,
+                                            int* s_dec, uint4* s_cw, Team* tm, long long base,
+                                            int hmask, int RB,
                                             int lane, int& n, int& hits, int& stopped,
                                             long long& attempts, long long& exact) {
   constexpr int NE = 2 * K, NC = K * K, NV = NW / 4;
@@ -747,44 +819,20 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
 #pragma unroll
       for (int v = 0; v < NV; ++v) s_cw[lane * NV + v] = cw[v];
       __syncwarp();
-      // children b < avail - 1, two at a time; child b counts for lanes > b
-      uint32_t h1[NE], h2[NE], h4[NE];
-      int h8[NE];
-#pragma unroll
-      for (int e = 0; e < NE; ++e) {
-        h1[e] = h2[e] = h4[e] = 0u;
-        h8[e] = 0;
+      // the overlap pass, one entrant per warp of the CTA: post the job,
+      // take entrant 0 here, collect entrants 1 .. 3 from the helpers
+      if (lane == 0) {
+        tm->sb = sb;
+        tm->avail = avail;
+        tm->job = 1;
       }
-      for (int b = 0; b + 1 < avail; b += 2) {
-        uint32_t m[2][NW];
-#pragma unroll
-        for (int i = 0; i < 2; ++i) {
-          const bool on = lane > b + i;
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            const uint4 w = s_cw[(b + i) * NV + v];
-            m[i][4 * v + 0] = on ? w.x : 0u;
-            m[i][4 * v + 1] = on ? w.y : 0u;
-            m[i][4 * v + 2] = on ? w.z : 0u;
-            m[i][4 * v + 3] = on ? w.w : 0u;
-          }
-        }
-#pragma unroll
-        for (int e = 0; e < NE; ++e) {
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            const uint32_t x[8] = {bits[e][v].x & m[0][4 * v], bits[e][v].y & m[0][4 * v + 1],
-                                   bits[e][v].z & m[0][4 * v + 2], bits[e][v].w & m[0][4 * v + 3],
-                                   bits[e][v].x & m[1][4 * v], bits[e][v].y & m[1][4 * v + 1],
-                                   bits[e][v].z & m[1][4 * v + 2], bits[e][v].w & m[1][4 * v + 3]};
-            hs8(x, h1[e], h2[e], h4[e], h8[e]);
-          }
-        }
-      }
-#pragma unroll
-      for (int e = 0; e < NE; ++e)
-        Sx[e] += 8 * h8[e] + 4 * __popc(h4[e]) + 2 * __popc(h2[e]) + __popc(h1[e]);
       __syncwarp();
+      bar_team();
+      const int ov0 = pass0_share<K, NV>(l, cur, sb, avail, 0, lane, RB, s_cw);
+      bar_team();
+      Sx[0] += ov0;
+#pragma unroll
+      for (int e = 1; e < NE; ++e) Sx[e] += tm->ov[4 * lane + e];
     }
     // lanes below `first` are settled (committed, or excluded as hits)
     int first = 0;
@@ -941,7 +989,6 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
 // Shared memory: hkey[H] (u64) | href[H] | pen[C] | cLf[Lmax + 1] |
 //                2 record buffers of kB records (128-byte aligned).
 // ---------------------------------------------------------------------------
-constexpr int kBuildThreads = 128;
 constexpr long long kMaxSpin = 1ll << 22;   // bounded mbarrier polling
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
@@ -1005,8 +1052,11 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
   __shared__ int s_n, s_done, s_E, s_fail;
   __shared__ int s_dec[32];              // outcomes of the batch's lanes (fast path)
   __shared__ uint4 s_cw[32 * 2];         // their children's bitsets (fast path)
+  __shared__ Team s_team;                // the fast path's helper-warp protocol
   // fast path: tournaments of at most 2 entrants, column sets of at most 256 bits
   const bool fast = d.k <= 2 && l.nw > 0;
+  // the helper warps take part in the overlap pass (tournaments of 2)
+  const bool team = !INIT && fast && d.k == 2;
 
   const int nchunks = (d.J + kB - 1) / kB;
   if (tid == 0) {
@@ -1065,21 +1115,21 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
       } else if (!INIT && fast) {
         if (k == 2) {
           if (l.nw == 4)
-            build_batch<2, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, base,
-                              hmask, RB,
+            build_batch<2, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, &s_team,
+                              base, hmask, RB,
                              lane, n, hits, stopped, attempts, exact);
           else
-            build_batch<2, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, base,
-                              hmask, RB,
+            build_batch<2, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, &s_team,
+                              base, hmask, RB,
                              lane, n, hits, stopped, attempts, exact);
         } else {
           if (l.nw == 4)
-            build_batch<1, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, base,
-                              hmask, RB,
+            build_batch<1, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, &s_team,
+                              base, hmask, RB,
                              lane, n, hits, stopped, attempts, exact);
           else
-            build_batch<1, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, base,
-                              hmask, RB,
+            build_batch<1, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, &s_team,
+                              base, hmask, RB,
                              lane, n, hits, stopped, attempts, exact);
         }
       } else {
@@ -1191,6 +1241,14 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
         s_done = (n >= d.P || stopped) ? 1 : 0;
         if (stopped == 4) s_fail = 1;
       }
+      if (team) {               // release the helpers from this chunk
+        if (lane == 0) s_team.job = 0;
+        __syncwarp();
+        bar_team();
+      }
+    } else if (team) {
+      if (l.nw == 4) team_helper<1>(l, cur, RB, warp, lane, &s_team, s_cw);
+      else team_helper<2>(l, cur, RB, warp, lane, &s_team, s_cw);
     }
     __syncthreads();            // the consumed buffer may now be refilled
     if (s_done) {
