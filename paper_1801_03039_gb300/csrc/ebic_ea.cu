@@ -3,9 +3,11 @@
 // penalty, crossover and the four mutations of Fig. 1, the tabu list, Step 4
 // evaluation and the top-rank list), kept entirely on one GPU.
 //
-// One generation = five launches, captured once into a CUDA graph and
-// replayed; every kernel reads the generation number and the stop flag from a
-// device control block, so replays need no host involvement:
+// One generation = five launches, captured once into a CUDA graph (two
+// branches: tabu insertion beside evaluation, Step 5 beside the next
+// generation's k_spec) and replayed; every kernel reads the generation number
+// and the stop flag from a device control block, so replays need no host
+// involvement:
 //   k_spec         parallel over attempts j < 2P + 1: draws the attempt's
 //                  random numbers (Philox-4x32-10, keyed by seed, generation,
 //                  attempt) and builds the child for EVERY possible outcome of
@@ -18,7 +20,8 @@
 //   k_tabu_insert  parallel: the accepted children enter the tabu hash table.
 //   K3 evaluation  support + Eq. (1) of the new population (ebic_matrix.cu).
 //   k_rank         one CTA: sorts by fitness and runs the Step 5 top-rank
-//                  update.
+//                  update (k_rank_warp: the visit by one warp from shared
+//                  column bitsets, up to 256 columns).
 // At most 2P + 1 attempts are ever needed: every attempt either adds one of at
 // most P individuals or is one of at most P + 1 hits.
 #include <cuda_runtime.h>
@@ -43,7 +46,7 @@ struct Ctl {
   int32_t n_elite;      // elites at the front of the current population
   int32_t last_hits;    // tabu hits in the last Step 3
   int32_t gens_done;    // Steps 2-5 passes completed
-  int32_t pad;
+  int32_t spec_gen;     // generation whose attempt records come next (set by k_build)
   long long hits_total, attempts_total, evals_total, exact_total;
 };
 
@@ -284,7 +287,9 @@ __device__ bool tabu_contains(const EaDev& d, unsigned long long key, const uint
 template <bool INIT, bool SCREEN>
 __global__ void __launch_bounds__(128) k_spec(EaDev d) {
   if (*(volatile int32_t*)&d.ctl->stop) return;
-  const int g = d.ctl->gen;
+  // generation g's records are built while Step 5 of generation g - 1 may
+  // still be running (it advances ctl->gen), so g comes from spec_gen
+  const int g = INIT ? 0 : d.ctl->spec_gen;
   const int nc = INIT ? 1 : d.ncombo;
   const int V = SCREEN ? d.V : 1;
   const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -374,7 +379,7 @@ __global__ void __launch_bounds__(256) k_pseudo_score(EaDev d) {
   const long long jc = t / d.V;
   const int j = (int)(jc / d.ncombo), c = (int)(jc % d.ncombo);
   uint32_t w[4];
-  philox_block((uint32_t)j, (uint32_t)d.ctl->gen, 65536u + (uint32_t)(c * d.V + v), d.seed, w);
+  philox_block((uint32_t)j, (uint32_t)d.ctl->spec_gen, 65536u + (uint32_t)(c * d.V + v), d.seed, w);
   d.var_score[t] = (float)(w[0] >> 8);
 }
 
@@ -1034,6 +1039,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
   if (*(volatile int32_t*)&d.ctl->stop) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = d.ctl->gen;
+  if (tid == 0) d.ctl->spec_gen = g + 1;    // read by the next k_spec only
   const int H = hmask + 1, k = d.k, nc = INIT ? 1 : k * k, S = d.S;
   const RecLayout l = rec_layout(k, S, INIT, bit_words(d.WC));
   const int RB = d.rec_bytes;
@@ -1718,12 +1724,20 @@ struct EaState {
   long long var_rows = 0;
   DevBuf var_seq, var_len, var_score, act;
   int32_t launches_per_gen = 5;
+  cudaStream_t side = nullptr;         // second branch of the generation graph
+  cudaEvent_t fork_ev[4] = {nullptr, nullptr, nullptr, nullptr};
 
   void release() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     exec = nullptr;
     graph = nullptr;
+    for (cudaEvent_t& e : fork_ev) {
+      if (e) cudaEventDestroy(e);
+      e = nullptr;
+    }
+    if (side) cudaStreamDestroy(side);
+    side = nullptr;
     for (DevBuf* b : {&seq, &len, &inc, &dec, &fit, &lnf, &tkey, &tref, &rec, &list_ref,
                       &list_f, &pow_tab, &pow_off, &c_over_L, &ctl, &gather, &var_seq, &var_len,
                       &var_score, &act})
@@ -1801,23 +1815,35 @@ static void launch_rank(const EaState* st, cudaStream_t s) {
     k_rank<<<1, kRankThreads, st->smem_rank, s>>>(st->dev, st->Pp);
 }
 
-static ebic_status launch_generation(ebic_ctx* h, EaState* st, bool init, cudaStream_t s) {
+// One generation g as captured for replay.  Step 3 first; then tabu
+// insertion beside the evaluation; then Step 5 of g beside the attempt
+// records of g + 1 (they need g's fitness and tabu list, not its top-rank
+// list, which only the next Step 2 reads):
+//
+//   k_build(g) -+- eval(g) ----------+- records(g + 1) -+- (next replay)
+//               +- k_tabu_insert(g) -+- k_rank(g) ------+
+//
+// The records of generation 1 are built at the end of ebic_run_init.
+static ebic_status launch_generation(ebic_ctx* h, EaState* st, cudaStream_t s) {
   const EaDev& d = st->dev;
-  if (init) {
-    const unsigned sblocks = (unsigned)((st->J + 127) / 128);
-    k_spec<true, false><<<sblocks, 128, 0, s>>>(d);
-    k_build<true><<<1, kBuildThreads, st->smem_build, s>>>(d, st->hmask, st->kB);
-  } else {
-    int nrec = 0;
-    EBIC_TRY(launch_records(st, s, &nrec));
-    st->launches_per_gen = nrec + 4;
-    k_build<false><<<1, kBuildThreads, st->smem_build, s>>>(d, st->hmask, st->kB);
-  }
-  k_tabu_insert<<<(unsigned)((st->p.pop_size + 255) / 256), 256, 0, s>>>(d);
+  cudaStream_t s2 = st->side;
+  k_build<false><<<1, kBuildThreads, st->smem_build, s>>>(d, st->hmask, st->kB);
+  EBIC_CUDA_TRY(cudaEventRecord(st->fork_ev[0], s));
+  EBIC_CUDA_TRY(cudaStreamWaitEvent(s2, st->fork_ev[0], 0));
+  k_tabu_insert<<<(unsigned)((st->p.pop_size + 255) / 256), 256, 0, s2>>>(d);
   EBIC_CUDA_TRY(cudaGetLastError());
   EBIC_TRY(eval_archive(h, st->apop, st->eargs, s));
-  launch_rank(st, s);
+  EBIC_CUDA_TRY(cudaEventRecord(st->fork_ev[1], s2));
+  EBIC_CUDA_TRY(cudaStreamWaitEvent(s, st->fork_ev[1], 0));
+  EBIC_CUDA_TRY(cudaEventRecord(st->fork_ev[2], s));
+  EBIC_CUDA_TRY(cudaStreamWaitEvent(s2, st->fork_ev[2], 0));
+  launch_rank(st, s2);
   EBIC_CUDA_TRY(cudaGetLastError());
+  int nrec = 0;
+  EBIC_TRY(launch_records(st, s, &nrec));
+  st->launches_per_gen = nrec + 4;
+  EBIC_CUDA_TRY(cudaEventRecord(st->fork_ev[3], s2));
+  EBIC_CUDA_TRY(cudaStreamWaitEvent(s, st->fork_ev[3], 0));
   return EBIC_OK;
 }
 
@@ -2043,11 +2069,17 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
   launch_rank(st, s);
   count_launches(1);
   EBIC_CUDA_TRY(cudaGetLastError());
+  // attempt records of generation 1
+  int nrec = 0;
+  EBIC_TRY(launch_records(st, s, &nrec));
+  count_launches((uint64_t)nrec);
 
   // One generation (Steps 2-5) captured as a graph for replay.
   st->tuning = h->tuning;
+  EBIC_CUDA_TRY(cudaStreamCreateWithFlags(&st->side, cudaStreamNonBlocking));
+  for (cudaEvent_t& e : st->fork_ev) EBIC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   EBIC_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  ebic_status cap_st = launch_generation(h, st, false, s);
+  ebic_status cap_st = launch_generation(h, st, s);
   cudaGraph_t graph = nullptr;
   cudaError_t ce = cudaStreamEndCapture(s, &graph);
   h->tuning = user_tuning;
@@ -2133,6 +2165,9 @@ static ebic_status run_step_async(ebic_ctx* h, int32_t generations, cudaStream_t
 }
 
 // One generation as five separate launches with events between them.
+// One generation as separate launches with events between them, in the
+// order of the graph's dependencies: Step 3, tabu insertion, evaluation,
+// Step 5, then the next generation's attempt records (reported first).
 static ebic_status run_step_profiled(ebic_ctx* h, float* us) {
   EaState* st = h->ea;
   if (!st || !st->initialised) return fail(EBIC_ERR_STATE, "ebic_run_init has not run");
@@ -2141,33 +2176,31 @@ static ebic_status run_step_profiled(ebic_ctx* h, float* us) {
   for (int i = 0; i < 6; ++i) EBIC_CUDA_TRY(cudaEventCreate(&ev[i]));
   const EaDev& d = st->dev;
   cudaEventRecord(ev[0], s);
-  int nrec = 0;
-  ebic_status rs = launch_records(st, s, &nrec);
-  if (rs != EBIC_OK) {
-    cudaStreamSynchronize(s);
-    for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
-    return rs;
-  }
-  cudaEventRecord(ev[1], s);
   k_build<false><<<1, kBuildThreads, st->smem_build, s>>>(d, st->hmask, st->kB);
-  cudaEventRecord(ev[2], s);
+  cudaEventRecord(ev[1], s);
   k_tabu_insert<<<(unsigned)((st->p.pop_size + 255) / 256), 256, 0, s>>>(d);
-  cudaEventRecord(ev[3], s);
+  cudaEventRecord(ev[2], s);
   const ebic_eval_tuning_t user = h->tuning;
   h->tuning = st->tuning;
   ebic_status es = eval_archive(h, st->apop, st->eargs, s);
   h->tuning = user;
-  cudaEventRecord(ev[4], s);
+  cudaEventRecord(ev[3], s);
   launch_rank(st, s);
+  cudaEventRecord(ev[4], s);
+  int nrec = 0;
+  ebic_status rs = launch_records(st, s, &nrec);
   cudaEventRecord(ev[5], s);
   count_launches((uint64_t)(3 + nrec));
   cudaError_t e = cudaEventSynchronize(ev[5]);
+  // kernel_us order: records, build, tabu insertion, evaluation, rank
+  const int from[5] = {4, 0, 1, 2, 3};
   for (int i = 0; i < 5 && us; ++i) {
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, ev[i], ev[i + 1]);
+    cudaEventElapsedTime(&ms, ev[from[i]], ev[from[i] + 1]);
     us[i] = ms * 1000.f;
   }
   for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+  EBIC_TRY(rs);
   EBIC_TRY(es);
   EBIC_CUDA_TRY(e);
   return EBIC_OK;
