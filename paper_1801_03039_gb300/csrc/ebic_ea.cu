@@ -1977,10 +1977,7 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
     EBIC_TRY(st->var_seq.reserve_zeroed((size_t)rows * st->S * sizeof(uint16_t), s));
     EBIC_TRY(st->var_len.reserve_zeroed((size_t)rows * sizeof(int32_t), s));
     EBIC_TRY(st->var_score.reserve((size_t)rows * sizeof(float)));
-    if (h->screen_mode == EBIC_SCREEN_SURROGATE) {
-      EBIC_TRY(st->act.reserve(sur_act_bytes(rows)));
-      st->sur = h->screen_sur;
-    }
+    if (h->screen_mode == EBIC_SCREEN_SURROGATE) st->sur = h->screen_sur;
     st->var_rows = rows;
     d.V = V;
     d.screen = h->screen_mode;

@@ -172,9 +172,10 @@ void ea_release(ebic_ctx* h);
 ebic_status ea_archive(ebic_ctx* h, const uint16_t** seq, const int32_t** len, const double** fit,
                        long long* n, int32_t* stride);
 
-// Surrogate forward pass for screening (ebic_surrogate.cu).  act holds
-// sur_act_bytes(n) bytes of activations; y[n] receives the predictions.
-// Launches only (no allocation, no synchronisation): safe under stream capture.
+// Surrogate forward pass for screening (ebic_surrogate.cu): y[n] receives the
+// predictions of n series (act is unused: the fused kernel keeps no
+// activations).  Launches only (no allocation, no synchronisation): safe
+// under stream capture.
 size_t sur_act_bytes(long long rows);
 ebic_status sur_forward_scores(ebic_surrogate_ctx* s, const uint16_t* seq, const int32_t* len,
                                int32_t stride, int32_t n, void* act, float* y, cudaStream_t st,

@@ -352,6 +352,212 @@ __global__ void k_sample(uint64_t seed, uint32_t step, long long n, int B, int32
   idx[b] = (int32_t)((((unsigned long long)x0 << 32 | x1) % (unsigned long long)n));
 }
 
+// ---------------------------------------------------------------------------
+// Fused forward pass for scoring (no activations kept): a persistent CTA holds
+// W1^T and W2^T in shared memory (bf16, padded rows against bank conflicts)
+// and loops over tiles of 64 series.  Per tile: features by the 8 warps (one
+// series per warp at a time, embedding sums in fp32, rounded to bf16 as in
+// k_features), h1 = relu(x W1 + b1) and h2 = relu(h1 W2 + b2) on the tensor
+// cores (mma.sync m16n8k16 bf16, fp32 accumulation; warp w owns output
+// columns [32 w, 32 w + 32)), and y = h2 . w3 + b3 reduced in the second
+// epilogue, so h2 never leaves registers.
+// ---------------------------------------------------------------------------
+constexpr int kFT = 64;                 // series per tile
+constexpr int kLdX = kF + 8;            // row stride (bf16) of x and W1^T
+constexpr int kLdH = kH + 8;            // row stride (bf16) of h1 and W2^T
+constexpr int kFwdThreads = 256;
+constexpr size_t kFwdSmem = (size_t)kH * kLdX * 2 + (size_t)kH * kLdH * 2 +
+                            (size_t)kFT * kLdX * 2 + (size_t)kFT * kLdH * 2 +
+                            (size_t)kFT * 8 * 4 + 3 * (size_t)kH * 4;
+
+__device__ __forceinline__ uint32_t lds32(const bf16* p) {
+  return *reinterpret_cast<const uint32_t*>(p);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t a2,
+                                         uint32_t a3, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(kFwdThreads, 1)
+k_mlp_forward(const uint16_t* __restrict__ seq, const int32_t* __restrict__ len, int32_t stride,
+              int32_t n, int32_t C, const float* __restrict__ emb,
+              const float* __restrict__ cmean, const float* __restrict__ csd, float len_scale,
+              const bf16* __restrict__ w1, const float* __restrict__ b1,
+              const bf16* __restrict__ w2, const float* __restrict__ b2,
+              const float* __restrict__ w3, const float* __restrict__ b3, float* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char fsm[];
+  bf16* w1t = reinterpret_cast<bf16*>(fsm);                 // [kH][kLdX]
+  bf16* w2t = w1t + kH * kLdX;                              // [kH][kLdH]
+  bf16* xs = w2t + kH * kLdH;                               // [kFT][kLdX]
+  bf16* hs = xs + kFT * kLdX;                               // [kFT][kLdH]
+  float* yp = reinterpret_cast<float*>(hs + kFT * kLdH);    // [kFT][8]
+  float* b1s = yp + kFT * 8;
+  float* b2s = b1s + kH;
+  float* w3s = b2s + kH;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = lane >> 2, tq = lane & 3;
+
+  // weights, transposed so that a B fragment is one 32-bit load
+  for (int i = tid; i < kF * kH; i += kFwdThreads) {
+    const int k = i / kH, nn = i % kH;
+    w1t[nn * kLdX + k] = w1[i];
+  }
+  for (int i = tid; i < kH * kH; i += kFwdThreads) {
+    const int k = i / kH, nn = i % kH;
+    w2t[nn * kLdH + k] = w2[i];
+  }
+  for (int i = tid; i < kH; i += kFwdThreads) {
+    b1s[i] = b1[i];
+    b2s[i] = b2[i];
+    w3s[i] = w3[i];
+  }
+  const float bias3 = b3[0];
+  __syncthreads();
+
+  const int ntiles = (n + kFT - 1) / kFT;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int r0 = tile * kFT;
+    // ---- features: warp w fills rows 8 w .. 8 w + 7 ----
+    for (int rr = 0; rr < 8; ++rr) {
+      const int lr = warp * 8 + rr, row = r0 + lr;
+      float e0 = 0.f, e1 = 0.f, m = 0.f, dsum = 0.f;
+      int L = 0;
+      if (row < n) {
+        L = min(max(len[row], 0), stride);
+        const uint16_t* sp = seq + (size_t)row * stride;
+        const int cA = lane < L ? (int)sp[lane] : 0;
+        const int cB = lane + 32 < L ? (int)sp[lane + 32] : 0;
+        for (int i = 0; i < L; ++i) {
+          const int c = __shfl_sync(0xffffffffu, i < 32 ? cA : cB, i & 31);
+          if (c >= C) continue;
+          e0 += emb[(size_t)c * kEmb + lane];
+          e1 += emb[(size_t)c * kEmb + 32 + lane];
+          m += cmean[c];
+          dsum += csd[c];
+        }
+      }
+      bf16* xr = xs + lr * kLdX;
+      xr[lane] = __float2bfloat16_rn(e0);
+      xr[32 + lane] = __float2bfloat16_rn(e1);
+      if (lane < 16) {
+        float v = 0.f;
+        if (lane == 0) v = L ? m / (float)L : 0.f;
+        if (lane == 1) v = L ? dsum / (float)L : 0.f;
+        if (lane == 2) v = (float)L / len_scale;
+        xr[64 + lane] = __float2bfloat16_rn(v);
+      }
+    }
+    __syncthreads();
+    const int n0 = warp * 32;
+    // ---- layer 1: h1 = relu(x W1 + b1), K = 80 ----
+    {
+      float acc[4][4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+#pragma unroll
+      for (int k0 = 0; k0 < kF; k0 += 16) {
+        uint32_t bq[4][2];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bf16* bp = w1t + (n0 + 8 * j + g) * kLdX + k0 + 2 * tq;
+          bq[j][0] = lds32(bp);
+          bq[j][1] = lds32(bp + 8);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const bf16* ap = xs + (16 * i + g) * kLdX + k0 + 2 * tq;
+          const uint32_t a0 = lds32(ap), a1 = lds32(ap + 8 * kLdX), a2 = lds32(ap + 8),
+                         a3 = lds32(ap + 8 * kLdX + 8);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a0, a1, a2, a3, bq[j][0], bq[j][1]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int col = n0 + 8 * j + 2 * tq;
+          const int ra = 16 * i + g;
+          const float bA = b1s[col], bB = b1s[col + 1];
+          __nv_bfloat162 lo, hi;
+          lo.x = __float2bfloat16_rn(fmaxf(acc[i][j][0] + bA, 0.f));
+          lo.y = __float2bfloat16_rn(fmaxf(acc[i][j][1] + bB, 0.f));
+          hi.x = __float2bfloat16_rn(fmaxf(acc[i][j][2] + bA, 0.f));
+          hi.y = __float2bfloat16_rn(fmaxf(acc[i][j][3] + bB, 0.f));
+          *reinterpret_cast<__nv_bfloat162*>(hs + ra * kLdH + col) = lo;
+          *reinterpret_cast<__nv_bfloat162*>(hs + (ra + 8) * kLdH + col) = hi;
+        }
+    }
+    __syncthreads();
+    // ---- layer 2 + output: y = relu(h1 W2 + b2) . w3 + b3, K = 256 ----
+    {
+      float acc[4][4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.f;
+#pragma unroll 4
+      for (int k0 = 0; k0 < kH; k0 += 16) {
+        uint32_t bq[4][2];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bf16* bp = w2t + (n0 + 8 * j + g) * kLdH + k0 + 2 * tq;
+          bq[j][0] = lds32(bp);
+          bq[j][1] = lds32(bp + 8);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const bf16* ap = hs + (16 * i + g) * kLdH + k0 + 2 * tq;
+          const uint32_t a0 = lds32(ap), a1 = lds32(ap + 8 * kLdH), a2 = lds32(ap + 8),
+                         a3 = lds32(ap + 8 * kLdH + 8);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], a0, a1, a2, a3, bq[j][0], bq[j][1]);
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float pa = 0.f, pb = 0.f;               // rows 16 i + g and 16 i + g + 8
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int col = n0 + 8 * j + 2 * tq;
+          const float vA = __bfloat162float(__float2bfloat16_rn(fmaxf(acc[i][j][0] + b2s[col], 0.f)));
+          const float vB = __bfloat162float(__float2bfloat16_rn(fmaxf(acc[i][j][1] + b2s[col + 1], 0.f)));
+          const float vC = __bfloat162float(__float2bfloat16_rn(fmaxf(acc[i][j][2] + b2s[col], 0.f)));
+          const float vD = __bfloat162float(__float2bfloat16_rn(fmaxf(acc[i][j][3] + b2s[col + 1], 0.f)));
+          pa += vA * w3s[col] + vB * w3s[col + 1];
+          pb += vC * w3s[col] + vD * w3s[col + 1];
+        }
+        pa += __shfl_xor_sync(0xffffffffu, pa, 1);
+        pa += __shfl_xor_sync(0xffffffffu, pa, 2);
+        pb += __shfl_xor_sync(0xffffffffu, pb, 1);
+        pb += __shfl_xor_sync(0xffffffffu, pb, 2);
+        if (tq == 0) {
+          yp[(16 * i + g) * 8 + warp] = pa;
+          yp[(16 * i + g + 8) * 8 + warp] = pb;
+        }
+      }
+    }
+    __syncthreads();
+    if (tid < kFT && r0 + tid < n) {
+      float t = bias3;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) t += yp[tid * 8 + w];
+      y[r0 + tid] = t;
+    }
+  }
+}
+
 }  // namespace ebic
 
 using namespace ebic;
@@ -447,16 +653,22 @@ static void sur_hidden(ebic_surrogate_ctx* s, const uint16_t* seq, const int32_t
 ebic_status sur_forward_scores(ebic_surrogate_ctx* s, const uint16_t* seq, const int32_t* len,
                                int32_t stride, int32_t n, void* act, float* y, cudaStream_t st,
                                int* launches) {
+  (void)act;
   if (n <= 0) {
     if (launches) *launches = 0;
     return EBIC_OK;
   }
-  const ActView a = act_view(act, n);
-  sur_hidden(s, seq, len, stride, nullptr, n, a, st);
+  // opt in to the large shared-memory carve-out (per device; cheap to repeat)
+  EBIC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kFwdSmem));
   const float* P = s->par.as<float>();
-  k_out<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(a.h2, P + s->o_w3, P + s->o_b3, n, y, nullptr,
-                                                 nullptr, nullptr, nullptr);
-  if (launches) *launches = 4;
+  const int ntiles = (n + kFT - 1) / kFT;
+  const int grid = std::min(ntiles, 152);
+  k_mlp_forward<<<grid, kFwdThreads, kFwdSmem, st>>>(
+      seq, len, stride, n, s->C, P + s->o_emb, s->cmean.as<float>(), s->csd.as<float>(),
+      s->len_scale, s->w1b.as<bf16>(), P + s->o_b1, s->w2b.as<bf16>(), P + s->o_b2, P + s->o_w3,
+      P + s->o_b3, y);
+  if (launches) *launches = 1;
   EBIC_CUDA_TRY(cudaGetLastError());
   return EBIC_OK;
 }
@@ -824,7 +1036,7 @@ ebic_status ebic_surrogate_predict(ebic_surrogate s, const uint16_t* d_seq, cons
     const int32_t m = (int32_t)std::min<int64_t>(chunk, n - b0);
     EBIC_TRY(sur_forward_scores(s, d_seq + (size_t)b0 * stride, d_len + b0, stride, m,
                                 s->act.ptr, d_out + b0, st, nullptr));
-    count_launches(4);
+    count_launches(1);
   }
   if (!stream) EBIC_CUDA_TRY(cudaStreamSynchronize(st));
   return EBIC_OK;
