@@ -31,6 +31,7 @@
 #include <cstring>
 #include <vector>
 
+#include "ebic_async.cuh"
 #include "ebic_internal.cuh"
 
 namespace ebic {
@@ -994,45 +995,6 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
 // Shared memory: hkey[H] (u64) | href[H] | pen[C] | cLf[Lmax + 1] |
 //                2 record buffers of kB records (128-byte aligned).
 // ---------------------------------------------------------------------------
-constexpr long long kMaxSpin = 1ll << 22;   // bounded mbarrier polling
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, int count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count)
-               : "memory");
-}
-
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes,
-                                          unsigned long long* bar) {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-          "r"(smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-
-// Waits for phase `parity` of the barrier to complete; false after kMaxSpin polls.
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t parity) {
-  for (long long it = 0; it < kMaxSpin; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_addr(bar)), "r"(parity)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
 template <bool INIT>
 __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int kB) {
   extern __shared__ __align__(128) unsigned long long smem_u64[];

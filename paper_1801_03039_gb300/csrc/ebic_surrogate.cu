@@ -19,6 +19,7 @@
 #include <cmath>
 #include <vector>
 
+#include "ebic_async.cuh"
 #include "ebic_internal.cuh"
 
 namespace ebic {
@@ -310,6 +311,22 @@ __global__ void k_to_bf16(const float* __restrict__ src, bf16* __restrict__ dst,
   if (i < n) dst[i] = __float2bfloat16_rn(src[i]);
 }
 
+// W1^T and W2^T in the fused forward's shared-memory layout (bf16, rows of
+// kF + 8 / kH + 8 with zero padding), from the fp32 masters W1 [kF][kH] and
+// W2 [kH][kH]; one bulk copy moves the result into shared memory.
+__global__ void k_pack_fwd(const float* __restrict__ W1, const float* __restrict__ W2,
+                           bf16* __restrict__ out) {
+  constexpr int ldx = kF + 8, ldh = kH + 8;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < kH * ldx) {
+    const int nn = i / ldx, k = i % ldx;
+    out[i] = __float2bfloat16_rn(k < kF ? W1[k * kH + nn] : 0.f);
+  } else if (i < kH * ldx + kH * ldh) {
+    const int r = i - kH * ldx, nn = r / ldh, k = r % ldh;
+    out[i] = __float2bfloat16_rn(k < kH ? W2[k * kH + nn] : 0.f);
+  }
+}
+
 // standardised log1p targets: t = (log1p(f) - mean) / sd
 __global__ void k_targets(const double* __restrict__ f, long long n, float mean, float sd,
                           float* __restrict__ t) {
@@ -387,9 +404,9 @@ __global__ void __launch_bounds__(kFwdThreads, 1)
 k_mlp_forward(const uint16_t* __restrict__ seq, const int32_t* __restrict__ len, int32_t stride,
               int32_t n, int32_t C, const float* __restrict__ emb,
               const float* __restrict__ cmean, const float* __restrict__ csd, float len_scale,
-              const bf16* __restrict__ w1, const float* __restrict__ b1,
-              const bf16* __restrict__ w2, const float* __restrict__ b2,
-              const float* __restrict__ w3, const float* __restrict__ b3, float* __restrict__ y) {
+              const bf16* __restrict__ wpack, const float* __restrict__ b1,
+              const float* __restrict__ b2, const float* __restrict__ w3,
+              const float* __restrict__ b3, float* __restrict__ y, int* __restrict__ err) {
   extern __shared__ __align__(16) unsigned char fsm[];
   bf16* w1t = reinterpret_cast<bf16*>(fsm);                 // [kH][kLdX]
   bf16* w2t = w1t + kH * kLdX;                              // [kH][kLdH]
@@ -402,22 +419,32 @@ k_mlp_forward(const uint16_t* __restrict__ seq, const int32_t* __restrict__ len,
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int g = lane >> 2, tq = lane & 3;
 
-  // weights, transposed so that a B fragment is one 32-bit load
-  for (int i = tid; i < kF * kH; i += kFwdThreads) {
-    const int k = i / kH, nn = i % kH;
-    w1t[nn * kLdX + k] = w1[i];
+  // W1^T and W2^T (packed by k_pack_fwd in this layout) by one bulk copy
+  __shared__ __align__(8) unsigned long long wbar;
+  constexpr uint32_t kWBytes = (uint32_t)((kH * kLdX + kH * kLdH) * sizeof(bf16));
+  if (tid == 0) {
+    mbar_init(&wbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = tid; i < kH * kH; i += kFwdThreads) {
-    const int k = i / kH, nn = i % kH;
-    w2t[nn * kLdH + k] = w2[i];
-  }
+  __syncthreads();
+  if (tid == 0) bulk_load(w1t, wpack, kWBytes, &wbar);
   for (int i = tid; i < kH; i += kFwdThreads) {
     b1s[i] = b1[i];
     b2s[i] = b2[i];
     w3s[i] = w3[i];
   }
   const float bias3 = b3[0];
-  __syncthreads();
+  const bool ok = mbar_wait(&wbar, 0);
+  if (!__syncthreads_and(ok)) {
+    // the copy did not complete in time: wait once more (bounded) for it to
+    // land before the CTA exits, flag the error, leave NaN scores
+    if (!ok) mbar_wait(&wbar, 0);
+    if (tid == 0) atomicExch(err, 1);
+    const int ntiles_ = (n + kFT - 1) / kFT;
+    for (int tile = blockIdx.x; tile < ntiles_; tile += gridDim.x)
+      if (tid < kFT && tile * kFT + tid < n) y[tile * kFT + tid] = __int_as_float(0x7fc00000);
+    return;
+  }
 
   const int ntiles = (n + kFT - 1) / kFT;
   for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -432,6 +459,7 @@ k_mlp_forward(const uint16_t* __restrict__ seq, const int32_t* __restrict__ len,
         const uint16_t* sp = seq + (size_t)row * stride;
         const int cA = lane < L ? (int)sp[lane] : 0;
         const int cB = lane + 32 < L ? (int)sp[lane + 32] : 0;
+#pragma unroll 4
         for (int i = 0; i < L; ++i) {
           const int c = __shfl_sync(0xffffffffu, i < 32 ? cA : cB, i & 31);
           if (c >= C) continue;
@@ -577,6 +605,8 @@ struct ebic_surrogate_ctx {
   long long n_par = 0;
   long long o_emb = 0, o_w1 = 0, o_b1 = 0, o_w2 = 0, o_b2 = 0, o_w3 = 0, o_b3 = 0;
   DevBuf par, grad, mom, vel, w1b, w2b, cmean, csd;
+  DevBuf wpack;                // W1^T | W2^T in the fused forward's layout (bf16)
+  DevBuf ferr;                 // set by the fused forward on a copy timeout
   // training activations (capacity rows)
   int32_t cap = 0;
   DevBuf act, dh1, dh2, dx, y, dy, idx, loss, tgt, tmp;
@@ -666,8 +696,8 @@ ebic_status sur_forward_scores(ebic_surrogate_ctx* s, const uint16_t* seq, const
   const int grid = std::min(ntiles, 152);
   k_mlp_forward<<<grid, kFwdThreads, kFwdSmem, st>>>(
       seq, len, stride, n, s->C, P + s->o_emb, s->cmean.as<float>(), s->csd.as<float>(),
-      s->len_scale, s->w1b.as<bf16>(), P + s->o_b1, s->w2b.as<bf16>(), P + s->o_b2, P + s->o_w3,
-      P + s->o_b3, y);
+      s->len_scale, s->wpack.as<bf16>(), P + s->o_b1, P + s->o_b2, P + s->o_w3, P + s->o_b3, y,
+      s->ferr.as<int>());
   if (launches) *launches = 1;
   EBIC_CUDA_TRY(cudaGetLastError());
   return EBIC_OK;
@@ -730,7 +760,9 @@ static ebic_status sur_step(ebic_surrogate_ctx* s, const uint16_t* seq, const in
           P + g.o, G + g.o, s->mom.as<float>() + g.o, s->vel.as<float>() + g.o, g.n, lr, b1, b2,
           1e-8f, c1, c2, g.copy);
     }
-    count_launches(5);
+    constexpr int npack = kH * (kF + 8) + kH * (kH + 8);
+    k_pack_fwd<<<(npack + 255) / 256, 256, 0, st>>>(P + s->o_w1, P + s->o_w2, s->wpack.as<bf16>());
+    count_launches(6);
   }
   EBIC_CUDA_TRY(cudaGetLastError());
   return EBIC_OK;
@@ -742,7 +774,9 @@ static ebic_status refresh_copies(ebic_surrogate_ctx* s, cudaStream_t st) {
                                                    (long long)kF * kH);
   k_to_bf16<<<(kH * kH + 255) / 256, 256, 0, st>>>(P + s->o_w2, s->w2b.as<bf16>(),
                                                    (long long)kH * kH);
-  count_launches(2);
+  constexpr int npack = kH * (kF + 8) + kH * (kH + 8);
+  k_pack_fwd<<<(npack + 255) / 256, 256, 0, st>>>(P + s->o_w1, P + s->o_w2, s->wpack.as<bf16>());
+  count_launches(3);
   EBIC_CUDA_TRY(cudaGetLastError());
   return EBIC_OK;
 }
@@ -774,7 +808,8 @@ static void init_weights(ebic_surrogate_ctx* s, std::vector<float>& p) {
 
 static void sur_release(ebic_surrogate_ctx* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
-  for (DevBuf* b : {&s->par, &s->grad, &s->mom, &s->vel, &s->w1b, &s->w2b, &s->cmean, &s->csd,
+  for (DevBuf* b : {&s->par, &s->grad, &s->mom, &s->vel, &s->w1b, &s->w2b, &s->wpack, &s->ferr,
+                    &s->cmean, &s->csd,
                     &s->act, &s->dh1, &s->dh2, &s->dx, &s->y, &s->dy, &s->idx, &s->loss,
                     &s->tgt, &s->tmp, &s->log_seq, &s->log_len, &s->log_fit})
     b->release();
@@ -805,6 +840,8 @@ static ebic_status sur_create(ebic_ctx* h, int32_t len_scale, uint64_t seed,
   EBIC_TRY(s->vel.reserve_zeroed(pb, s->stream));
   EBIC_TRY(s->w1b.reserve((size_t)kF * kH * sizeof(bf16)));
   EBIC_TRY(s->w2b.reserve((size_t)kH * kH * sizeof(bf16)));
+  EBIC_TRY(s->wpack.reserve((size_t)(kH * (kF + 8) + kH * (kH + 8)) * sizeof(bf16)));
+  EBIC_TRY(s->ferr.reserve_zeroed(sizeof(int), s->stream));
   EBIC_TRY(s->cmean.reserve((size_t)s->C * sizeof(float)));
   EBIC_TRY(s->csd.reserve((size_t)s->C * sizeof(float)));
   EBIC_TRY(s->loss.reserve(sizeof(float)));
@@ -1038,7 +1075,12 @@ ebic_status ebic_surrogate_predict(ebic_surrogate s, const uint16_t* d_seq, cons
                                 s->act.ptr, d_out + b0, st, nullptr));
     count_launches(1);
   }
-  if (!stream) EBIC_CUDA_TRY(cudaStreamSynchronize(st));
+  if (!stream) {
+    int e = 0;
+    EBIC_CUDA_TRY(cudaMemcpyAsync(&e, s->ferr.ptr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    EBIC_CUDA_TRY(cudaStreamSynchronize(st));
+    if (e) return fail(EBIC_ERR_TIMEOUT, "a bounded wait for the surrogate's weights expired");
+  }
   return EBIC_OK;
 }
 
