@@ -235,6 +235,40 @@ def test_launch_shapes_do_not_change_results(shape, tune):
         eb.ebic_free(h)
 
 
+@pytest.mark.parametrize("kernel,batch_steps,nv", [(2, 4, 1), (2, 8, 1), (2, 4, 2), (2, 8, 2),
+                                                   (2, 4, 4)])
+def test_long_series_batches(kernel, batch_steps, nv):
+    """Series of 30-45 columns: several 32-step windows per series."""
+    R, C = 3000, 60
+    prob = synth.matrix_random(7, R, C, n_plants=2, plant_rows=(300, 600), plant_cols=(40, 50))
+    off, cols = synth.population(8, 300, C, 30, 45, plants=prob.plants)
+    oinc, _, ofit = oracle_eval(prob.A, off, cols, 30)
+    h = eb.ebic_load_matrix(prob.A)
+    try:
+        eb.ebic_set_path(h, eb.PATH_BITMASK)
+        eb.ebic_set_eval_tuning(h, kernel=kernel, batch_steps=batch_steps, vecs_per_lane=nv)
+        inc, _, fit = eb.ebic_eval_population(h, off, cols, 30)
+        assert_bits_equal(inc, oinc, "inc")
+        assert_bits_equal(fit, ofit, "fit")
+        assert (oinc > 0).sum() > 10      # planted series survive all windows
+    finally:
+        eb.ebic_free(h)
+
+
+def test_tuning_rejects_bad_batch():
+    prob = synth.matrix_tiny(seed=0)
+    h = eb.ebic_load_matrix(prob.A)
+    try:
+        with pytest.raises(eb.EbicError):
+            eb.ebic_set_eval_tuning(h, kernel=2, batch_steps=8, vecs_per_lane=4)
+        with pytest.raises(eb.EbicError):
+            eb.ebic_set_eval_tuning(h, kernel=2, batch_steps=12)
+        with pytest.raises(eb.EbicError):
+            eb.ebic_set_eval_tuning(h, kernel=5)
+    finally:
+        eb.ebic_free(h)
+
+
 @pytest.mark.parametrize("which", ["paper", "expression"])
 def test_autotuner_keeps_results_exact(which):
     torch = pytest.importorskip("torch")
