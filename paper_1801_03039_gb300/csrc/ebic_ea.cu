@@ -1446,22 +1446,43 @@ __global__ void __launch_bounds__(kRankThreads) k_rank(EaDev d, int Pp) {
 // ---------------------------------------------------------------------------
 // k_rank_warp: the same Step 5 for column sets of at most NW * 32 columns.
 // The whole CTA sorts (as k_rank) and then prefetches, in visiting order, each
-// individual's fitness, length and column bitset, and the bitsets of the
-// listed records, into shared memory.  The visit itself -- sequential by
-// definition -- is run by warp 0 alone from shared memory: overlaps are
-// popcounts of bitset intersections, |a & b| > tau * min(|a|, |b|) is an
-// integer test against floor(tau * m) (the binary64 product, as in k_rank),
-// and evictions and the insertion are stable warp-wide compactions and
-// shifts, with no CTA barrier per individual.
+// individual's fitness, length and column bitset, and the listed records'
+// fitness, reference, length and bitset, into shared memory.  The visit
+// itself -- sequential by definition -- is run by warp 0 alone from shared
+// memory: overlaps are popcounts of bitset intersections, and
+// |a & b| > tau * min(|a|, |b|) is an integer test against floor(tau * m)
+// (the binary64 product, as in k_rank).  The list is kept sorted by
+// decreasing fitness, so the records of fitness >= f(x) form a prefix of
+// length ge; nothing in that prefix can move (evictions need lower fitness,
+// and x goes after every record of higher or equal fitness), so an accepted x
+// only rewrites the suffix: a stable compaction of the kept records, then a
+// shift by one, then x at position ge.
 //
-// Shared memory: skey[Pp] (u64) | sidx[Pp] | pf[P] (f64) | pL[P] | pbits[P][NW] |
-//                lf[cap] (f64) | lr[cap] | lL[cap] | lbits[cap][NW] | thr[Lmax + 1]
+// Shared memory: skey[Pp] (u64) | sidx[Pp] | pf[P] (f64) | pL[P] |
+//                lm[cap] (RankRec, 16 B) | pbits[P][NW] | lbits[cap][NW] | thr
 // ---------------------------------------------------------------------------
+struct RankRec {
+  double f;
+  int32_t r, L;
+};
+
 constexpr int kRankWarpThreads = 512;   // register room for the deciding warp
 
 template <int NW>
+__device__ __forceinline__ int overlap_bits(const uint32_t* a, const uint32_t (&xb)[NW]) {
+  int inter = 0;
+#pragma unroll
+  for (int v = 0; v < NW / 4; ++v) {
+    const uint4 w = reinterpret_cast<const uint4*>(a)[v];
+    inter += __popc(w.x & xb[4 * v]) + __popc(w.y & xb[4 * v + 1]) +
+             __popc(w.z & xb[4 * v + 2]) + __popc(w.w & xb[4 * v + 3]);
+  }
+  return inter;
+}
+
+template <int NW>
 __global__ void __launch_bounds__(kRankWarpThreads) k_rank_warp(EaDev d, int Pp) {
-  extern __shared__ unsigned long long smem_u64[];
+  extern __shared__ __align__(128) unsigned long long smem_u64[];
   if (*(volatile int32_t*)&d.ctl->stop) return;
   const int tid = threadIdx.x, lane = tid & 31;
   const int g = d.ctl->gen;
@@ -1470,13 +1491,14 @@ __global__ void __launch_bounds__(kRankWarpThreads) k_rank_warp(EaDev d, int Pp)
   unsigned long long* skey = smem_u64;
   int32_t* sidx = reinterpret_cast<int32_t*>(skey + Pp);
   double* pf = reinterpret_cast<double*>(sidx + Pp + (Pp & 1));
-  double* lf = pf + P;
-  int32_t* pL = reinterpret_cast<int32_t*>(lf + cap);
-  int32_t* lr = pL + P;
-  int32_t* lL = lr + cap;
-  int32_t* thr = lL + cap;
-  uint32_t* pbits = reinterpret_cast<uint32_t*>(thr + ((d.Lmax + 1 + 3) & ~3));
+  int32_t* pL = reinterpret_cast<int32_t*>(pf + P);
+  // the records and bitsets are read as 16-byte vectors: align by offset
+  char* const sb = reinterpret_cast<char*>(smem_u64);
+  RankRec* lm = reinterpret_cast<RankRec*>(
+      sb + ((reinterpret_cast<char*>(pL + P) - sb + 15) & ~(ptrdiff_t)15));
+  uint32_t* pbits = reinterpret_cast<uint32_t*>(lm + cap);
   uint32_t* lbits = pbits + (size_t)P * NW;
+  int32_t* thr = reinterpret_cast<int32_t*>(lbits + (size_t)cap * NW);
 
   for (int i = tid; i < Pp; i += kRankWarpThreads) {
     if (i < P) {
@@ -1489,13 +1511,10 @@ __global__ void __launch_bounds__(kRankWarpThreads) k_rank_warp(EaDev d, int Pp)
   }
   for (int m = tid; m <= d.Lmax; m += kRankWarpThreads) thr[m] = (int32_t)floor(d.tau * (double)m);
   int n = d.ctl->n_top;
-  // the listed records: reference, fitness, length, bitset
   for (int t = tid; t < n; t += kRankWarpThreads) {
     const int32_t r = d.list_ref[t];
-    lr[t] = r;
-    lf[t] = d.list_f[t];
     const int L = d.len[r];
-    lL[t] = L;
+    lm[t] = RankRec{d.list_f[t], r, L};
     uint32_t* b = lbits + (size_t)t * NW;     // this thread's entry
 #pragma unroll
     for (int w = 0; w < NW; ++w) b[w] = 0u;
@@ -1538,107 +1557,95 @@ __global__ void __launch_bounds__(kRankWarpThreads) k_rank_warp(EaDev d, int Pp)
   __syncthreads();
 
   if (tid < 32) {
+    const unsigned FULL = 0xffffffffu;
     for (int oi = 0; oi < P; ++oi) {
       const double xf = pf[oi];
       const int xL = pL[oi];
       uint32_t xb[NW];
 #pragma unroll
-      for (int w = 0; w < NW; ++w) xb[w] = pbits[(size_t)oi * NW + w];
-      // records strictly fitter, and overlapping records of higher or equal
-      // fitness (which block x)
-      int above = 0;
+      for (int v = 0; v < NW / 4; ++v) {
+        const uint4 w = reinterpret_cast<const uint4*>(pbits + (size_t)oi * NW)[v];
+        xb[4 * v] = w.x;
+        xb[4 * v + 1] = w.y;
+        xb[4 * v + 2] = w.z;
+        xb[4 * v + 3] = w.w;
+      }
+      // records strictly fitter (above), of higher or equal fitness (ge, a
+      // prefix), and whether one of the latter overlaps x (blocks it)
+      int above = 0, ge = 0;
       bool block = false;
       for (int t0 = 0; t0 < n; t0 += 32) {
         const int t = t0 + lane;
+        bool is_ge = false;
         if (t < n) {
-          const double f = lf[t];
-          above += f > xf ? 1 : 0;
-          if (f >= xf) {
-            int inter = 0;
-#pragma unroll
-            for (int w = 0; w < NW; ++w) inter += __popc(lbits[(size_t)t * NW + w] & xb[w]);
-            block = block || inter > thr[min(lL[t], xL)];
-          }
+          const RankRec rec = lm[t];
+          above += rec.f > xf ? 1 : 0;
+          is_ge = rec.f >= xf;
+          if (is_ge) block = block || overlap_bits<NW>(lbits + (size_t)t * NW, xb) > thr[min(rec.L, xL)];
         }
+        const unsigned gb = __ballot_sync(FULL, is_ge);
+        ge += __popc(gb);
+        if (gb != FULL) break;                  // the prefix ends in this chunk
       }
-      above = __reduce_add_sync(0xffffffffu, (unsigned)above);
-      if (above >= d.T) break;                            // see k_rank
-      if (__any_sync(0xffffffffu, block)) continue;
-      // stable compaction of the records kept (not: overlapping and less fit),
-      // counting those of higher or equal fitness (x goes after them)
-      int m = 0, pos = 0;
-      for (int t0 = 0; t0 < n; t0 += 32) {
+      above = __reduce_add_sync(FULL, (unsigned)above);
+      if (above >= d.T) break;                  // see k_rank
+      if (__any_sync(FULL, block)) continue;
+      // suffix [ge, n): stable compaction of the kept records (not:
+      // overlapping and less fit) ...
+      int m = ge;
+      for (int t0 = ge; t0 < n; t0 += 32) {
         const int t = t0 + lane;
         bool keep = false;
-        double f = 0.0;
-        int32_t r = 0, L = 0;
-        uint32_t b[NW];
+        RankRec rec{0.0, 0, 0};
+        uint4 b[NW / 4];
         if (t < n) {
-          f = lf[t];
-          r = lr[t];
-          L = lL[t];
-          int inter = 0;
+          rec = lm[t];
 #pragma unroll
-          for (int w = 0; w < NW; ++w) {
-            b[w] = lbits[(size_t)t * NW + w];
-            inter += __popc(b[w] & xb[w]);
-          }
-          keep = !(inter > thr[min(L, xL)] && f < xf);
+          for (int v = 0; v < NW / 4; ++v) b[v] = reinterpret_cast<const uint4*>(lbits + (size_t)t * NW)[v];
+          keep = !(overlap_bits<NW>(lbits + (size_t)t * NW, xb) > thr[min(rec.L, xL)]);
         }
-        const unsigned bal = __ballot_sync(0xffffffffu, keep);
-        const unsigned ge = __ballot_sync(0xffffffffu, keep && f >= xf);
+        const unsigned bal = __ballot_sync(FULL, keep);
         __syncwarp();
         if (keep) {
           const int dst = m + __popc(bal & ((1u << lane) - 1u));
-          lf[dst] = f;
-          lr[dst] = r;
-          lL[dst] = L;
+          lm[dst] = rec;
 #pragma unroll
-          for (int w = 0; w < NW; ++w) lbits[(size_t)dst * NW + w] = b[w];
+          for (int v = 0; v < NW / 4; ++v) reinterpret_cast<uint4*>(lbits + (size_t)dst * NW)[v] = b[v];
         }
         __syncwarp();
         m += __popc(bal);
-        pos += __popc(ge);
       }
-      // shift [pos, m) up by one, from the end, and place x at pos
-      for (int t0 = ((m - 1) & ~31); t0 >= pos - 31 && t0 >= 0; t0 -= 32) {
+      // ... shifted up by one (from the end), and x at ge
+      for (int t0 = ((m - 1) & ~31); t0 >= ge - 31 && t0 >= 0; t0 -= 32) {
         const int t = t0 + lane;
-        const bool mv = t >= pos && t < m;
-        double f = 0.0;
-        int32_t r = 0, L = 0;
-        uint32_t b[NW];
+        const bool mv = t >= ge && t < m;
+        RankRec rec{0.0, 0, 0};
+        uint4 b[NW / 4];
         if (mv) {
-          f = lf[t];
-          r = lr[t];
-          L = lL[t];
+          rec = lm[t];
 #pragma unroll
-          for (int w = 0; w < NW; ++w) b[w] = lbits[(size_t)t * NW + w];
+          for (int v = 0; v < NW / 4; ++v) b[v] = reinterpret_cast<const uint4*>(lbits + (size_t)t * NW)[v];
         }
         __syncwarp();
         if (mv) {
-          lf[t + 1] = f;
-          lr[t + 1] = r;
-          lL[t + 1] = L;
+          lm[t + 1] = rec;
 #pragma unroll
-          for (int w = 0; w < NW; ++w) lbits[(size_t)(t + 1) * NW + w] = b[w];
+          for (int v = 0; v < NW / 4; ++v) reinterpret_cast<uint4*>(lbits + (size_t)(t + 1) * NW)[v] = b[v];
         }
         __syncwarp();
       }
-      if (lane == 0) {
-        lf[pos] = xf;
-        lr[pos] = (int32_t)(base + sidx[oi]);
-        lL[pos] = xL;
-      }
+      if (lane == 0) lm[ge] = RankRec{xf, (int32_t)(base + sidx[oi]), xL};
 #pragma unroll
       for (int w = 0; w < NW; ++w)
-        if (lane == w) lbits[(size_t)pos * NW + w] = xb[w];
+        if (lane == w) lbits[(size_t)ge * NW + w] = xb[w];
       __syncwarp();
       n = m + 1;
     }
     if (n > d.T) n = d.T;
     for (int i = lane; i < n; i += 32) {
-      d.list_ref[i] = lr[i];
-      d.list_f[i] = lf[i];
+      const RankRec rec = lm[i];
+      d.list_ref[i] = rec.r;
+      d.list_f[i] = rec.f;
     }
     if (lane == 0) {
       Ctl* ctl = d.ctl;
@@ -1653,8 +1660,8 @@ __global__ void __launch_bounds__(kRankWarpThreads) k_rank_warp(EaDev d, int Pp)
 // Shared bytes of k_rank_warp<NW> for population P (padded Pp), list T.
 static size_t rank_warp_smem(int P, int Pp, int T, int Lmax, int NW) {
   const size_t cap = (size_t)T + P;
-  return (size_t)Pp * 12 + 4 * (Pp & 1) + ((size_t)P + cap) * 8 + ((size_t)P + 2 * cap) * 4 +
-         (size_t)((Lmax + 1 + 3) & ~3) * 4 + ((size_t)P + cap) * NW * 4;
+  return (size_t)Pp * 12 + 4 * (Pp & 1) + (size_t)P * 12 + 16 + cap * sizeof(RankRec) +
+         ((size_t)P + cap) * NW * 4 + (size_t)(Lmax + 1) * 4;
 }
 
 // ---------------------------------------------------------------------------
