@@ -110,10 +110,12 @@ k_features(const uint16_t* __restrict__ seq, const int32_t* __restrict__ len, in
 // GEMM on the tensor cores: C[M x N] = op(A)[M x K] . op(B)[K x N], bf16
 // operands, fp32 accumulation (mma.sync m16n8k16).  op(A)(m, k) = A[m*lda+k]
 // (TA: A[k*lda+m]); op(B)(k, n) = B[k*ldb+n] (TB: B[n*ldb+k]).  CTA tile
-// 64 x 64 x 32, four warps of 32 x 32.  gridDim.z splits K (fp32 atomic
-// accumulation, EPI_F32_ADD only).  grid = (M tiles, N tiles, K splits).
+// 64 x 64 x 32, four warps of 32 x 32.  gridDim.z splits K: with
+// EPI_F32_SPLIT split z writes its partial product to slice z of Cf
+// ([splits][M][ldc]), summed afterwards in split order (k_sum_splits), so the
+// result does not depend on scheduling.  grid = (M tiles, N tiles, K splits).
 // ---------------------------------------------------------------------------
-enum { EPI_BIAS_RELU_BF16 = 0, EPI_MASK_BF16 = 1, EPI_F32 = 2, EPI_F32_ADD = 3 };
+enum { EPI_BIAS_RELU_BF16 = 0, EPI_MASK_BF16 = 1, EPI_F32 = 2, EPI_F32_SPLIT = 3 };
 constexpr int kBM = 64, kBN = 64, kBK = 32;
 
 __device__ __forceinline__ uint32_t pack2(bf16 lo, bf16 hi) {
@@ -205,16 +207,18 @@ k_gemm_bf16(int M, int N, int K, const bf16* __restrict__ A, int lda, const bf16
         } else if (EPI == EPI_F32) {
           Cf[(size_t)m * ldc + n] = v;
         } else {
-          atomicAdd(&Cf[(size_t)m * ldc + n], v);
+          Cf[(size_t)blockIdx.z * M * ldc + (size_t)m * ldc + n] = v;
         }
       }
 }
 
-// y = h2 . w3 + b3 (warp per row); with targets: loss sum and dy = 2 (y - t) / B
+// y = h2 . w3 + b3 (warp per row); with targets: dy = 2 (y - t) / B and the
+// row's share of the mean squared error, (y - t)^2 / B, in sq (summed later
+// in row order)
 __global__ void __launch_bounds__(256)
 k_out(const bf16* __restrict__ h2, const float* __restrict__ w3, const float* __restrict__ b3,
       int n, float* __restrict__ y, const float* __restrict__ t, const int32_t* __restrict__ idx,
-      float* __restrict__ dy, float* __restrict__ loss_sum) {
+      float* __restrict__ dy, float* __restrict__ sq) {
   const int lane = threadIdx.x & 31;
   const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (b >= n) return;
@@ -229,7 +233,7 @@ k_out(const bf16* __restrict__ h2, const float* __restrict__ w3, const float* __
       const float tt = t[idx ? idx[b] : b];
       const float r = s - tt;
       dy[b] = 2.f * r / (float)n;
-      atomicAdd(loss_sum, r * r / (float)n);
+      sq[b] = r * r / (float)n;
     }
   }
 }
@@ -269,24 +273,66 @@ k_colsum(const bf16* __restrict__ Xb, const float* __restrict__ Xf, int n, int c
   }
 }
 
-// dEmb[c] += dx[b][0:64] for every column c of series b
+// Embedding gradient without atomics: dEmb[c] = sum over the batch's series
+// b of (occurrences of c in series b) * dx[b][0:64].  CTA (column tile of 64,
+// series segment) accumulates its segment in series order into
+// part[segment][c][64]; k_emb_grad_reduce adds the segments in order.
+constexpr int kEmbSeg = 32;     // series per chunk held in shared memory
 __global__ void __launch_bounds__(256)
-k_emb_scatter(const uint16_t* __restrict__ seq, const int32_t* __restrict__ len, int32_t stride,
-              const int32_t* __restrict__ idx, int n, int32_t C, const float* __restrict__ dx,
-              float* __restrict__ demb) {
-  const int lane = threadIdx.x & 31;
-  const int b = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  if (b >= n) return;
-  const long long r = idx ? (long long)idx[b] : b;
-  const int L = min(max(len[r], 0), stride);
-  const uint16_t* s = seq + (size_t)r * stride;
-  const float g0 = dx[(size_t)b * kF + lane], g1 = dx[(size_t)b * kF + 32 + lane];
-  for (int i = 0; i < L; ++i) {
-    const int c = s[i];
-    if (c >= C) continue;
-    atomicAdd(&demb[(size_t)c * kEmb + lane], g0);
-    atomicAdd(&demb[(size_t)c * kEmb + 32 + lane], g1);
+k_emb_grad_part(const uint16_t* __restrict__ seq, const int32_t* __restrict__ len, int32_t stride,
+                const int32_t* __restrict__ idx, int32_t B, int32_t C, int32_t seg_len,
+                const float* __restrict__ dx, float* __restrict__ part) {
+  __shared__ float dxs[kEmbSeg][kEmb];
+  __shared__ uint8_t cnt[kEmbSeg][64];
+  const int tid = threadIdx.x;
+  const int c0 = blockIdx.x * 64, seg = blockIdx.y;
+  const int cc = tid >> 2, k0 = (tid & 3) * 16;            // column in tile, 16 dims
+  float acc[16];
+#pragma unroll
+  for (int q = 0; q < 16; ++q) acc[q] = 0.f;
+  const int b_lo = seg * seg_len, b_hi = min(B, b_lo + seg_len);
+  for (int b0 = b_lo; b0 < b_hi; b0 += kEmbSeg) {
+    for (int i = tid; i < kEmbSeg * kEmb; i += 256) {
+      const int bb = i / kEmb, k = i % kEmb;
+      dxs[bb][k] = b0 + bb < b_hi ? dx[(size_t)(b0 + bb) * kF + k] : 0.f;
+    }
+    for (int i = tid; i < kEmbSeg * 64; i += 256) cnt[i / 64][i % 64] = 0;
+    __syncthreads();
+    if (tid < kEmbSeg && b0 + tid < b_hi) {                  // one thread per series
+      const long long r = idx ? (long long)idx[b0 + tid] : b0 + tid;
+      const int L = min(max(len[r], 0), stride);
+      const uint16_t* sp = seq + (size_t)r * stride;
+      for (int i = 0; i < L; ++i) {
+        const int c = sp[i] - c0;
+        if (c >= 0 && c < 64 && sp[i] < C) cnt[tid][c] += 1;
+      }
+    }
+    __syncthreads();
+    const int nb = min(kEmbSeg, b_hi - b0);
+    for (int bb = 0; bb < nb; ++bb) {
+      const float w = (float)cnt[bb][cc];
+      if (w != 0.f) {
+#pragma unroll
+        for (int q = 0; q < 16; ++q) acc[q] += w * dxs[bb][k0 + q];
+      }
+    }
+    __syncthreads();
   }
+  const int c = c0 + cc;
+  if (c < C) {
+    float* o = part + ((size_t)seg * C + c) * kEmb + k0;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) o[q] = acc[q];
+  }
+}
+
+__global__ void k_sum_splits(const float* __restrict__ part, int splits, long long count,
+                             float* __restrict__ out) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= count) return;
+  float s = 0.f;
+  for (int z = 0; z < splits; ++z) s += part[(size_t)z * count + i];
+  out[i] = s;
 }
 
 // Adam over one flat parameter array; optional bf16 copy of the result
@@ -334,7 +380,12 @@ __global__ void k_targets(const double* __restrict__ f, long long n, float mean,
   if (i < n) t[i] = (float)((log1p(f[i]) - (double)mean) / (double)sd);
 }
 
-__global__ void k_sum_log1p(const double* __restrict__ f, long long n, double* out) {
+// Sum and sum of squares of log1p(f): block b writes its partial sums to
+// out[2 b], out[2 b + 1] (a fixed-order tree inside the block); the host adds
+// the blocks in order.
+__global__ void __launch_bounds__(256) k_sum_log1p(const double* __restrict__ f, long long n,
+                                                  double* __restrict__ out) {
+  __shared__ double r1[256], r2[256];
   double s = 0.0, s2 = 0.0;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
@@ -342,8 +393,20 @@ __global__ void k_sum_log1p(const double* __restrict__ f, long long n, double* o
     s += v;
     s2 += v * v;
   }
-  atomicAdd(&out[0], s);
-  atomicAdd(&out[1], s2);
+  r1[threadIdx.x] = s;
+  r2[threadIdx.x] = s2;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      r1[threadIdx.x] += r1[threadIdx.x + o];
+      r2[threadIdx.x] += r2[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[2 * blockIdx.x] = r1[0];
+    out[2 * blockIdx.x + 1] = r2[0];
+  }
 }
 
 // minibatch indices: idx[b] = floor(u * n), u from Philox-4x32-10 keyed by (seed, step)
@@ -609,15 +672,25 @@ struct ebic_surrogate_ctx {
   DevBuf ferr;                 // set by the fused forward on a copy timeout
   // training activations (capacity rows)
   int32_t cap = 0;
-  DevBuf act, dh1, dh2, dx, y, dy, idx, loss, tgt, tmp;
+  DevBuf act, dh1, dh2, dx, y, dy, idx, loss, tgt, tmp, sq, split, epart;
   // training log: series [log_n][kLogStride], lengths, exact fitness
   long long log_n = 0, log_cap = 0;
   DevBuf log_seq, log_len, log_fit;
+
+  // series per segment of the embedding gradient: at most 32 segments and at
+  // most 16 MB of partial sums, each segment a multiple of 32 series
+  int emb_seg_len(int B) const {
+    long long segs = std::min<long long>(32, std::max<long long>(1, (16ll << 20) / ((long long)C * 64 * 4)));
+    segs = std::min<long long>(segs, (B + 31) / 32);
+    long long len = (B + segs - 1) / segs;
+    return (int)((len + 31) / 32 * 32);
+  }
 };
 
 namespace ebic {
 
 constexpr int kLogStride = EBIC_MAX_EA_LEN;
+constexpr int kSumBlocks = 456;     // partial sums of the target statistics
 
 // x [rows][80] | h1 [rows][256] | h2 [rows][256], bf16, each 256-byte aligned
 static inline size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
@@ -652,6 +725,11 @@ static ebic_status sur_reserve(ebic_surrogate_ctx* s, int32_t rows) {
   EBIC_TRY(s->y.reserve(r * sizeof(float)));
   EBIC_TRY(s->dy.reserve(r * sizeof(float)));
   EBIC_TRY(s->idx.reserve(r * sizeof(int32_t)));
+  EBIC_TRY(s->sq.reserve(r * sizeof(float)));
+  const int ks = std::max(1, std::min(32, rows / 256));
+  EBIC_TRY(s->split.reserve((size_t)ks * kH * kH * sizeof(float)));
+  const int seg = s->emb_seg_len(rows);
+  EBIC_TRY(s->epart.reserve((size_t)((rows + seg - 1) / seg) * s->C * kEmb * sizeof(float)));
   s->cap = rows;
   return EBIC_OK;
 }
@@ -713,35 +791,45 @@ static ebic_status sur_step(ebic_surrogate_ctx* s, const uint16_t* seq, const in
   sur_hidden(s, seq, len, stride, idx, B, a, st);
   float* P = s->par.as<float>();
   float* G = s->grad.as<float>();
-  EBIC_CUDA_TRY(cudaMemsetAsync(G, 0, (size_t)s->n_par * sizeof(float), st));
-  EBIC_CUDA_TRY(cudaMemsetAsync(s->loss.ptr, 0, sizeof(float), st));
   const unsigned wb = (unsigned)((B + 7) / 8);
   k_out<<<wb, 256, 0, st>>>(a.h2, P + s->o_w3, P + s->o_b3, B, s->y.as<float>(), t, idx,
-                            s->dy.as<float>(), s->loss.as<float>());
+                            s->dy.as<float>(), s->sq.as<float>());
+  k_colsum<<<1, 256, 0, st>>>(nullptr, s->sq.as<float>(), B, 1, nullptr, s->loss.as<float>());
   // output layer
   k_colsum<<<(kH + 31) / 32, 256, 0, st>>>(a.h2, nullptr, B, kH, s->dy.as<float>(), G + s->o_w3);
   k_colsum<<<1, 256, 0, st>>>(nullptr, s->dy.as<float>(), B, 1, nullptr, G + s->o_b3);
   const long long nb = (long long)B * kH;
   k_dh2<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(s->dy.as<float>(), P + s->o_w3, a.h2, B,
                                                       s->dh2.as<bf16>());
-  // layer 2: dW2 = h1^T dh2, db2, dh1 = (dh2 W2^T) [h1 > 0]
+  // layer 2: dW2 = h1^T dh2 (split K, partials summed in order), db2,
+  // dh1 = (dh2 W2^T) [h1 > 0]
   const int ks = std::max(1, std::min(32, B / 256));
-  gemm<true, false, EPI_F32_ADD>(kH, kH, B, a.h1, kH, s->dh2.as<bf16>(), kH, nullptr, nullptr, 0,
-                                 G + s->o_w2, nullptr, kH, ks, st);
+  float* split = s->split.as<float>();
+  gemm<true, false, EPI_F32_SPLIT>(kH, kH, B, a.h1, kH, s->dh2.as<bf16>(), kH, nullptr, nullptr,
+                                   0, split, nullptr, kH, ks, st);
+  k_sum_splits<<<(kH * kH + 255) / 256, 256, 0, st>>>(split, ks, (long long)kH * kH, G + s->o_w2);
   k_colsum<<<(kH + 31) / 32, 256, 0, st>>>(s->dh2.as<bf16>(), nullptr, B, kH, nullptr,
                                            G + s->o_b2);
   gemm<false, true, EPI_MASK_BF16>(B, kH, kH, s->dh2.as<bf16>(), kH, s->w2b.as<bf16>(), kH,
                                    nullptr, a.h1, kH, nullptr, s->dh1.as<bf16>(), kH, 1, st);
   // layer 1: dW1 = x^T dh1, db1, dx = dh1 W1^T, then the embedding rows
-  gemm<true, false, EPI_F32_ADD>(kF, kH, B, a.x, kF, s->dh1.as<bf16>(), kH, nullptr, nullptr, 0,
-                                 G + s->o_w1, nullptr, kH, ks, st);
+  gemm<true, false, EPI_F32_SPLIT>(kF, kH, B, a.x, kF, s->dh1.as<bf16>(), kH, nullptr, nullptr, 0,
+                                   split, nullptr, kH, ks, st);
+  k_sum_splits<<<(kF * kH + 255) / 256, 256, 0, st>>>(split, ks, (long long)kF * kH, G + s->o_w1);
   k_colsum<<<(kH + 31) / 32, 256, 0, st>>>(s->dh1.as<bf16>(), nullptr, B, kH, nullptr,
                                            G + s->o_b1);
   gemm<false, true, EPI_F32>(B, kF, kH, s->dh1.as<bf16>(), kH, s->w1b.as<bf16>(), kH, nullptr,
                              nullptr, 0, s->dx.as<float>(), nullptr, kF, 1, st);
-  k_emb_scatter<<<wb, 256, 0, st>>>(seq, len, stride, idx, B, s->C, s->dx.as<float>(),
-                                    G + s->o_emb);
-  count_launches(14);
+  {
+    const int seg = s->emb_seg_len(B);
+    const dim3 eg((unsigned)((s->C + 63) / 64), (unsigned)((B + seg - 1) / seg));
+    k_emb_grad_part<<<eg, 256, 0, st>>>(seq, len, stride, idx, B, s->C, seg, s->dx.as<float>(),
+                                        s->epart.as<float>());
+    const long long ne = (long long)s->C * kEmb;
+    k_sum_splits<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(s->epart.as<float>(), (int)eg.y, ne,
+                                                              G + s->o_emb);
+  }
+  count_launches(17);
   if (update) {
     s->steps_done += 1;
     const float b1 = 0.9f, b2 = 0.999f;
@@ -845,7 +933,7 @@ static ebic_status sur_create(ebic_ctx* h, int32_t len_scale, uint64_t seed,
   EBIC_TRY(s->cmean.reserve((size_t)s->C * sizeof(float)));
   EBIC_TRY(s->csd.reserve((size_t)s->C * sizeof(float)));
   EBIC_TRY(s->loss.reserve(sizeof(float)));
-  EBIC_TRY(s->tmp.reserve(2 * sizeof(double)));
+  EBIC_TRY(s->tmp.reserve(2 * kSumBlocks * sizeof(double)));
   std::vector<float> p;
   init_weights(s, p);
   EBIC_CUDA_TRY(cudaMemcpyAsync(s->par.ptr, p.data(), pb, cudaMemcpyHostToDevice, s->stream));
@@ -864,13 +952,17 @@ static ebic_status sur_train(ebic_surrogate_ctx* s, const uint16_t* seq, const i
   cudaStream_t st = s->stream;
   // standardised log1p targets over the whole set
   EBIC_TRY(s->tgt.reserve((size_t)n * sizeof(float)));
-  EBIC_CUDA_TRY(cudaMemsetAsync(s->tmp.ptr, 0, 2 * sizeof(double), st));
-  k_sum_log1p<<<456, 256, 0, st>>>(fit, n, s->tmp.as<double>());
-  double m2[2];
+  k_sum_log1p<<<kSumBlocks, 256, 0, st>>>(fit, n, s->tmp.as<double>());
+  double m2[2 * kSumBlocks];
   EBIC_CUDA_TRY(cudaMemcpyAsync(m2, s->tmp.ptr, sizeof(m2), cudaMemcpyDeviceToHost, st));
   EBIC_CUDA_TRY(cudaStreamSynchronize(st));
-  const double mean = m2[0] / (double)n;
-  const double var = m2[1] / (double)n - mean * mean;
+  double s1 = 0.0, s2 = 0.0;
+  for (int i = 0; i < kSumBlocks; ++i) {
+    s1 += m2[2 * i];
+    s2 += m2[2 * i + 1];
+  }
+  const double mean = s1 / (double)n;
+  const double var = s2 / (double)n - mean * mean;
   s->t_mean = (float)mean;
   s->t_sd = (float)std::sqrt(var > 1e-12 ? var : 1.0);
   k_targets<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(fit, n, s->t_mean, s->t_sd,

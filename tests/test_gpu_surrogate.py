@@ -314,3 +314,22 @@ def test_trained_surrogate_picks_fitter_children(paper_problem):
     finally:
         eb.ebic_run_screen(h, None, 1, eb.SCREEN_OFF)
         eb.ebic_surrogate_free(s)
+
+
+def test_training_is_deterministic(paper_problem):
+    """Two surrogates created with the same seed and trained on the same log
+    end with bit-identical parameters (no atomics in the reverse pass), and a
+    large minibatch exercises the split-K weight gradients."""
+    prob, h = paper_problem
+    _plain_run(h, 50, iters=20)
+    out = []
+    for _ in range(2):
+        s = eb.ebic_surrogate_create(h, 20, 77)
+        try:
+            eb.ebic_surrogate_log(s, h)
+            loss = eb.ebic_surrogate_train(s, 40, 2048, 1e-3)
+            out.append((eb.ebic_surrogate_params(s), loss))
+        finally:
+            eb.ebic_surrogate_free(s)
+    assert_bits_equal(out[0][0], out[1][0], "trained parameters")
+    assert out[0][1] == out[1][1]
