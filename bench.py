@@ -707,22 +707,23 @@ def roofline(wl, gens, extra, per_step_ms, peaks):
     dom = max(kern, key=kern.get)
     if dom != "k_build":
         return {"dominant_kernel": dom, "kernel_us": kern}
-    # The Step 3 builder is sequential: one warp decides attempt after attempt.
-    # Its bound is that warp's issue rate: one warp-instruction per cycle at
-    # the SM clock.  Work per launch = the kernel's warp-instructions (ncu
-    # count committed under profiles/ for this kernel build).
+    # The Step 3 builder is sequential and runs in one CTA (one SM).  Its
+    # bound is that SM's issue rate: four warp-instructions per cycle (one
+    # per sub-partition) at the SM clock.  Work per launch = the kernel's
+    # warp-instructions (ncu count committed under profiles/ for this kernel
+    # build).
     prof = read_profile("k_build-generations-paper-1000x100.json")
     inst = prof.get("smsp__inst_executed.sum") if prof else None
     mhz = (extra.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0)
-    peak = mhz * 1e6 / 1e9                       # G warp-instructions / s
+    peak = 4 * mhz * 1e6 / 1e9                   # G warp-instructions / s
     dur = kern["k_build"] * 1e-6
     achieved = inst / dur / 1e9 if inst else None
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G warp-inst/s",
             "frac": achieved / peak if achieved else None,
             "traffic": prof.get("dram_bytes_per_launch") if prof else None,
-            "kernel": "k_build (Step 3 builder, one CTA, one deciding warp)",
+            "kernel": "k_build (Step 3 builder, one CTA of four warps on one SM)",
             "work_per_launch": inst, "work_def": "warp-instructions per launch (ncu)",
-            "peak_source": "1 warp-instruction/cycle x median SM clock sampled in this run",
+            "peak_source": "4 warp-instructions/cycle (one SM) x median SM clock sampled in this run",
             "kernel_us": kern}
 
 
