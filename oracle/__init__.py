@@ -77,6 +77,9 @@ def _load():
             lib.or_draw.restype = ctypes.c_uint32
             lib.or_support.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, _P,
                                        ctypes.c_int32, _P, _P, ctypes.c_int32]
+            lib.or_rows.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
+                                    ctypes.c_int32, _P]
+            lib.or_rows.restype = ctypes.c_int32
             lib.or_fitness.argtypes = [ctypes.c_int64, ctypes.c_int32, ctypes.c_int32]
             lib.or_fitness.restype = ctypes.c_double
             lib.or_omp_max_threads.restype = ctypes.c_int32
@@ -222,6 +225,38 @@ def toprank_update(list_seqs, list_f, pop_seqs, pop_f, T, tau):
                                   _ptr(ocols), _ptr(of))
     seqs = [ocols[ooff[i]:ooff[i + 1]].tolist() for i in range(n)]
     return seqs, of[:n].copy()
+
+
+def rows(A, seq, mode: int = 0) -> np.ndarray:
+    """Step 6: rows rising strictly along seq (mode 0); with Step 7's
+    negative-trend expansion, rows rising or falling strictly (mode 1)."""
+    A = _c(A, np.float32)
+    R, C = A.shape
+    s = np.ascontiguousarray(seq, np.int32)
+    out = np.zeros(R, np.int32)
+    n = _load().or_rows(_ptr(A), R, C, _ptr(s), len(s), int(mode), _ptr(out))
+    return out[:n].copy()
+
+
+def recovery_relevance(expected, found):
+    """Eq. (2)-(3): a bicluster is the set of cells rows x cols; the Jaccard
+    index of two biclusters is |e & f| / |e | f| over cells.  Recovery is the
+    mean over expected biclusters of the best Jaccard index against the found
+    ones, relevance the mean over found biclusters of the best against the
+    expected ones (reading: the sums of Eq. (2)-(3) divided by the number of
+    terms, which puts both in [0, 1]; no found bicluster gives 0 and 0)."""
+    def jac(e, f):
+        er, ec = set(map(int, e[0])), set(map(int, e[1]))
+        fr, fc = set(map(int, f[0])), set(map(int, f[1]))
+        inter = len(er & fr) * len(ec & fc)
+        union = len(er) * len(ec) + len(fr) * len(fc) - inter
+        return inter / union if union else 0.0
+    if not expected or not found:
+        return 0.0, 0.0
+    J = [[jac(e, f) for f in found] for e in expected]
+    rec = sum(max(row) for row in J) / len(expected)
+    rel = sum(max(J[i][j] for i in range(len(expected))) for j in range(len(found))) / len(found)
+    return rec, rel
 
 
 def make_params(**kw) -> Params:

@@ -11,6 +11,7 @@
 //   support          -- section "Motivation": #{k : a_kp < a_kq < a_kr ...}
 //   fitness          -- Eq. (1)
 //   CBF              -- Fig. 3 (offsets + column indices)
+//   rows of a series -- Step 6 (and Step 7's negative-trend expansion)
 //   tournament/penalty, mutations, crossover, tabu list, elitism,
 //   top-rank list    -- section "EBIC Algorithm", Steps 1-5, and the paragraph
 //                       on genetic operations and crowding (Fig. 1)
@@ -424,6 +425,25 @@ uint32_t or_draw(uint64_t seed, int32_t g, int32_t j, int32_t d) { return draw(s
 
 // Support of every series of a CBF population (offsets has P + 1 entries).
 // A is row-major R x C.  nthreads > 1 splits the series across OpenMP threads.
+// Step 6 ("determine ... the indices of rows that match each of the series"):
+// the rows whose values rise strictly along the series (mode 0), or -- Step 7's
+// expansion by negative trends -- the rows that rise or fall strictly along it
+// (mode 1).  Row indices ascending into out_rows; returns their number.
+int32_t or_rows(const float* A, int32_t R, int32_t C, const int32_t* s, int32_t L, int32_t mode,
+                int32_t* out_rows) {
+  int32_t n = 0;
+  for (int32_t k = 0; k < R; ++k) {
+    const float* row = A + (size_t)k * (size_t)C;
+    bool rising = true, falling = true;
+    for (int32_t i = 0; i + 1 < L; ++i) {
+      if (!(row[s[i]] < row[s[i + 1]])) rising = false;
+      if (!(row[s[i]] > row[s[i + 1]])) falling = false;
+    }
+    if (rising || (mode == 1 && falling)) out_rows[n++] = k;
+  }
+  return n;
+}
+
 void or_support(const float* A, int32_t R, int32_t C, const int32_t* offsets,
                 const int32_t* cols, int32_t P, uint32_t* inc, uint32_t* dec, int32_t nthreads) {
 #ifdef _OPENMP
