@@ -338,6 +338,47 @@ ebic_status ebic_run_generations(ebic_handle h, const ebic_params_t* p, int32_t*
                                  ebic_stats_t* stats);
 
 /* ---------------------------------------------------------------------------
+ * Step 6 ("Prepare biclusters": the indices of the rows that match each
+ * series of columns) and Step 7's expansion by negative trends.
+ * EBIC_ROWS_RISING: the rows whose values rise strictly along the series (the
+ * support of Step 4, as a list).  EBIC_ROWS_RISING_OR_FALLING: also the rows
+ * that fall strictly along it (negative trends).  A one-column series matches
+ * every row.  The expansion by "approximate" trends is not defined by the
+ * paper and is not offered.
+ *
+ * offsets / cols: a CBF population as for ebic_eval_population (host).
+ * row_offsets[P + 1] (host, int64) and rows (host): the row indices of series
+ * i, ascending, are rows[row_offsets[i] .. row_offsets[i + 1]).
+ * *inout_capacity: entries of `rows` on entry, entries written on return.  If
+ * the rows do not fit, the call returns EBIC_ERR_ARG with the number needed in
+ * *inout_capacity and writes nothing else (rows may be NULL to ask for it).
+ * ------------------------------------------------------------------------- */
+typedef enum {
+  EBIC_ROWS_RISING = 0,
+  EBIC_ROWS_RISING_OR_FALLING = 1
+} ebic_rows_mode;
+ebic_status ebic_extract_rows(ebic_handle h, const int32_t* offsets, const int32_t* cols,
+                              int32_t P, int32_t mode, int64_t* row_offsets, int32_t* rows,
+                              int64_t* inout_capacity);
+
+/* Recovery and relevance, Eq. (2)-(3): a bicluster is the set of cells rows x
+ * columns and the Jaccard index of two biclusters is |e & f| / |e | f| over
+ * cells.  recovery = mean over the E expected biclusters of the best index
+ * against the F found ones; relevance = mean over the found ones of the best
+ * against the expected ones (the paper's sums divided by their number of
+ * terms).  Each bicluster is given as ascending, distinct row and column
+ * indices in CSR form (host buffers: *_off[n + 1] int64 offsets into the
+ * index arrays).  out_jaccard (nullable, host, E x F row-major) receives the
+ * pairwise indices.  E or F = 0 gives 0 and 0.  Synchronous; runs on the
+ * current device. */
+ebic_status ebic_recovery_relevance(int32_t E, const int64_t* e_row_off, const int32_t* e_rows,
+                                    const int64_t* e_col_off, const int32_t* e_cols, int32_t F,
+                                    const int64_t* f_row_off, const int32_t* f_rows,
+                                    const int64_t* f_col_off, const int32_t* f_cols,
+                                    double* out_recovery, double* out_relevance,
+                                    double* out_jaccard);
+
+/* ---------------------------------------------------------------------------
  * Fitness surrogate and offspring screening.  The paper has no counterpart:
  * EBIC evaluates every child exactly (Step 4).  This is an optional
  * pre-screen: a small learned model predicts which of several candidate

@@ -35,11 +35,13 @@ __all__ = [
     "ebic_surrogate_colstats", "ebic_surrogate_step", "ebic_surrogate_log", "ebic_surrogate_train",
     "ebic_surrogate_target_norm", "ebic_surrogate_predict", "ebic_run_screen",
     "SCREEN_OFF", "SCREEN_SURROGATE", "SCREEN_PSEUDO",
+    "ebic_extract_rows", "ebic_recovery_relevance", "ROWS_RISING", "ROWS_RISING_OR_FALLING",
 ]
 
 PATH_AUTO, PATH_GATHER, PATH_BITMASK = 0, 1, 2
 SUPPORT_INC, SUPPORT_INC_PLUS_DEC = 0, 1
 SCREEN_OFF, SCREEN_SURROGATE, SCREEN_PSEUDO = 0, 1, 2
+ROWS_RISING, ROWS_RISING_OR_FALLING = 0, 1
 STATUS = {0: "EBIC_OK", 1: "EBIC_ERR_ARG", 2: "EBIC_ERR_CUDA", 3: "EBIC_ERR_OOM",
           4: "EBIC_ERR_TIMEOUT", 5: "EBIC_ERR_STATE", 6: "EBIC_ERR_CANCELLED",
           7: "EBIC_ERR_DEVICE"}
@@ -120,6 +122,8 @@ _SIGS = {
     "ebic_surrogate_target_norm": ([_P, _P, _P], _I32),
     "ebic_surrogate_predict": ([_P, _P, _P, _I32, ctypes.c_int64, _P, _P], _I32),
     "ebic_run_screen": ([_P, _P, _I32, _I32], _I32),
+    "ebic_extract_rows": ([_P, _P, _P, _I32, _I32, _P, _P, _P], _I32),
+    "ebic_recovery_relevance": ([_I32, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P], _I32),
 }
 
 _lock = threading.Lock()
@@ -518,3 +522,48 @@ def ebic_surrogate_predict(s, d_seq, d_len, stride: int, n: int, d_out, stream=N
 
 def ebic_run_screen(h, s=None, oversample: int = 1, mode: int = SCREEN_OFF):
     _check(lib().ebic_run_screen(h, s, int(oversample), int(mode)))
+
+
+# ---------------------------------------------------------------------------
+# Step 6 rows and Step 7 negative-trend expansion; Eq. (2)-(3)
+def ebic_extract_rows(h, offsets, cols, mode: int = ROWS_RISING):
+    """Rows matching each series of a CBF population: list of int32 arrays."""
+    off, po = _host(offsets, np.int32)
+    c, pc = _host(cols, np.int32)
+    P = len(off) - 1
+    roff = np.zeros(P + 1, np.int64)
+    cap = ctypes.c_int64(0)
+    st = lib().ebic_extract_rows(h, po, pc, P, int(mode), roff.ctypes.data_as(_P), None,
+                                 ctypes.byref(cap))
+    if st != 0 and cap.value == 0 and P > 0:
+        _check(st)
+    rows = np.zeros(max(1, cap.value), np.int32)
+    _check(lib().ebic_extract_rows(h, po, pc, P, int(mode), roff.ctypes.data_as(_P),
+                                   rows.ctypes.data_as(_P), ctypes.byref(cap)))
+    return [rows[roff[i]:roff[i + 1]].copy() for i in range(P)]
+
+
+def _csr(lists):
+    off = np.zeros(len(lists) + 1, np.int64)
+    for i, x in enumerate(lists):
+        off[i + 1] = off[i] + len(x)
+    v = np.concatenate([np.asarray(x, np.int32) for x in lists]) if lists else np.zeros(0, np.int32)
+    return off, np.ascontiguousarray(v if len(v) else np.zeros(1, np.int32), np.int32)
+
+
+def ebic_recovery_relevance(expected, found, want_jaccard: bool = False):
+    """expected / found: lists of (rows, cols) with ascending distinct indices."""
+    E, F = len(expected), len(found)
+    er, ev = _csr([e[0] for e in expected])
+    ec, ecv = _csr([e[1] for e in expected])
+    fr, fv = _csr([f[0] for f in found])
+    fc, fcv = _csr([f[1] for f in found])
+    rec, rel = ctypes.c_double(0), ctypes.c_double(0)
+    J = np.zeros(max(1, E * F), np.float64)
+    p = lambda a: a.ctypes.data_as(_P)
+    _check(lib().ebic_recovery_relevance(E, p(er), p(ev), p(ec), p(ecv), F, p(fr), p(fv), p(fc),
+                                         p(fcv), ctypes.byref(rec), ctypes.byref(rel),
+                                         p(J) if want_jaccard else None))
+    if want_jaccard:
+        return rec.value, rel.value, J[:E * F].reshape(E, F)
+    return rec.value, rel.value

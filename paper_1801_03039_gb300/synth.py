@@ -100,6 +100,28 @@ def matrix_paper(seed: int = 0, noise: float = 0.01) -> Problem:
     return Problem("paper-1000x100", A.astype(np.float32), plants, sigma=25)
 
 
+def matrix_overlap(seed: int = 0, overlap: int = 0, noise: float = 0.01) -> Problem:
+    """200 x 150 (rows x columns), N(0,1) background with three 20 x 20
+    order-preserving biclusters, each sharing ``overlap`` rows and
+    ``overlap`` columns with the next (the paper's overlap benchmark shape:
+    0x0, 3x3, 6x6, 9x9).  A later plant overwrites an earlier one in the
+    shared cells."""
+    rng = np.random.default_rng(seed)
+    R, C = 200, 150
+    A = rng.standard_normal((R, C)).astype(np.float64)
+    rows = rng.permutation(R)
+    cols = rng.permutation(C)
+    plants = []
+    r0 = c0 = 0
+    for b in range(3):
+        pr = rows[r0:r0 + 20]
+        pc = cols[c0:c0 + 20]
+        plants.append(_plant_op(rng, A, pr, pc, noise))
+        r0 += 20 - overlap
+        c0 += 20 - overlap
+    return Problem(f"overlap-200x150-{overlap}", A.astype(np.float32), plants, sigma=10)
+
+
 def matrix_expression(seed: int = 0, R: int = 20000, C: int = 200, n_plants: int = 10,
                       noise: float = 0.05) -> Problem:
     """Expression-shaped: log-normal(0, 1) background, ``n_plants`` order-preserving
