@@ -100,7 +100,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL,
+                 "-lms", "50", "-f", self.path], stdout=subprocess.DEVNULL,
                 stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
@@ -147,6 +147,7 @@ def load_peaks() -> dict:
 # ---------------------------------------------------------------------------
 class EvalExpression:
     name = "eval-expression"
+    DEFAULT_STEPS = 20000          # about 0.5 s of timed passes
     R, C, P, LMIN, LMAX, SIGMA = 20000, 200, 4096, 3, 30, 50
 
     def __init__(self, rank: int):
@@ -258,6 +259,7 @@ class GenerationsPaper:
     (Steps 2-5: elitism, tournaments, operators, tabu, evaluation, top-rank)."""
     name = "generations-paper"
     R, C, P, LMIN, LMAX, SIGMA, T, GENS = 1000, 100, 600, 3, 20, 25, 100, 1000
+    DEFAULT_STEPS = 1000           # the configuration's 1,000 generations
 
     def __init__(self, rank: int):
         from paper_1801_03039_gb300 import synth
@@ -342,6 +344,7 @@ class GenerationsScreened(GenerationsPaper):
     comparison (1,000 generations each, same seed) run outside the timed
     region."""
     name = "generations-screened"
+    DEFAULT_STEPS = 1000
     V = 8
     TRAIN_SEEDS = (1001, 1002)       # 2 plain runs x 1,001 generations x 600 = 1.2M pairs
     HOLDOUT_SEED = 1003
@@ -518,6 +521,7 @@ class EvalBatch:
     20-500, populations 256-2,048, lengths 3-30): one step is one persistent
     launch over all of them (graph replay)."""
     name = "eval-batch"
+    DEFAULT_STEPS = 300
 
     def __init__(self, rank: int):
         from paper_1801_03039_gb300 import synth
@@ -766,8 +770,9 @@ def run_reference(args, ws, rank):
     import oracle
     wl = WORKLOADS[args.workload](0)
     cores = os.cpu_count() or 1
+    per_step = min(1.0, max(0.02, 120.0 / max(args.steps, 1)))   # seconds of oracle work
     if isinstance(wl, GenerationsPaper):
-        g, _ = wl.oracle_generations(oracle, 4.0)
+        g, _ = wl.oracle_generations(oracle, 4.0 * per_step)
         for _ in range(args.warmup):
             oracle.run(wl.prob.A, **wl.params_kw(1))
         t0 = time.perf_counter()
@@ -778,7 +783,7 @@ def run_reference(args, ws, rank):
         sample = f"each step: Step 1 + {g} generations, sequential oracle on one core"
         used = 1
     else:
-        n, _ = wl.oracle_sample(oracle, 8.0, cores)
+        n, _ = wl.oracle_sample(oracle, 4.0 * per_step, cores)
         if isinstance(wl, EvalBatch):
             big = max(wl.items, key=lambda x: x.problem.A.shape[0])
             A, off, cols = big.problem.A, big.offsets[:n + 1], big.cols[:big.offsets[n]]
@@ -810,13 +815,20 @@ def run_reference(args, ws, rank):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default: the configured 1,000 generations for the "
+                         "generation workloads, about half a second of GPU work for the "
+                         "others; 20 for --impl reference)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="generations-paper")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")
+    if args.steps is None:
+        args.steps = 20 if args.impl == "reference" else WORKLOADS[args.workload].DEFAULT_STEPS
+    if args.steps < 1:
+        ap.error("--steps must be at least 1")
     ws, rank, local = dist_env()
     if args.impl == "reference":
         out = run_reference(args, ws, rank)
