@@ -87,7 +87,8 @@ def barrier(ws: int):
 class ClockSampler:
     FIELDS = ("pci.bus_id,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap,"
+              "timestamp")
 
     def __init__(self, bus_id: str | None):
         self.bus_id = (bus_id or "").lower()
@@ -105,10 +106,21 @@ class ClockSampler:
         except OSError:
             self.proc = None
         time.sleep(0.3)
+        self.t0 = time.time()
+
+    @staticmethod
+    def _when(stamp: str):
+        """nvidia-smi's local timestamp ("YYYY/MM/DD HH:MM:SS.mmm") as epoch seconds."""
+        try:
+            import datetime
+            return datetime.datetime.strptime(stamp.strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
 
     def stop(self) -> dict:
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        t1 = time.time()
         time.sleep(0.25)
         self.proc.terminate()
         try:
@@ -124,6 +136,11 @@ class ClockSampler:
         if len(buses) > 1 and self.bus_id:
             rows = [r for r in rows if r[0].lower()[-7:] == self.bus_id[-7:]]
         os.unlink(self.path)
+        # keep the samples taken inside the timed region when the stamps allow
+        inside = [r for r in rows if len(r) >= 10 and (self._when(r[9]) or 0) >= self.t0 - 0.05
+                  and (self._when(r[9]) or 0) <= t1 + 0.05]
+        if inside:
+            rows = inside
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
