@@ -323,6 +323,19 @@ ebic_status ebic_run_step_async(ebic_handle h, int32_t generations, void* stream
  * speculation, the sequential Step 3 builder, tabu insertion, Step 4
  * evaluation, Step 5 ranking.  Synchronous; for measurement. */
 ebic_status ebic_run_step_profiled(ebic_handle h, float* kernel_us);
+/* In-graph timing of the Step 3 builder, for measurement.  Set before
+ * ebic_run_init (it takes effect there; 0, the default, turns it off): the
+ * captured generation then holds two event-record nodes around k_build, and
+ * each replay by ebic_run_step / ebic_run_step_async points them at the next
+ * of `slots` event pairs (a replay that reuses a pair first waits for the one
+ * that used it).  EBIC_ERR_ARG unless 0 <= slots <= 2^20. */
+ebic_status ebic_set_kernel_timing(ebic_handle h, int32_t slots);
+/* Waits for every timed replay, then writes the mean k_build duration (us)
+ * and the number of replays it covers since the run began or since the last
+ * read with `reset` != 0, which starts the count again.  EBIC_ERR_STATE if the
+ * run was started without timing. */
+ebic_status ebic_read_kernel_timing(ebic_handle h, int32_t reset, double* mean_us,
+                                    long long* count);
 /* The current top-rank list as CBF: *inout_n = capacity in records on entry,
  * records written on return; offsets needs capacity + 1 entries and cols
  * capacity * len_max.  fitness / inc may be NULL. */

@@ -28,6 +28,7 @@ __all__ = [
     "ebic_batch_create", "ebic_batch_eval", "ebic_batch_describe", "ebic_batch_free",
     "BATCH_AUTOTUNE", "BATCH_GRAPH", "BATCH_BUILD_TABLES",
     "ebic_run_init", "ebic_run_step", "ebic_run_step_async", "ebic_run_step_profiled",
+    "ebic_set_kernel_timing", "ebic_read_kernel_timing",
     "ebic_get_toprank", "ebic_get_population",
     "ebic_run_generations", "Params", "Stats", "PATH_AUTO", "PATH_GATHER", "PATH_BITMASK",
     "SUPPORT_INC", "SUPPORT_INC_PLUS_DEC",
@@ -107,6 +108,8 @@ _SIGS = {
     "ebic_run_step": ([_P, _I32, _P], _I32),
     "ebic_run_step_async": ([_P, _I32, _P], _I32),
     "ebic_run_step_profiled": ([_P, _P], _I32),
+    "ebic_set_kernel_timing": ([_P, _I32], _I32),
+    "ebic_read_kernel_timing": ([_P, _I32, _P, _P], _I32),
     "ebic_get_toprank": ([_P, _P, _P, _P, _P, _P], _I32),
     "ebic_get_population": ([_P, _P, _P, _P, _P, _P, _P], _I32),
     "ebic_run_generations": ([_P, _P, _P, _P, _P, _P, _P], _I32),
@@ -378,6 +381,17 @@ def ebic_run_step_profiled(h) -> dict:
     us = (ctypes.c_float * 5)()
     _check(lib().ebic_run_step_profiled(h, us))
     return dict(zip(KERNELS, list(us)))
+
+
+def ebic_set_kernel_timing(h, slots: int) -> None:
+    _check(lib().ebic_set_kernel_timing(h, int(slots)))
+
+
+def ebic_read_kernel_timing(h, reset: bool = False):
+    """(mean k_build microseconds, replays covered) of the in-graph timing."""
+    us, n = ctypes.c_double(), ctypes.c_longlong()
+    _check(lib().ebic_read_kernel_timing(h, int(bool(reset)), ctypes.byref(us), ctypes.byref(n)))
+    return us.value, n.value
 
 
 def _records(off, cols, n):

@@ -1695,6 +1695,13 @@ struct EaState {
   int32_t launches_per_gen = 5;
   cudaStream_t side = nullptr;         // second branch of the generation graph
   cudaEvent_t fork_ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  // In-graph timing of k_build: two event-record nodes bracket it in the
+  // graph; each replay points them at the next pair of a ring of events.
+  int32_t tslots = 0;
+  std::vector<cudaEvent_t> tev;        // [2 * tslots]: begin, end per slot
+  cudaGraphNode_t tnode[2] = {nullptr, nullptr};
+  long long tlaunched = 0, tharvested = 0, tcount = 0;
+  double tsum_ms = 0.0;
 
   void release() {
     if (exec) cudaGraphExecDestroy(exec);
@@ -1705,6 +1712,10 @@ struct EaState {
       if (e) cudaEventDestroy(e);
       e = nullptr;
     }
+    for (cudaEvent_t& e : tev)
+      if (e) cudaEventDestroy(e);
+    tev.clear();
+    tslots = 0;
     if (side) cudaStreamDestroy(side);
     side = nullptr;
     for (DevBuf* b : {&seq, &len, &inc, &dec, &fit, &lnf, &tkey, &tref, &rec, &list_ref,
@@ -1796,7 +1807,9 @@ static void launch_rank(const EaState* st, cudaStream_t s) {
 static ebic_status launch_generation(ebic_ctx* h, EaState* st, cudaStream_t s) {
   const EaDev& d = st->dev;
   cudaStream_t s2 = st->side;
+  if (st->tslots) EBIC_CUDA_TRY(cudaEventRecordWithFlags(st->tev[0], s, cudaEventRecordExternal));
   k_build<false><<<1, kBuildThreads, st->smem_build, s>>>(d, st->hmask, st->kB);
+  if (st->tslots) EBIC_CUDA_TRY(cudaEventRecordWithFlags(st->tev[1], s, cudaEventRecordExternal));
   EBIC_CUDA_TRY(cudaEventRecord(st->fork_ev[0], s));
   EBIC_CUDA_TRY(cudaStreamWaitEvent(s2, st->fork_ev[0], 0));
   k_tabu_insert<<<(unsigned)((st->p.pop_size + 255) / 256), 256, 0, s2>>>(d);
@@ -2044,6 +2057,11 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
   st->tuning = h->tuning;
   EBIC_CUDA_TRY(cudaStreamCreateWithFlags(&st->side, cudaStreamNonBlocking));
   for (cudaEvent_t& e : st->fork_ev) EBIC_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  if (h->ktime_slots > 0) {
+    st->tev.assign(2 * (size_t)h->ktime_slots, nullptr);
+    st->tslots = h->ktime_slots;
+    for (cudaEvent_t& e : st->tev) EBIC_CUDA_TRY(cudaEventCreate(&e));
+  }
   EBIC_CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   ebic_status cap_st = launch_generation(h, st, s);
   cudaGraph_t graph = nullptr;
@@ -2055,9 +2073,54 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
   }
   EBIC_CUDA_TRY(ce);
   st->graph = graph;
+  if (st->tslots) {
+    size_t n = 0;
+    EBIC_CUDA_TRY(cudaGraphGetNodes(graph, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    EBIC_CUDA_TRY(cudaGraphGetNodes(graph, nodes.data(), &n));
+    for (cudaGraphNode_t nd : nodes) {
+      cudaGraphNodeType t;
+      EBIC_CUDA_TRY(cudaGraphNodeGetType(nd, &t));
+      if (t != cudaGraphNodeTypeEventRecord) continue;
+      cudaEvent_t e = nullptr;
+      EBIC_CUDA_TRY(cudaGraphEventRecordNodeGetEvent(nd, &e));
+      for (int j = 0; j < 2; ++j)
+        if (e == st->tev[j]) st->tnode[j] = nd;
+    }
+    if (!st->tnode[0] || !st->tnode[1])
+      return fail(EBIC_ERR_DEVICE, "the captured generation has no timing nodes");
+  }
   EBIC_CUDA_TRY(cudaGraphInstantiate(&st->exec, graph, 0));
   EBIC_CUDA_TRY(cudaStreamSynchronize(s));
   st->initialised = true;
+  return EBIC_OK;
+}
+
+// Adds the k_build time of timing slot `slot` to the running sum (waits for
+// that replay to finish).
+static ebic_status harvest_timing(EaState* st, long long slot) {
+  cudaEvent_t a = st->tev[2 * (size_t)(slot % st->tslots)];
+  cudaEvent_t b = st->tev[2 * (size_t)(slot % st->tslots) + 1];
+  EBIC_CUDA_TRY(cudaEventSynchronize(b));
+  float ms = 0.f;
+  EBIC_CUDA_TRY(cudaEventElapsedTime(&ms, a, b));
+  st->tsum_ms += ms;
+  st->tcount += 1;
+  return EBIC_OK;
+}
+
+// One replay of the generation graph; with in-graph timing on, its two event
+// nodes first move to the next slot of the ring (harvesting the replay that
+// used the slot before).
+static ebic_status graph_launch(EaState* st, cudaStream_t s) {
+  if (st->tslots) {
+    if (st->tlaunched - st->tharvested >= st->tslots) EBIC_TRY(harvest_timing(st, st->tharvested++));
+    const size_t k = 2 * (size_t)(st->tlaunched % st->tslots);
+    EBIC_CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(st->exec, st->tnode[0], st->tev[k]));
+    EBIC_CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(st->exec, st->tnode[1], st->tev[k + 1]));
+    st->tlaunched += 1;
+  }
+  EBIC_CUDA_TRY(cudaGraphLaunch(st->exec, s));
   return EBIC_OK;
 }
 
@@ -2074,7 +2137,7 @@ static ebic_status run_step(ebic_ctx* h, int32_t generations, ebic_stats_t* stat
   int32_t left = c.stop ? 0 : generations;
   while (left > 0) {
     const int32_t chunk = std::min<int32_t>(left, 64);
-    for (int32_t i = 0; i < chunk; ++i) EBIC_CUDA_TRY(cudaGraphLaunch(st->exec, s));
+    for (int32_t i = 0; i < chunk; ++i) EBIC_TRY(graph_launch(st, s));
     count_launches((uint64_t)chunk * st->launches_per_gen);
     left -= chunk;
     EBIC_TRY(read_ctl(st, s, &c));
@@ -2125,7 +2188,7 @@ static ebic_status run_step_async(ebic_ctx* h, int32_t generations, cudaStream_t
   EaState* st = h->ea;
   if (!st || !st->initialised) return fail(EBIC_ERR_STATE, "ebic_run_init has not run");
   if (generations < 0) return fail(EBIC_ERR_ARG, "negative generation count");
-  for (int32_t i = 0; i < generations; ++i) EBIC_CUDA_TRY(cudaGraphLaunch(st->exec, s));
+  for (int32_t i = 0; i < generations; ++i) EBIC_TRY(graph_launch(st, s));
   count_launches((uint64_t)generations * st->launches_per_gen);
   return EBIC_OK;
 }
@@ -2134,10 +2197,9 @@ static ebic_status run_step_async(ebic_ctx* h, int32_t generations, cudaStream_t
 // One generation as separate launches with events between them, in the
 // order of the graph's dependencies: Step 3, tabu insertion, evaluation,
 // Step 5, then the next generation's attempt records (reported first).
-static ebic_status run_step_profiled(ebic_ctx* h, float* us) {
+static ebic_status run_step_profiled(ebic_ctx* h, float* us, cudaStream_t s) {
   EaState* st = h->ea;
   if (!st || !st->initialised) return fail(EBIC_ERR_STATE, "ebic_run_init has not run");
-  const cudaStream_t s = h->stream;
   cudaEvent_t ev[6];
   for (int i = 0; i < 6; ++i) EBIC_CUDA_TRY(cudaEventCreate(&ev[i]));
   const EaDev& d = st->dev;
@@ -2268,7 +2330,29 @@ ebic_status ebic_run_step_async(ebic_handle h, int32_t generations, void* stream
 
 ebic_status ebic_run_step_profiled(ebic_handle h, float* kernel_us) {
   if (!h) return fail(EBIC_ERR_ARG, "null handle");
-  return run_step_profiled(h, kernel_us);
+  return run_step_profiled(h, kernel_us, h->stream);
+}
+
+ebic_status ebic_set_kernel_timing(ebic_handle h, int32_t slots) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  if (slots < 0 || slots > (1 << 20)) return fail(EBIC_ERR_ARG, "timing slots %d outside [0, 2^20]", slots);
+  h->ktime_slots = slots;
+  return EBIC_OK;
+}
+
+ebic_status ebic_read_kernel_timing(ebic_handle h, int32_t reset, double* mean_us, long long* count) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  EaState* st = h->ea;
+  if (!st || !st->initialised) return fail(EBIC_ERR_STATE, "ebic_run_init has not run");
+  if (!st->tslots) return fail(EBIC_ERR_STATE, "the run was started without kernel timing");
+  while (st->tharvested < st->tlaunched) EBIC_TRY(harvest_timing(st, st->tharvested++));
+  if (mean_us) *mean_us = st->tcount ? 1e3 * st->tsum_ms / (double)st->tcount : 0.0;
+  if (count) *count = st->tcount;
+  if (reset) {
+    st->tsum_ms = 0.0;
+    st->tcount = 0;
+  }
+  return EBIC_OK;
 }
 
 ebic_status ebic_run_screen(ebic_handle h, ebic_surrogate s, int32_t oversample, int32_t mode) {

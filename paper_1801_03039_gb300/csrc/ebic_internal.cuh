@@ -80,6 +80,7 @@ struct ebic_ctx {
   ebic_surrogate_ctx* screen_sur = nullptr;
   int32_t screen_v = 1;
   int32_t screen_mode = 0;
+  int32_t ktime_slots = 0;        // in-graph timing of Step 3's builder (0: off)
 };
 
 namespace ebic {

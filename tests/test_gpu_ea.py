@@ -147,6 +147,35 @@ def test_one_call_run_generations_equals_stepping():
     assert_bits_equal(fit, ref["toprank_f"], "toprank fitness")
 
 
+def test_in_graph_kernel_timing_leaves_the_run_unchanged():
+    """Event nodes around k_build in the replayed graph: the run is the
+    oracle's, every replay is timed, and a ring of three event pairs wraps."""
+    prob = synth.matrix_tiny(seed=3)
+    kw = {**BASE, "iterations": 12, "seed": 7}
+    ref = oracle.run(prob.A, **kw)
+    h = eb.ebic_load_matrix(prob.A)
+    try:
+        with pytest.raises(eb.EbicError):
+            eb.ebic_set_kernel_timing(h, -1)
+        eb.ebic_run_init(h, _device_params(kw))
+        with pytest.raises(eb.EbicError):               # started without timing
+            eb.ebic_read_kernel_timing(h)
+        eb.ebic_set_kernel_timing(h, 3)
+        eb.ebic_run_init(h, _device_params(kw))
+        eb.ebic_run_step(h, 5)
+        us, n = eb.ebic_read_kernel_timing(h, reset=True)
+        assert n == 5 and 0 < us < 1e5
+        eb.ebic_run_step(h, 7)
+        us, n = eb.ebic_read_kernel_timing(h)
+        assert n == 7 and 0 < us < 1e5
+        top, fit, _ = eb.ebic_get_toprank(h, kw["toprank_size"], kw["len_max"])
+        st = eb.ebic_run_step(h, 0)
+    finally:
+        eb.ebic_free(h)
+    assert top == ref["toprank"] and st["generations_done"] == 12
+    assert_bits_equal(fit, ref["toprank_f"], "toprank fitness")
+
+
 def test_state_errors():
     prob = synth.matrix_tiny(seed=0)
     h = eb.ebic_load_matrix(prob.A)
