@@ -637,6 +637,11 @@ __device__ __forceinline__ void hs8(const uint32_t (&v)[8], uint32_t& ones, uint
 // Named barrier 1 over the builder's CTA: warp 0 and the helper warps meet
 // there twice per batch (job posted, shares done) and once per chunk (release).
 constexpr int kBuildThreads = 128;
+// Step 3 fast path: a bit filter over the keys of the generation's committed
+// children (one bit per key, chosen by the key's high 32 bits) in front of a
+// dense list of those keys; a clear bit proves a child new.
+constexpr int kFilterBits = 1 << 17;
+constexpr int kFilterWords = kFilterBits / 32;
 __device__ __forceinline__ void bar_team() {
   asm volatile("bar.sync 1, %0;" ::"n"(kBuildThreads) : "memory");
 }
@@ -727,21 +732,24 @@ __device__ __forceinline__ bool same_cols(const uint16_t* a, const uint16_t* b, 
 // iteration).  Lane 0 is final after the first pass and lane k after pass k,
 // so the iteration stops after at most 32 passes, at the unique fixpoint: the
 // outcomes of taking the attempts one by one.  Then duplicates are found in
-// parallel (the record's tabu flag, a probe of this generation's hash set,
-// equal keys among earlier lanes of the batch), and the batch is committed up
+// parallel (the record's tabu flag; the filter bit of the key and, where it
+// is set, a warp-wide scan of the generation's committed keys; equal keys
+// among earlier lanes of the batch), and the batch is committed up
 // to the first duplicate, which counts as a hit; the next batch starts after
 // it, from penalty counts that include every acceptance so far.
 template <int K, int NW>
 __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, const char* cur,
                                             int cnt, int j0, uint32_t* pen, const float* cLf,
-                                            unsigned long long* hkey, int32_t* href,
+                                            unsigned long long* lkey, int32_t* lref,
+                                            uint32_t* fbits, int E,
                                             int* s_dec, uint4* s_cw, Team* tm, long long base,
-                                            int hmask, int RB,
+                                            int RB,
                                             int lane, int& n, int& hits, int& stopped,
                                             long long& attempts, long long& exact) {
   constexpr int NE = 2 * K, NC = K * K, NV = NW / 4;
   const int S = d.S;
   const unsigned FULL = 0xffffffffu;
+  long long ex_lane = 0;                 // exact tournaments of this lane's attempts
   int sb = 0;
   while (sb < cnt && n < d.P && !stopped) {
     const int avail = min(32, cnt - sb);
@@ -770,15 +778,28 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
           const uint4* eb = reinterpret_cast<const uint4*>(ra + l.ebit) + e * NV;
 #pragma unroll
           for (int v = 0; v < NV; ++v) bits[e][v] = eb[v];
-          const uint16_t* cs = reinterpret_cast<const uint16_t*>(ra + l.ecols) + (size_t)e * S;
-          uint32_t s0 = 0, s1 = 0;
-          int c = 0;
-          for (; c + 2 <= Lx[e]; c += 2) {
-            s0 += pen[cs[c]];
-            s1 += pen[cs[c + 1]];
-          }
-          if (c < Lx[e]) s0 += pen[cs[c]];
-          Sx[e] = (int32_t)(s0 + s1);
+        }
+      }
+      // penalty sums of the entrants, eight columns of each entrant per
+      // round: every column index and penalty load of a round is issued
+      // before any of them is used
+      {
+        const uint16_t* ecols = reinterpret_cast<const uint16_t*>(ra + l.ecols);
+        int lmax = 0;
+#pragma unroll
+        for (int e = 0; e < NE; ++e) lmax = max(lmax, Lx[e]);
+        for (int c0 = 0; c0 < lmax; c0 += 8) {
+          uint32_t col[NE][8];
+#pragma unroll
+          for (int e = 0; e < NE; ++e)
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              col[e][i] = c0 + i < Lx[e] ? ecols[(size_t)e * S + c0 + i] : 0u;
+#pragma unroll
+          for (int e = 0; e < NE; ++e)
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              if (c0 + i < Lx[e]) Sx[e] += (int32_t)pen[col[e][i]];
         }
       }
       pc[0] = pair_const(ln[1], ln[0], cl[1], cl[0], id[1], id[0], Sx[1], Sx[0], Lx[1], Lx[0]);
@@ -883,35 +904,41 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
           }
         }
       }
-      // duplicates: tabu flag, this generation's hash set (which holds every
-      // child committed so far), equal keys among unsettled earlier lanes
+      // duplicates: tabu flag, this generation's committed children (filter,
+      // then the key list), equal keys among unsettled earlier lanes
       const bool live = have && lane >= first;
       const unsigned long long key =
           have ? reinterpret_cast<const unsigned long long*>(ra + l.chash)[dec] : 0ull;
       const int L = have ? reinterpret_cast<const int32_t*>(ra + l.cL)[dec] : 0;
       const uint16_t* child = reinterpret_cast<const uint16_t*>(ra + l.ccols) + (size_t)dec * S;
       bool dup = live && reinterpret_cast<const int32_t*>(ra + l.ctabu)[dec] != 0;
-      if (live && !dup) {
-        int sl = (int)(key & (unsigned long long)hmask);
-        for (int probe = 0; probe <= hmask; ++probe) {
-          const unsigned long long kk = hkey[sl];
-          if (kk == 0ull) break;
-          if (kk == key) {
-            const int32_t r = href[sl];
-            const char* orec = d.rec + (size_t)(r / NC) * RB;
-            const int oc = r % NC;
-            if (reinterpret_cast<const int32_t*>(orec + l.cL)[oc] == L &&
-                same_cols(reinterpret_cast<const uint16_t*>(orec + l.ccols) + (size_t)oc * S,
-                          child, L)) {
-              dup = true;
-              break;
-            }
-          }
-          sl = (sl + 1) & hmask;
-        }
-      }
+      const uint32_t fb = (uint32_t)(key >> 32) & (uint32_t)(kFilterBits - 1);
+      const bool maybe = live && !dup && ((fbits[fb >> 5] >> (fb & 31)) & 1u);
       s_dec[lane] = dec;
       __syncwarp();
+      unsigned mm = __ballot_sync(FULL, maybe);
+      while (mm) {
+        // the whole warp scans the committed keys for lane b's child
+        const int b = __ffs(mm) - 1;
+        mm &= mm - 1;
+        const unsigned long long kb = __shfl_sync(FULL, key, b);
+        const int Lb = __shfl_sync(FULL, L, b);
+        const uint16_t* cb = reinterpret_cast<const uint16_t*>(cur + (size_t)(sb + b) * RB + l.ccols) +
+                             (size_t)s_dec[b] * S;
+        bool found = false;
+        for (int i = lane; i < n - E; i += 32) {
+          if (lkey[i] == kb) {
+            const int32_t r = lref[i];
+            const char* orec = d.rec + (size_t)(r / NC) * RB;
+            const int oc = r % NC;
+            if (reinterpret_cast<const int32_t*>(orec + l.cL)[oc] == Lb &&
+                same_cols(reinterpret_cast<const uint16_t*>(orec + l.ccols) + (size_t)oc * S, cb,
+                          Lb))
+              found = true;
+          }
+        }
+        if (__any_sync(FULL, found) && lane == b) dup = true;
+      }
       unsigned twins = __match_any_sync(FULL, key) & ((1u << lane) - 1u) & ~((1u << first) - 1u);
       if (!live) twins = 0u;
       while (twins && !dup) {
@@ -933,27 +960,27 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
       const int processed = nacc + (hit ? 1 : 0);
       const int k = lane - first;
       if (k >= 0 && k < nacc) {
-        const int32_t rec_id = (int32_t)((j0 + sb + lane) * NC + dec);
-        int sl = (int)(key & (unsigned long long)hmask);
-        for (int probe = 0; probe <= hmask; ++probe) {
-          if (atomicCAS(&hkey[sl], 0ull, key) == 0ull) {
-            href[sl] = rec_id;
-            break;
-          }
-          sl = (sl + 1) & hmask;
-        }
+        lkey[n - E + k] = key;
+        lref[n - E + k] = (int32_t)((j0 + sb + lane) * NC + dec);
+        atomicOr(&fbits[fb >> 5], 1u << (fb & 31));
         uint16_t* dst = d.seq + (size_t)(base + n + k) * S;
-        for (int c = 0; c < L; ++c) {
-          const uint16_t v = child[c];
-          dst[c] = v;
-          atomicAdd(&pen[v], 1u);
+        // eight columns per round, loads issued before the stores and the
+        // penalty increments that use them
+        for (int c0 = 0; c0 < L; c0 += 8) {
+          uint32_t v[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) v[i] = c0 + i < L ? child[c0 + i] : 0u;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            if (c0 + i < L) {
+              dst[c0 + i] = (uint16_t)v[i];
+              atomicAdd(&pen[v[i]], 1u);
+            }
+          }
         }
         d.len[base + n + k] = L;
       }
-      int ex = (k >= 0 && k < processed) ? nex : 0;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) ex += __shfl_xor_sync(FULL, ex, o);
-      exact += ex;
+      if (k >= 0 && k < processed) ex_lane += nex;
       attempts += processed;
       n += nacc;
       if (hit && ++hits > d.P) stopped = 1;
@@ -979,6 +1006,9 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
       __syncwarp();
     }
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) ex_lane += __shfl_xor_sync(FULL, ex_lane, o);
+  exact += ex_lane;
 }
 
 // ---------------------------------------------------------------------------
@@ -993,7 +1023,11 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
 // (at acceptance, or once per 32 attempts in the fast path).
 //
 // Shared memory: hkey[H] (u64) | href[H] | pen[C] | cLf[Lmax + 1] |
+//                fbits[kFilterWords] (16-byte aligned) |
 //                2 record buffers of kB records (128-byte aligned).
+// hkey / href are the generation's hash set of committed children in the
+// general path; the fast path keeps them as a dense list (key, record) in
+// commit order behind the bit filter fbits.
 // ---------------------------------------------------------------------------
 template <bool INIT>
 __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int kB) {
@@ -1009,10 +1043,12 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
   int32_t* href = reinterpret_cast<int32_t*>(hkey + H);
   uint32_t* pen = reinterpret_cast<uint32_t*>(href + H);
   float* cLf = reinterpret_cast<float*>(pen + d.C);
-  // 128-byte aligned by an offset from the shared base (integer round trips
-  // through uintptr_t would lose the shared address space)
+  // aligned by offsets from the shared base (integer round trips through
+  // uintptr_t would lose the shared address space)
   char* const sbase = reinterpret_cast<char*>(smem_u64);
-  char* buf0 = sbase + ((reinterpret_cast<char*>(cLf + d.Lmax + 1) - sbase + 127) & ~(ptrdiff_t)127);
+  uint32_t* fbits = reinterpret_cast<uint32_t*>(
+      sbase + ((reinterpret_cast<char*>(cLf + d.Lmax + 1) - sbase + 15) & ~(ptrdiff_t)15));
+  char* buf0 = sbase + ((reinterpret_cast<char*>(fbits + kFilterWords) - sbase + 127) & ~(ptrdiff_t)127);
   // record buffer i at buf0 + i * kB * RB (computed, not looked up, so that the
   // compiler keeps the shared-memory address space of every record access)
   const size_t buf_bytes = (size_t)kB * RB;
@@ -1043,6 +1079,9 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
     }
   }
   for (int i = tid; i < H; i += kBuildThreads) hkey[i] = 0ull;
+  if (!INIT && fast)
+    for (int i = tid; i < kFilterWords / 4; i += kBuildThreads)
+      reinterpret_cast<uint4*>(fbits)[i] = make_uint4(0u, 0u, 0u, 0u);
   for (int i = tid; i < d.C; i += kBuildThreads) pen[i] = 0u;
   for (int i = tid; i <= d.Lmax; i += kBuildThreads) cLf[i] = d.c_over_L[i];
   const long long base = (long long)g * d.P;
@@ -1083,21 +1122,21 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
       } else if (!INIT && fast) {
         if (k == 2) {
           if (l.nw == 4)
-            build_batch<2, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, &s_team,
-                              base, hmask, RB,
+            build_batch<2, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, fbits, E, s_dec,
+                              s_cw, &s_team, base, RB,
                              lane, n, hits, stopped, attempts, exact);
           else
-            build_batch<2, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, &s_team,
-                              base, hmask, RB,
+            build_batch<2, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, fbits, E, s_dec,
+                              s_cw, &s_team, base, RB,
                              lane, n, hits, stopped, attempts, exact);
         } else {
           if (l.nw == 4)
-            build_batch<1, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, &s_team,
-                              base, hmask, RB,
+            build_batch<1, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, fbits, E, s_dec,
+                              s_cw, &s_team, base, RB,
                              lane, n, hits, stopped, attempts, exact);
           else
-            build_batch<1, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, s_dec, s_cw, &s_team,
-                              base, hmask, RB,
+            build_batch<1, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, fbits, E, s_dec,
+                              s_cw, &s_team, base, RB,
                              lane, n, hits, stopped, attempts, exact);
         }
       } else {
@@ -1984,10 +2023,11 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
   a.fit = d.fit;
   a.lnf = d.lnf;
 
-  // build: wset + accepted + pen + cL, then two record buffers of kB attempts
+  // build: hash set / key list + pen + cL + filter, then two record buffers of kB attempts
   const size_t fixed = (size_t)H * (sizeof(unsigned long long) + sizeof(int32_t)) +
                        (size_t)h->C * sizeof(uint32_t) +
-                       (size_t)(p->len_max + 2) * sizeof(float) + 128;
+                       (size_t)(p->len_max + 2) * sizeof(float) + 16 +
+                       (size_t)kFilterWords * sizeof(uint32_t) + 128;
   st->kB = 64;
   while (st->kB > 2 && fixed + 2 * (size_t)st->kB * st->rec_bytes > 200 * 1024) st->kB >>= 1;
   st->smem_build = fixed + 2 * (size_t)st->kB * st->rec_bytes;
