@@ -718,6 +718,25 @@ __device__ __forceinline__ bool same_cols(const uint16_t* a, const uint16_t* b, 
   return true;
 }
 
+// The same test with sixteen columns of both series loaded before any is
+// compared (for a series in global memory, one round trip per sixteen).
+__device__ __forceinline__ bool same_cols_wide(const uint16_t* a, const uint16_t* b, int L) {
+  bool eq = true;
+  for (int c0 = 0; c0 < L && eq; c0 += 16) {
+    uint32_t x[16], y[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      x[i] = c0 + i < L ? a[c0 + i] : 0u;
+      y[i] = c0 + i < L ? b[c0 + i] : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < 16; ++i) eq = eq && x[i] == y[i];
+  }
+  return eq;
+}
+
+constexpr int kTwinSlots = 4096;    // lane-id scratch of the twin pre-check
+
 // The Step 3 consumer for tournaments of K <= 2 entrants and NW-word column
 // bitsets, run by one warp on one chunk of records in shared memory, 32
 // attempts (one per lane) at a time.
@@ -741,7 +760,7 @@ template <int K, int NW>
 __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, const char* cur,
                                             int cnt, int j0, uint32_t* pen, const float* cLf,
                                             unsigned long long* lkey, int32_t* lref,
-                                            uint32_t* fbits, int E,
+                                            uint32_t* fbits, int E, uint8_t* s_twin,
                                             int* s_dec, uint4* s_cw, Team* tm, long long base,
                                             int RB,
                                             int lane, int& n, int& hits, int& stopped,
@@ -926,21 +945,32 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
         const uint16_t* cb = reinterpret_cast<const uint16_t*>(cur + (size_t)(sb + b) * RB + l.ccols) +
                              (size_t)s_dec[b] * S;
         bool found = false;
+#pragma unroll 4
         for (int i = lane; i < n - E; i += 32) {
           if (lkey[i] == kb) {
             const int32_t r = lref[i];
             const char* orec = d.rec + (size_t)(r / NC) * RB;
             const int oc = r % NC;
             if (reinterpret_cast<const int32_t*>(orec + l.cL)[oc] == Lb &&
-                same_cols(reinterpret_cast<const uint16_t*>(orec + l.ccols) + (size_t)oc * S, cb,
-                          Lb))
+                same_cols_wide(reinterpret_cast<const uint16_t*>(orec + l.ccols) + (size_t)oc * S,
+                               cb, Lb))
               found = true;
           }
         }
         if (__any_sync(FULL, found) && lane == b) dup = true;
       }
-      unsigned twins = __match_any_sync(FULL, key) & ((1u << lane) - 1u) & ~((1u << first) - 1u);
-      if (!live) twins = 0u;
+      // equal keys among unsettled earlier lanes: each live lane writes its
+      // id into a slot chosen by its key; only when some lane finds another
+      // lane's id in its slot does the warp match the keys exactly
+      const uint32_t ts = (uint32_t)key & (uint32_t)(kTwinSlots - 1);
+      if (live) s_twin[ts] = (uint8_t)lane;
+      __syncwarp();
+      const bool clash = live && s_twin[ts] != (uint8_t)lane;
+      unsigned twins = 0u;
+      if (__any_sync(FULL, clash)) {
+        twins = __match_any_sync(FULL, key) & ((1u << lane) - 1u) & ~((1u << first) - 1u);
+        if (!live) twins = 0u;
+      }
       while (twins && !dup) {
         const int b = __ffs(twins) - 1;
         twins &= twins - 1;
@@ -1055,6 +1085,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
   __shared__ __align__(8) unsigned long long bars[2];
   __shared__ int s_n, s_done, s_E, s_fail;
   __shared__ int s_dec[32];              // outcomes of the batch's lanes (fast path)
+  __shared__ uint8_t s_twin[kTwinSlots];  // lane ids by key (fast path twin pre-check)
   __shared__ uint4 s_cw[32 * 2];         // their children's bitsets (fast path)
   __shared__ Team s_team;                // the fast path's helper-warp protocol
   // fast path: tournaments of at most 2 entrants, column sets of at most 256 bits
@@ -1122,21 +1153,21 @@ __global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int
       } else if (!INIT && fast) {
         if (k == 2) {
           if (l.nw == 4)
-            build_batch<2, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, fbits, E, s_dec,
-                              s_cw, &s_team, base, RB,
+            build_batch<2, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, fbits, E, s_twin,
+                              s_dec, s_cw, &s_team, base, RB,
                              lane, n, hits, stopped, attempts, exact);
           else
-            build_batch<2, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, fbits, E, s_dec,
-                              s_cw, &s_team, base, RB,
+            build_batch<2, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, fbits, E, s_twin,
+                              s_dec, s_cw, &s_team, base, RB,
                              lane, n, hits, stopped, attempts, exact);
         } else {
           if (l.nw == 4)
-            build_batch<1, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, fbits, E, s_dec,
-                              s_cw, &s_team, base, RB,
+            build_batch<1, 4>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, fbits, E, s_twin,
+                              s_dec, s_cw, &s_team, base, RB,
                              lane, n, hits, stopped, attempts, exact);
           else
-            build_batch<1, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, fbits, E, s_dec,
-                              s_cw, &s_team, base, RB,
+            build_batch<1, 8>(d, l, cur, cnt, chunk * kB, pen, cLf, hkey, href, fbits, E, s_twin,
+                              s_dec, s_cw, &s_team, base, RB,
                              lane, n, hits, stopped, attempts, exact);
         }
       } else {
