@@ -883,7 +883,13 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
     // lanes below `first` are settled (committed, or excluded as hits)
     int first = 0;
     bool done_batch = false;
+    // duplicate flags of the lanes' current children; they stay exact for a
+    // round that changes no child (after a hit, a child equal to the hit's or
+    // to a child committed with it was already flagged as equal to an
+    // earlier lane's)
+    bool dup = false, dups_valid = false;
     while (!done_batch) {
+      bool round_changed = false;
       if (K == 2) {
         // Jacobi passes until no outcome changes (at most 32 passes)
         for (int pass = 0; pass < 33; ++pass) {
@@ -891,6 +897,7 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
           const int nd = decide(&nx);
           unsigned changed = __ballot_sync(FULL, have && lane >= first && nd != dec);
           if (!changed) break;
+          round_changed = true;
           uint4 nw[NV];
           const uint4* nb = reinterpret_cast<const uint4*>(ra + l.cbit) + nd * NV;
 #pragma unroll
@@ -930,57 +937,62 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
           have ? reinterpret_cast<const unsigned long long*>(ra + l.chash)[dec] : 0ull;
       const int L = have ? reinterpret_cast<const int32_t*>(ra + l.cL)[dec] : 0;
       const uint16_t* child = reinterpret_cast<const uint16_t*>(ra + l.ccols) + (size_t)dec * S;
-      bool dup = live && reinterpret_cast<const int32_t*>(ra + l.ctabu)[dec] != 0;
       const uint32_t fb = (uint32_t)(key >> 32) & (uint32_t)(kFilterBits - 1);
-      const bool maybe = live && !dup && ((fbits[fb >> 5] >> (fb & 31)) & 1u);
-      s_dec[lane] = dec;
-      __syncwarp();
-      unsigned mm = __ballot_sync(FULL, maybe);
-      while (mm) {
-        // the whole warp scans the committed keys for lane b's child
-        const int b = __ffs(mm) - 1;
-        mm &= mm - 1;
-        const unsigned long long kb = __shfl_sync(FULL, key, b);
-        const int Lb = __shfl_sync(FULL, L, b);
-        const uint16_t* cb = reinterpret_cast<const uint16_t*>(cur + (size_t)(sb + b) * RB + l.ccols) +
-                             (size_t)s_dec[b] * S;
-        bool found = false;
-#pragma unroll 4
-        for (int i = lane; i < n - E; i += 32) {
-          if (lkey[i] == kb) {
-            const int32_t r = lref[i];
-            const char* orec = d.rec + (size_t)(r / NC) * RB;
-            const int oc = r % NC;
-            if (reinterpret_cast<const int32_t*>(orec + l.cL)[oc] == Lb &&
-                same_cols_wide(reinterpret_cast<const uint16_t*>(orec + l.ccols) + (size_t)oc * S,
-                               cb, Lb))
-              found = true;
+      if (dups_valid && !round_changed) {
+        dup = dup && live;
+      } else {
+        dups_valid = true;
+        dup = live && reinterpret_cast<const int32_t*>(ra + l.ctabu)[dec] != 0;
+        const bool maybe = live && !dup && ((fbits[fb >> 5] >> (fb & 31)) & 1u);
+        s_dec[lane] = dec;
+        __syncwarp();
+        unsigned mm = __ballot_sync(FULL, maybe);
+        while (mm) {
+          // the whole warp scans the committed keys for lane b's child
+          const int b = __ffs(mm) - 1;
+          mm &= mm - 1;
+          const unsigned long long kb = __shfl_sync(FULL, key, b);
+          const int Lb = __shfl_sync(FULL, L, b);
+          const uint16_t* cb = reinterpret_cast<const uint16_t*>(cur + (size_t)(sb + b) * RB + l.ccols) +
+                               (size_t)s_dec[b] * S;
+          bool found = false;
+  #pragma unroll 4
+          for (int i = lane; i < n - E; i += 32) {
+            if (lkey[i] == kb) {
+              const int32_t r = lref[i];
+              const char* orec = d.rec + (size_t)(r / NC) * RB;
+              const int oc = r % NC;
+              if (reinterpret_cast<const int32_t*>(orec + l.cL)[oc] == Lb &&
+                  same_cols_wide(reinterpret_cast<const uint16_t*>(orec + l.ccols) + (size_t)oc * S,
+                                 cb, Lb))
+                found = true;
+            }
           }
+          if (__any_sync(FULL, found) && lane == b) dup = true;
         }
-        if (__any_sync(FULL, found) && lane == b) dup = true;
+        // equal keys among unsettled earlier lanes: each live lane writes its
+        // id into a slot chosen by its key; only when some lane finds another
+        // lane's id in its slot does the warp match the keys exactly
+        const uint32_t ts = (uint32_t)key & (uint32_t)(kTwinSlots - 1);
+        if (live) s_twin[ts] = (uint8_t)lane;
+        __syncwarp();
+        const bool clash = live && s_twin[ts] != (uint8_t)lane;
+        unsigned twins = 0u;
+        if (__any_sync(FULL, clash)) {
+          twins = __match_any_sync(FULL, key) & ((1u << lane) - 1u) & ~((1u << first) - 1u);
+          if (!live) twins = 0u;
+        }
+        while (twins && !dup) {
+          const int b = __ffs(twins) - 1;
+          twins &= twins - 1;
+          const char* rbb = cur + (size_t)(sb + b) * RB;
+          const int db = s_dec[b];
+          if (reinterpret_cast<const int32_t*>(rbb + l.cL)[db] == L &&
+              same_cols(reinterpret_cast<const uint16_t*>(rbb + l.ccols) + (size_t)db * S, child, L))
+            dup = true;
+        }
+        __syncwarp();
       }
-      // equal keys among unsettled earlier lanes: each live lane writes its
-      // id into a slot chosen by its key; only when some lane finds another
-      // lane's id in its slot does the warp match the keys exactly
-      const uint32_t ts = (uint32_t)key & (uint32_t)(kTwinSlots - 1);
-      if (live) s_twin[ts] = (uint8_t)lane;
-      __syncwarp();
-      const bool clash = live && s_twin[ts] != (uint8_t)lane;
-      unsigned twins = 0u;
-      if (__any_sync(FULL, clash)) {
-        twins = __match_any_sync(FULL, key) & ((1u << lane) - 1u) & ~((1u << first) - 1u);
-        if (!live) twins = 0u;
-      }
-      while (twins && !dup) {
-        const int b = __ffs(twins) - 1;
-        twins &= twins - 1;
-        const char* rbb = cur + (size_t)(sb + b) * RB;
-        const int db = s_dec[b];
-        if (reinterpret_cast<const int32_t*>(rbb + l.cL)[db] == L &&
-            same_cols(reinterpret_cast<const uint16_t*>(rbb + l.ccols) + (size_t)db * S, child, L))
-          dup = true;
-      }
-      __syncwarp();
       // commit lanes first .. first_dup - 1, as far as the population needs
       const unsigned dupmask = __ballot_sync(FULL, dup);
       const int first_dup = dupmask ? __ffs(dupmask) - 1 : avail;
