@@ -753,9 +753,12 @@ constexpr int kTwinSlots = 4096;    // lane-id scratch of the twin pre-check
 // outcomes of taking the attempts one by one.  Then duplicates are found in
 // parallel (the record's tabu flag; the filter bit of the key and, where it
 // is set, a warp-wide scan of the generation's committed keys; equal keys
-// among earlier lanes of the batch), and the batch is committed up
-// to the first duplicate, which counts as a hit; the next batch starts after
-// it, from penalty counts that include every acceptance so far.
+// among earlier lanes of the batch).  The first duplicate is a hit: its child
+// leaves the later lanes' sums, which are re-decided (and, if a child
+// changed, re-checked) in the next round.  Once no hit remains (or the
+// population is full, or the tabu rule stops the run) the accepted lanes are
+// committed together, and the next batch starts from penalty counts that
+// include every acceptance so far.
 template <int K, int NW>
 __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, const char* cur,
                                             int cnt, int j0, uint32_t* pen, const float* cLf,
@@ -880,8 +883,13 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
 #pragma unroll
       for (int e = 1; e < NE; ++e) Sx[e] += tm->ov[4 * lane + e];
     }
-    // lanes below `first` are settled (committed, or excluded as hits)
+    // Lanes below `first` are settled: accepted (committed together at the
+    // end of the batch) or hits.  A round finds the next hit; the hit's child
+    // leaves the later lanes' sums and the next round re-decides them.
     int first = 0;
+    unsigned hitmask = 0u;              // settled hits
+    int acc = 0;                        // settled accepted lanes
+    int cut = avail;                    // lanes processed by the batch
     bool done_batch = false;
     // duplicate flags of the lanes' current children; they stay exact for a
     // round that changes no child (after a hit, a child equal to the hit's or
@@ -970,16 +978,19 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
           }
           if (__any_sync(FULL, found) && lane == b) dup = true;
         }
-        // equal keys among unsettled earlier lanes: each live lane writes its
-        // id into a slot chosen by its key; only when some lane finds another
-        // lane's id in its slot does the warp match the keys exactly
+        // equal keys among earlier lanes of the batch (settled ones too: an
+        // accepted lane is not in the key list before the batch commits, and
+        // a child equal to a hit's is a duplicate of what the hit duplicated):
+        // each lane writes its id into a slot chosen by its key; only when
+        // some lane finds another lane's id in its slot does the warp match
+        // the keys exactly
         const uint32_t ts = (uint32_t)key & (uint32_t)(kTwinSlots - 1);
-        if (live) s_twin[ts] = (uint8_t)lane;
+        if (have) s_twin[ts] = (uint8_t)lane;
         __syncwarp();
-        const bool clash = live && s_twin[ts] != (uint8_t)lane;
+        const bool clash = have && s_twin[ts] != (uint8_t)lane;
         unsigned twins = 0u;
         if (__any_sync(FULL, clash)) {
-          twins = __match_any_sync(FULL, key) & ((1u << lane) - 1u) & ~((1u << first) - 1u);
+          twins = __match_any_sync(FULL, key) & ((1u << lane) - 1u);
           if (!live) twins = 0u;
         }
         while (twins && !dup) {
@@ -993,15 +1004,55 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
         }
         __syncwarp();
       }
-      // commit lanes first .. first_dup - 1, as far as the population needs
+      // the next hit, unless the population fills before it
       const unsigned dupmask = __ballot_sync(FULL, dup);
       const int first_dup = dupmask ? __ffs(dupmask) - 1 : avail;
-      const int need = d.P - n;
-      const int nacc = min(first_dup - first, need);
-      const bool hit = first_dup < avail && first_dup - first < need;
-      const int processed = nacc + (hit ? 1 : 0);
-      const int k = lane - first;
-      if (k >= 0 && k < nacc) {
+      const int need = d.P - n - acc;
+      if (first_dup - first >= need) {
+        acc += need;
+        cut = first + need;
+        done_batch = true;
+      } else {
+        acc += first_dup - first;
+        if (first_dup >= avail) {
+          done_batch = true;
+        } else {
+          hitmask |= 1u << first_dup;
+          if (++hits > d.P) {
+            stopped = 1;
+            cut = first_dup + 1;
+            done_batch = true;
+          } else if (first_dup + 1 >= avail) {
+            done_batch = true;
+          } else {
+            // the hit's child is not accepted: take it out of the later
+            // lanes' sums and go on with the rest of the batch
+            if (K == 2) {
+              uint4 wo[NV];
+#pragma unroll
+              for (int v = 0; v < NV; ++v) {
+                wo[v].x = __shfl_sync(FULL, cw[v].x, first_dup);
+                wo[v].y = __shfl_sync(FULL, cw[v].y, first_dup);
+                wo[v].z = __shfl_sync(FULL, cw[v].z, first_dup);
+                wo[v].w = __shfl_sync(FULL, cw[v].w, first_dup);
+              }
+              if (lane > first_dup) add_overlap(wo, -1);
+            }
+            first = first_dup + 1;
+          }
+        }
+      }
+      __syncwarp();
+    }
+    // commit the accepted lanes of [0, cut) in lane order
+    {
+      const unsigned accm = __ballot_sync(FULL, have && lane < cut && !((hitmask >> lane) & 1u));
+      const int k = __popc(accm & ((1u << lane) - 1u));
+      if ((accm >> lane) & 1u) {
+        const unsigned long long key = reinterpret_cast<const unsigned long long*>(ra + l.chash)[dec];
+        const int L = reinterpret_cast<const int32_t*>(ra + l.cL)[dec];
+        const uint16_t* child = reinterpret_cast<const uint16_t*>(ra + l.ccols) + (size_t)dec * S;
+        const uint32_t fb = (uint32_t)(key >> 32) & (uint32_t)(kFilterBits - 1);
         lkey[n - E + k] = key;
         lref[n - E + k] = (int32_t)((j0 + sb + lane) * NC + dec);
         atomicOr(&fbits[fb >> 5], 1u << (fb & 31));
@@ -1022,29 +1073,10 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
         }
         d.len[base + n + k] = L;
       }
-      if (k >= 0 && k < processed) ex_lane += nex;
-      attempts += processed;
-      n += nacc;
-      if (hit && ++hits > d.P) stopped = 1;
-      if (hit && !stopped && n < d.P && first_dup + 1 < avail) {
-        // the hit's child is not accepted: take it out of the later lanes'
-        // sums and go on with the rest of the batch
-        if (K == 2) {
-          uint4 wo[NV];
-#pragma unroll
-          for (int v = 0; v < NV; ++v) {
-            wo[v].x = __shfl_sync(FULL, cw[v].x, first_dup);
-            wo[v].y = __shfl_sync(FULL, cw[v].y, first_dup);
-            wo[v].z = __shfl_sync(FULL, cw[v].z, first_dup);
-            wo[v].w = __shfl_sync(FULL, cw[v].w, first_dup);
-          }
-          if (lane > first_dup) add_overlap(wo, -1);
-        }
-        first = first_dup + 1;
-      } else {
-        sb += first + processed;
-        done_batch = true;
-      }
+      if (have && lane < cut) ex_lane += nex;
+      attempts += cut;
+      n += acc;
+      sb += cut;
       __syncwarp();
     }
   }
