@@ -124,9 +124,37 @@ __host__ __device__ inline RecLayout rec_layout(int k, int S, bool init, int nw)
 }
 
 // The column set of a series as nw bitset words.
+// (gathered in registers, eight columns read per round; nw <= 8)
 __device__ __forceinline__ void write_bits(uint32_t* out, int nw, const uint16_t* s, int L) {
-  for (int w = 0; w < nw; ++w) out[w] = 0u;
-  for (int i = 0; i < L; ++i) out[s[i] >> 5] |= 1u << (s[i] & 31);
+  uint32_t acc[8];
+#pragma unroll
+  for (int w = 0; w < 8; ++w) acc[w] = 0u;
+  for (int c0 = 0; c0 < L; c0 += 8) {
+    uint32_t col[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) col[i] = c0 + i < L ? (uint32_t)s[c0 + i] : 0xffffffffu;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const uint32_t bit = col[i] != 0xffffffffu ? 1u << (col[i] & 31) : 0u;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) acc[w] |= (col[i] >> 5) == (uint32_t)w ? bit : 0u;
+    }
+  }
+#pragma unroll
+  for (int w = 0; w < 8; ++w)
+    if (w < nw) out[w] = acc[w];
+}
+
+// Copies L columns, eight loads in flight per round.
+__device__ __forceinline__ void copy_cols(uint16_t* dst, const uint16_t* src, int L) {
+  for (int c0 = 0; c0 < L; c0 += 8) {
+    uint16_t v[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = c0 + i < L ? src[c0 + i] : (uint16_t)0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (c0 + i < L) dst[c0 + i] = v[i];
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -204,11 +232,56 @@ __device__ __forceinline__ bool holds(const uint16_t* s, int L, int c) {
   return false;
 }
 
+// A set of columns below 256 as eight words in registers (every word index
+// resolved by unrolled selects): membership in O(1) and the k-th absent
+// column by a popcount walk -- the same answers as holds / kth_absent.
+struct ColSet8 {
+  uint32_t w[8];
+  __device__ __forceinline__ void clear() {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) w[i] = 0u;
+  }
+  __device__ __forceinline__ void add(uint32_t c) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) w[i] |= (c >> 5) == (uint32_t)i ? 1u << (c & 31) : 0u;
+  }
+  __device__ __forceinline__ bool has(uint32_t c) const {
+    uint32_t r = 0u;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) r |= (c >> 5) == (uint32_t)i ? w[i] : 0u;
+    return (r >> (c & 31)) & 1u;
+  }
+  __device__ __forceinline__ void fill(const uint16_t* s, int L) {
+    clear();
+    for (int i = 0; i < L; ++i) add(s[i]);
+  }
+  // k-th (0-based) column below C, in increasing order, not in the set
+  __device__ __forceinline__ int kth_absent(uint32_t k, int C) const {
+    int found = -1;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int lo = 32 * i;
+      uint32_t z = ~w[i];
+      if (C - lo < 32) z &= C - lo > 0 ? (1u << (C - lo)) - 1u : 0u;
+      const uint32_t cnt = (uint32_t)__popc(z);
+      if (found < 0) {
+        if (k < cnt) {
+          for (uint32_t t = 0; t < k; ++t) z &= z - 1u;     // drop the k lowest
+          found = lo + __ffs(z) - 1;
+        } else {
+          k -= cnt;
+        }
+      }
+    }
+    return found;
+  }
+};
+
 // The four mutations (Fig. 1a-d): one, chosen uniformly among those that keep
 // the series in [Lmin, Lmax] with distinct columns (insert, delete, swap,
 // substitute in that order).
-__device__ void mutate(uint16_t* x, int& L, int C, int Lmin, int Lmax, uint32_t rt, uint32_t r1,
-                       uint32_t r2) {
+__device__ __forceinline__ void mutate(uint16_t* x, int& L, int C, int Lmin, int Lmax, uint32_t rt,
+                                       uint32_t r1, uint32_t r2, const ColSet8* cs = nullptr) {
   int allowed[4];
   int n = 0;
   if (L < Lmax && L < C) allowed[n++] = 0;
@@ -219,7 +292,8 @@ __device__ void mutate(uint16_t* x, int& L, int C, int Lmin, int Lmax, uint32_t 
   const int kind = allowed[below(rt, (uint32_t)n)];
   if (kind == 0) {
     const int pos = (int)below(r1, (uint32_t)(L + 1));
-    const int col = kth_absent(x, L, below(r2, (uint32_t)(C - L)));
+    const uint32_t kk = below(r2, (uint32_t)(C - L));
+    const int col = cs ? cs->kth_absent(kk, C) : kth_absent(x, L, kk);
     for (int i = L; i > pos; --i) x[i] = x[i - 1];
     x[pos] = (uint16_t)col;
     ++L;
@@ -236,7 +310,8 @@ __device__ void mutate(uint16_t* x, int& L, int C, int Lmin, int Lmax, uint32_t 
     x[j] = t;
   } else {
     const int pos = (int)below(r1, (uint32_t)L);
-    x[pos] = (uint16_t)kth_absent(x, L, below(r2, (uint32_t)(C - L)));
+    const uint32_t kk = below(r2, (uint32_t)(C - L));
+    x[pos] = (uint16_t)(cs ? cs->kth_absent(kk, C) : kth_absent(x, L, kk));
   }
 }
 
@@ -258,9 +333,18 @@ __device__ __forceinline__ unsigned long long seq_hash(const uint16_t* s, int L)
 
 __device__ __forceinline__ bool same_series(const uint16_t* a, int La, const uint16_t* b, int Lb) {
   if (La != Lb) return false;
-  for (int i = 0; i < La; ++i)
-    if (a[i] != b[i]) return false;
-  return true;
+  bool eq = true;
+  for (int c0 = 0; c0 < La && eq; c0 += 8) {    // eight columns of each side per round
+    uint32_t x[8], y[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      x[i] = c0 + i < La ? a[c0 + i] : 0u;
+      y[i] = c0 + i < La ? b[c0 + i] : 0u;
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) eq = eq && x[i] == y[i];
+  }
+  return eq;
 }
 
 __device__ bool tabu_contains(const EaDev& d, unsigned long long key, const uint16_t* s, int L) {
@@ -306,7 +390,16 @@ __global__ void __launch_bounds__(128) k_spec(EaDev d) {
   if (INIT) {
     // Step 1: length uniform in [Lmin, Lmax], then distinct uniform columns.
     L = d.Lmin + (int)below(r(0), (uint32_t)(d.Lmax - d.Lmin + 1));
-    for (int i = 0; i < L; ++i) x[i] = (uint16_t)kth_absent(x, i, below(r(1 + i), (uint32_t)(d.C - i)));
+    if (d.C <= 256) {
+      ColSet8 cs;
+      cs.clear();
+      for (int i = 0; i < L; ++i) {
+        x[i] = (uint16_t)cs.kth_absent(below(r(1 + i), (uint32_t)(d.C - i)), d.C);
+        cs.add(x[i]);
+      }
+    } else {
+      for (int i = 0; i < L; ++i) x[i] = (uint16_t)kth_absent(x, i, below(r(1 + i), (uint32_t)(d.C - i)));
+    }
   } else {
     const int k = d.k;
     const uint32_t P = (uint32_t)d.P;
@@ -323,36 +416,56 @@ __global__ void __launch_bounds__(128) k_spec(EaDev d) {
       reinterpret_cast<int32_t*>(rec + l.eL)[e] = eL;
       reinterpret_cast<int32_t*>(rec + l.ent)[e < k ? e : 4 + (e - k)] = idx;
       uint16_t* ec = reinterpret_cast<uint16_t*>(rec + l.ecols) + (size_t)e * d.S;
-      const uint16_t* src = d.seq + (size_t)er * d.S;
-      for (int i = 0; i < eL; ++i) ec[i] = src[i];
-      if (l.nw) write_bits(reinterpret_cast<uint32_t*>(rec + l.ebit) + (size_t)e * l.nw, l.nw, src, eL);
+      uint16_t t[kMaxLen];
+      copy_cols(t, d.seq + (size_t)er * d.S, eL);
+      copy_cols(ec, t, eL);
+      if (l.nw) write_bits(reinterpret_cast<uint32_t*>(rec + l.ebit) + (size_t)e * l.nw, l.nw, t, eL);
     }
     if (c == 0 && v == 0) reinterpret_cast<int32_t*>(rec + l.cross)[0] = cross ? 1 : 0;
     const int base = 2 * k + 1 + 5 * v;
     const int ia = (int)below(r(ta), P);
-    const uint16_t* a = d.seq + (size_t)(prev + ia) * d.S;
     const int La = d.len[prev + ia];
-    for (int i = 0; i < La; ++i) x[i] = a[i];
+    copy_cols(x, d.seq + (size_t)(prev + ia) * d.S, La);
+    const uint16_t* a = x;
     L = La;
     if (cross) {
       const int ib = (int)below(r(k + 1 + tb), P);
-      const uint16_t* b = d.seq + (size_t)(prev + ib) * d.S;
       const int Lb = d.len[prev + ib];
+      uint16_t b[kMaxLen];
+      copy_cols(b, d.seq + (size_t)(prev + ib) * d.S, Lb);
       const int cut_a = 1 + (int)below(r(base), (uint32_t)La);
       const int cut_b = (int)below(r(base + 1), (uint32_t)Lb);
       uint16_t y[kMaxLen];
       int Ly = 0;
       for (int i = 0; i < cut_a; ++i) y[Ly++] = a[i];
-      for (int i = cut_b; i < Lb; ++i) {
-        if (Ly >= d.Lmax) break;
-        if (!holds(y, Ly, b[i])) y[Ly++] = b[i];
+      if (d.C <= 256) {
+        ColSet8 ys;
+        ys.fill(y, Ly);
+        for (int i = cut_b; i < Lb; ++i) {
+          if (Ly >= d.Lmax) break;
+          if (!ys.has(b[i])) {
+            ys.add(b[i]);
+            y[Ly++] = b[i];
+          }
+        }
+      } else {
+        for (int i = cut_b; i < Lb; ++i) {
+          if (Ly >= d.Lmax) break;
+          if (!holds(y, Ly, b[i])) y[Ly++] = b[i];
+        }
       }
       if (Ly >= d.Lmin) {
         for (int i = 0; i < Ly; ++i) x[i] = y[i];
         L = Ly;
       }
     }
-    mutate(x, L, d.C, d.Lmin, d.Lmax, r(base + 2), r(base + 3), r(base + 4));
+    if (d.C <= 256) {
+      ColSet8 xs;
+      xs.fill(x, L);
+      mutate(x, L, d.C, d.Lmin, d.Lmax, r(base + 2), r(base + 3), r(base + 4), &xs);
+    } else {
+      mutate(x, L, d.C, d.Lmin, d.Lmax, r(base + 2), r(base + 3), r(base + 4));
+    }
   }
   if (SCREEN) {
     const long long row = jc * V + v;
@@ -1594,6 +1707,90 @@ __device__ __forceinline__ int overlap_bits(const uint32_t* a, const uint32_t (&
   return inter;
 }
 
+// Bitonic sort of N = EPT * kRankWarpThreads (key, index) pairs into
+// ascending order (key, then index), thread t holding elements EPT t .. EPT t
+// + EPT - 1 in registers: compare-exchanges within a thread, with a partner
+// thread of the warp by shuffles, and through shared memory (skey / sidx, N
+// entries) only for partners in other warps.
+template <int EPT>
+__device__ __forceinline__ void sort_pairs(unsigned long long* skey, int32_t* sidx, int tid) {
+  constexpr int N = EPT * kRankWarpThreads;
+  unsigned long long k[EPT];
+  int32_t x[EPT];
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    k[q] = skey[EPT * tid + q];
+    x[q] = sidx[EPT * tid + q];
+  }
+  // element e of the block-direction `up` keeps the smaller of the pair when
+  // it is the lower position of an ascending block (or the upper of a
+  // descending one), the larger otherwise
+  auto keep = [](unsigned long long& ka, int32_t& xa, unsigned long long kb, int32_t xb,
+                 bool want_min) {
+    const bool a_gt_b = ka > kb || (ka == kb && xa > xb);
+    if (a_gt_b == want_min) {
+      ka = kb;
+      xa = xb;
+    }
+  };
+  for (int size = 2; size <= N; size <<= 1) {
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      if (stride >= 32 * EPT) {
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+          skey[EPT * tid + q] = k[q];
+          sidx[EPT * tid + q] = x[q];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+          const int e = EPT * tid + q, p = e ^ stride;
+          keep(k[q], x[q], skey[p], sidx[p], (e < p) == ((e & size) == 0));
+        }
+      } else if (stride >= EPT) {
+        const int lane_x = stride / EPT;
+#pragma unroll
+        for (int q = 0; q < EPT; ++q) {
+          const int e = EPT * tid + q, p = e ^ stride;
+          const unsigned long long kp = __shfl_xor_sync(0xffffffffu, k[q], lane_x);
+          const int32_t xp = __shfl_xor_sync(0xffffffffu, x[q], lane_x);
+          keep(k[q], x[q], kp, xp, (e < p) == ((e & size) == 0));
+        }
+      } else {
+        // (the in-thread stride as a compile-time constant keeps k and x in
+        // registers)
+#pragma unroll
+        for (int ls = EPT / 2; ls > 0; ls >>= 1) {
+          if (ls != stride) continue;
+#pragma unroll
+          for (int q = 0; q < EPT; ++q) {
+            if (q & ls) continue;
+            const int e = EPT * tid + q;
+            const bool up = (e & size) == 0;
+            const unsigned long long ka = k[q], kb = k[q ^ ls];
+            const int32_t xa = x[q], xb = x[q ^ ls];
+            const bool a_gt_b = ka > kb || (ka == kb && xa > xb);
+            if (a_gt_b == up) {
+              k[q] = kb;
+              x[q] = xb;
+              k[q ^ ls] = ka;
+              x[q ^ ls] = xa;
+            }
+          }
+        }
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < EPT; ++q) {
+    skey[EPT * tid + q] = k[q];
+    sidx[EPT * tid + q] = x[q];
+  }
+  __syncthreads();
+}
+
 template <int NW>
 __global__ void __launch_bounds__(kRankWarpThreads) k_rank_warp(EaDev d, int Pp) {
   extern __shared__ __align__(128) unsigned long long smem_u64[];
@@ -1602,9 +1799,10 @@ __global__ void __launch_bounds__(kRankWarpThreads) k_rank_warp(EaDev d, int Pp)
   const int g = d.ctl->gen;
   const long long base = (long long)g * d.P;
   const int cap = d.T + d.P, P = d.P;
+  const int Ns = Pp > kRankWarpThreads ? Pp : kRankWarpThreads;   // sorted entries
   unsigned long long* skey = smem_u64;
-  int32_t* sidx = reinterpret_cast<int32_t*>(skey + Pp);
-  double* pf = reinterpret_cast<double*>(sidx + Pp + (Pp & 1));
+  int32_t* sidx = reinterpret_cast<int32_t*>(skey + Ns);
+  double* pf = reinterpret_cast<double*>(sidx + Ns);
   int32_t* pL = reinterpret_cast<int32_t*>(pf + P);
   // the records and bitsets are read as 16-byte vectors: align by offset
   char* const sb = reinterpret_cast<char*>(smem_u64);
@@ -1614,7 +1812,7 @@ __global__ void __launch_bounds__(kRankWarpThreads) k_rank_warp(EaDev d, int Pp)
   uint32_t* lbits = pbits + (size_t)P * NW;
   int32_t* thr = reinterpret_cast<int32_t*>(lbits + (size_t)cap * NW);
 
-  for (int i = tid; i < Pp; i += kRankWarpThreads) {
+  for (int i = tid; i < Ns; i += kRankWarpThreads) {
     if (i < P) {
       skey[i] = ~(unsigned long long)__double_as_longlong(d.fit[base + i]);
       sidx[i] = i;
@@ -1636,25 +1834,11 @@ __global__ void __launch_bounds__(kRankWarpThreads) k_rank_warp(EaDev d, int Pp)
     for (int c = 0; c < L; ++c) b[sq[c] >> 5] |= 1u << (sq[c] & 31);
   }
   __syncthreads();
-  for (int size = 2; size <= Pp; size <<= 1) {
-    for (int stride = size >> 1; stride > 0; stride >>= 1) {
-      for (int i = tid; i < Pp; i += kRankWarpThreads) {
-        const int jx = i ^ stride;
-        if (jx > i) {
-          const bool up = (i & size) == 0;
-          const unsigned long long ka = skey[i], kb = skey[jx];
-          const int ia = sidx[i], ib = sidx[jx];
-          const bool a_gt_b = ka > kb || (ka == kb && ia > ib);
-          if (a_gt_b == up) {
-            skey[i] = kb;
-            skey[jx] = ka;
-            sidx[i] = ib;
-            sidx[jx] = ia;
-          }
-        }
-      }
-      __syncthreads();
-    }
+  switch (Ns / kRankWarpThreads) {     // Ns is a power of two >= 512
+    case 1: sort_pairs<1>(skey, sidx, tid); break;
+    case 2: sort_pairs<2>(skey, sidx, tid); break;
+    case 4: sort_pairs<4>(skey, sidx, tid); break;
+    default: sort_pairs<8>(skey, sidx, tid); break;
   }
   // individuals in visiting order: fitness, length, bitset
   for (int oi = tid; oi < P; oi += kRankWarpThreads) {
@@ -1774,7 +1958,8 @@ __global__ void __launch_bounds__(kRankWarpThreads) k_rank_warp(EaDev d, int Pp)
 // Shared bytes of k_rank_warp<NW> for population P (padded Pp), list T.
 static size_t rank_warp_smem(int P, int Pp, int T, int Lmax, int NW) {
   const size_t cap = (size_t)T + P;
-  return (size_t)Pp * 12 + 4 * (Pp & 1) + (size_t)P * 12 + 16 + cap * sizeof(RankRec) +
+  const size_t Ns = (size_t)std::max(Pp, kRankWarpThreads);
+  return Ns * 12 + (size_t)P * 12 + 16 + cap * sizeof(RankRec) +
          ((size_t)P + cap) * NW * 4 + (size_t)(Lmax + 1) * 4;
 }
 
@@ -2113,7 +2298,7 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
   // Step 5 by one warp from shared bitsets when the columns and sizes allow
   st->rank_nw = 0;
   const int rnw = bit_words(st->WC);
-  if (rnw) {
+  if (rnw && st->Pp <= 8 * kRankWarpThreads) {    // the register sort holds 8 per thread
     const size_t need = rank_warp_smem(P, st->Pp, T, p->len_max, rnw);
     if (need <= 200 * 1024) {
       st->rank_nw = rnw;

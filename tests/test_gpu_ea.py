@@ -251,9 +251,10 @@ def test_wide_matrix_generic_paths():
     run_both(A, iterations=6, len_max=8)
 
 
-@pytest.mark.parametrize("P,T", [(37, 3), (300, 250), (1024, 1)])
+@pytest.mark.parametrize("P,T", [(37, 3), (300, 250), (1024, 1), (2000, 50)])
 def test_population_and_list_sizes(P, T):
     """Populations that are not powers of two, lists shorter and longer than
-    a warp's chunk, a list of one."""
+    a warp's chunk, a list of one; Step 5's sort with one, two and four keys
+    per thread (P up to 512, 1,024 and 2,048)."""
     prob = synth.matrix_tiny(seed=5)
     run_both(prob.A, iterations=5, pop_size=P, toprank_size=T, len_max=6)
