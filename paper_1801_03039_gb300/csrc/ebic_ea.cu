@@ -1121,7 +1121,58 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
       const unsigned dupmask = __ballot_sync(FULL, dup);
       const int first_dup = dupmask ? __ffs(dupmask) - 1 : avail;
       const int need = d.P - n - acc;
-      if (first_dup - first >= need) {
+      // Several hits at once: when every duplicate of the round is a hit
+      // (the population fills after the last one and the tabu rule does not
+      // stop the run), take all their children out of the later lanes' sums
+      // and re-decide once.  If no lane -- hits included -- changes, these
+      // are exactly the sequential outcome's hits and the batch is settled;
+      // otherwise the sums go back and the hits are taken one per round.
+      const int m = __popc(dupmask);
+      bool settled = false;
+      if (m >= 2 && (31 - __clz(dupmask) - first) - (m - 1) < need && hits + m <= d.P) {
+        int32_t keep_sx[NE];
+#pragma unroll
+        for (int e = 0; e < NE; ++e) keep_sx[e] = Sx[e];
+        if (K == 2) {
+          unsigned rest = dupmask;
+          while (rest) {
+            const int b = __ffs(rest) - 1;
+            rest &= rest - 1;
+            uint4 wo[NV];
+#pragma unroll
+            for (int v = 0; v < NV; ++v) {
+              wo[v].x = __shfl_sync(FULL, cw[v].x, b);
+              wo[v].y = __shfl_sync(FULL, cw[v].y, b);
+              wo[v].z = __shfl_sync(FULL, cw[v].z, b);
+              wo[v].w = __shfl_sync(FULL, cw[v].w, b);
+            }
+            if (lane > b) add_overlap(wo, -1);
+          }
+        }
+        int nx = 0;
+        const int nd = decide(&nx);
+        if (!__any_sync(FULL, have && lane >= first && nd != dec)) {
+          hitmask |= dupmask;
+          hits += m;
+          const int free_lanes = (avail - first) - m;
+          if (free_lanes >= need) {
+            // the need-th accepted lane fills the population and ends the batch
+            unsigned am = __ballot_sync(FULL, have && lane >= first && !dup);
+            for (int t = 1; t < need; ++t) am &= am - 1;
+            cut = __ffs(am);
+            acc += need;
+          } else {
+            acc += free_lanes;
+          }
+          done_batch = true;
+          settled = true;
+        } else {
+#pragma unroll
+          for (int e = 0; e < NE; ++e) Sx[e] = keep_sx[e];
+        }
+      }
+      if (settled) {
+      } else if (first_dup - first >= need) {
         acc += need;
         cut = first + need;
         done_batch = true;
