@@ -1006,8 +1006,8 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
     bool done_batch = false;
     // duplicate flags of the lanes' current children; they stay exact for a
     // round that changes no child (after a hit, a child equal to the hit's or
-    // to a child committed with it was already flagged as equal to an
-    // earlier lane's)
+    // to an earlier accepted lane's was already flagged by the twin check,
+    // which covers every earlier lane of the batch)
     bool dup = false, dups_valid = false;
     while (!done_batch) {
       bool round_changed = false;
@@ -1051,8 +1051,8 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
           }
         }
       }
-      // duplicates: tabu flag, this generation's committed children (filter,
-      // then the key list), equal keys among unsettled earlier lanes
+      // duplicates: tabu flag, the generation's children committed by earlier
+      // batches (filter, then the key list), equal keys among earlier lanes
       const bool live = have && lane >= first;
       const unsigned long long key =
           have ? reinterpret_cast<const unsigned long long*>(ra + l.chash)[dec] : 0ull;
@@ -1077,7 +1077,7 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
           const uint16_t* cb = reinterpret_cast<const uint16_t*>(cur + (size_t)(sb + b) * RB + l.ccols) +
                                (size_t)s_dec[b] * S;
           bool found = false;
-  #pragma unroll 4
+#pragma unroll 4
           for (int i = lane; i < n - E; i += 32) {
             if (lkey[i] == kb) {
               const int32_t r = lref[i];
@@ -1131,9 +1131,9 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
       bool settled = false;
       if (m >= 2 && (31 - __clz(dupmask) - first) - (m - 1) < need && hits + m <= d.P) {
         int32_t keep_sx[NE];
-#pragma unroll
-        for (int e = 0; e < NE; ++e) keep_sx[e] = Sx[e];
         if (K == 2) {
+#pragma unroll
+          for (int e = 0; e < NE; ++e) keep_sx[e] = Sx[e];
           unsigned rest = dupmask;
           while (rest) {
             const int b = __ffs(rest) - 1;
@@ -1166,7 +1166,7 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
           }
           done_batch = true;
           settled = true;
-        } else {
+        } else if (K == 2) {
 #pragma unroll
           for (int e = 0; e < NE; ++e) Sx[e] = keep_sx[e];
         }
