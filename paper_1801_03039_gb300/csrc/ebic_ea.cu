@@ -749,7 +749,9 @@ __device__ __forceinline__ void hs8(const uint32_t (&v)[8], uint32_t& ones, uint
 
 // Named barrier 1 over the builder's CTA: warp 0 and the helper warps meet
 // there twice per batch (job posted, shares done) and once per chunk (release).
-constexpr int kBuildThreads = 128;
+// Eight warps: warp w takes entrant w % 4 of the overlap pass over half
+// w / 4 of the earlier lanes.
+constexpr int kBuildThreads = 256;
 // Step 3 fast path: a bit filter over the keys of the generation's committed
 // children (one bit per key, chosen by the key's high 32 bits) in front of a
 // dense list of those keys; a clear bit proves a child new.
@@ -760,11 +762,13 @@ __device__ __forceinline__ void bar_team() {
 }
 
 // One entrant's share of a batch's overlap pass: for the attempt of lane a
-// (record sb + a of the chunk), sum over earlier lanes b < a of
-// |entrant e & child_b|, the children's bitsets in s_cw (Harley-Seal).
+// (record sb + a of the chunk), sum over earlier lanes b < a with b in
+// [b_lo, b_hi) of |entrant e & child_b|, the children's bitsets in s_cw
+// (Harley-Seal).  b_lo and b_hi are even.
 template <int K, int NV>
 __device__ __forceinline__ int pass0_share(const RecLayout& l, const char* cur, int sb, int avail,
-                                           int e, int lane, int RB, const uint4* s_cw) {
+                                           int e, int lane, int RB, const uint4* s_cw, int b_lo,
+                                           int b_hi) {
   constexpr int NW = 4 * NV;
   const bool have = lane < avail;
   const char* ra = cur + (size_t)(have ? sb + lane : sb) * RB;
@@ -777,7 +781,8 @@ __device__ __forceinline__ int pass0_share(const RecLayout& l, const char* cur, 
                  : make_uint4(0u, 0u, 0u, 0u);
   uint32_t h1 = 0u, h2 = 0u, h4 = 0u;
   int h8 = 0;
-  for (int b = 0; b + 1 < avail; b += 2) {
+  const int b_end = min(b_hi, avail);
+  for (int b = b_lo; b + 1 < b_end; b += 2) {
     uint32_t m[2][NW];
 #pragma unroll
     for (int i = 0; i < 2; ++i) {
@@ -806,12 +811,12 @@ __device__ __forceinline__ int pass0_share(const RecLayout& l, const char* cur, 
 // Shared words of the builder's team protocol.
 struct Team {
   int job, sb, avail;
-  int ov[32 * 4];       // entrant e of lane a: ov[4 a + e]
+  int ov[2][32 * 4];    // entrant e of lane a, half h of the earlier lanes: ov[h][4 a + e]
 };
 
-// Helper warps (1 .. 3) during one chunk of the fast path: each batch they
-// compute the overlap share of entrant `warp` for all 32 lanes; a job of 0
-// ends the chunk.
+// Helper warps (1 .. 7) during one chunk of the fast path: each batch warp w
+// computes the overlap share of entrant w % 4 over half w / 4 of the earlier
+// lanes, for all 32 lanes; a job of 0 ends the chunk.
 template <int NV>
 __device__ __forceinline__ void team_helper(const RecLayout& l, const char* cur, int RB,
                                             int warp, int lane, Team* tm, const uint4* s_cw) {
@@ -819,7 +824,9 @@ __device__ __forceinline__ void team_helper(const RecLayout& l, const char* cur,
     bar_team();
     if (*(volatile int*)&tm->job == 0) break;
     const int sb = tm->sb, avail = tm->avail;
-    tm->ov[4 * lane + warp] = pass0_share<2, NV>(l, cur, sb, avail, warp, lane, RB, s_cw);
+    const int e = warp & 3, h = warp >> 2;
+    tm->ov[h][4 * lane + e] = pass0_share<2, NV>(l, cur, sb, avail, e, lane, RB, s_cw, 16 * h,
+                                                 16 * h + 16);
     bar_team();
   }
 }
@@ -981,8 +988,9 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
 #pragma unroll
       for (int v = 0; v < NV; ++v) s_cw[lane * NV + v] = cw[v];
       __syncwarp();
-      // the overlap pass, one entrant per warp of the CTA: post the job,
-      // take entrant 0 here, collect entrants 1 .. 3 from the helpers
+      // the overlap pass, one (entrant, half of the earlier lanes) per warp
+      // of the CTA: post the job, take entrant 0's first half here, collect
+      // the other shares from the helpers
       if (lane == 0) {
         tm->sb = sb;
         tm->avail = avail;
@@ -990,11 +998,11 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
       }
       __syncwarp();
       bar_team();
-      const int ov0 = pass0_share<K, NV>(l, cur, sb, avail, 0, lane, RB, s_cw);
+      const int ov0 = pass0_share<K, NV>(l, cur, sb, avail, 0, lane, RB, s_cw, 0, 16);
       bar_team();
-      Sx[0] += ov0;
+      Sx[0] += ov0 + tm->ov[1][4 * lane];
 #pragma unroll
-      for (int e = 1; e < NE; ++e) Sx[e] += tm->ov[4 * lane + e];
+      for (int e = 1; e < NE; ++e) Sx[e] += tm->ov[0][4 * lane + e] + tm->ov[1][4 * lane + e];
     }
     // Lanes below `first` are settled: accepted (committed together at the
     // end of the batch) or hits.  A round finds the next hit; the hit's child
@@ -1268,7 +1276,7 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
 // commit order behind the bit filter fbits.
 // ---------------------------------------------------------------------------
 template <bool INIT>
-__global__ void __launch_bounds__(kBuildThreads) k_build(EaDev d, int hmask, int kB) {
+__global__ void __launch_bounds__(kBuildThreads, 1) k_build(EaDev d, int hmask, int kB) {
   extern __shared__ __align__(128) unsigned long long smem_u64[];
   if (*(volatile int32_t*)&d.ctl->stop) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
