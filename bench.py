@@ -754,7 +754,7 @@ def roofline(wl, gens, extra, per_step_ms, peaks):
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G warp-inst/s",
             "frac": achieved / peak if achieved else None,
             "traffic": prof.get("dram_bytes_per_launch") if prof else None,
-            "kernel": "k_build (Step 3 builder, one CTA of four warps on one SM)",
+            "kernel": "k_build (Step 3 builder, one CTA of eight warps on one SM)",
             "work_per_launch": inst, "work_def": "warp-instructions per launch (ncu)",
             "peak_source": "4 warp-instructions/cycle (one SM) x median SM clock sampled in this run",
             "duration_us": extra["k_build_us_timed"],
