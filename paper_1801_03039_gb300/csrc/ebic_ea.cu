@@ -811,20 +811,53 @@ __device__ __forceinline__ int pass0_share(const RecLayout& l, const char* cur, 
 // Shared words of the builder's team protocol.
 struct Team {
   int job, sb, avail;
+  int sx[2][4][32];     // penalty sum of entrant e of lane a over half h of its columns
   int ov[2][32 * 4];    // entrant e of lane a, half h of the earlier lanes: ov[h][4 a + e]
 };
 
+// One entrant's penalty sum over half h of its columns (the first
+// ceil(L / 2) or the rest), eight column loads in flight per round.
+template <int K>
+__device__ __forceinline__ int pen_share(const RecLayout& l, const char* cur, int sb, int avail,
+                                         int S, int e, int h, int lane, int RB,
+                                         const uint32_t* pen) {
+  const bool have = lane < avail;
+  const char* ra = cur + (size_t)(have ? sb + lane : sb) * RB;
+  const int cr = have ? *reinterpret_cast<const int32_t*>(ra + l.cross) : 0;
+  if (!(have && (e < K || cr))) return 0;
+  const int L = reinterpret_cast<const int32_t*>(ra + l.eL)[e];
+  const int half = (L + 1) >> 1;
+  const int c_lo = h ? half : 0, c_hi = h ? L : half;
+  const uint16_t* cs = reinterpret_cast<const uint16_t*>(ra + l.ecols) + (size_t)e * S;
+  int sum = 0;
+  for (int c0 = c_lo; c0 < c_hi; c0 += 8) {
+    uint32_t col[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) col[i] = c0 + i < c_hi ? cs[c0 + i] : 0u;
+#pragma unroll
+    for (int i = 0; i < 8; ++i)
+      if (c0 + i < c_hi) sum += (int)pen[col[i]];
+  }
+  return sum;
+}
+
 // Helper warps (1 .. 7) during one chunk of the fast path: each batch warp w
-// computes the overlap share of entrant w % 4 over half w / 4 of the earlier
-// lanes, for all 32 lanes; a job of 0 ends the chunk.
+// computes, for all 32 lanes, the penalty sum of entrant w % 4 over half
+// w / 4 of its columns, then (once warp 0 has posted the children) that
+// entrant's overlap share over half w / 4 of the earlier lanes; a job of 0
+// ends the chunk.  Four meetings at named barrier 1 per batch.
 template <int NV>
-__device__ __forceinline__ void team_helper(const RecLayout& l, const char* cur, int RB,
-                                            int warp, int lane, Team* tm, const uint4* s_cw) {
+__device__ __forceinline__ void team_helper(const RecLayout& l, const char* cur, int RB, int S,
+                                            int warp, int lane, Team* tm, const uint4* s_cw,
+                                            const uint32_t* pen) {
   for (;;) {
     bar_team();
     if (*(volatile int*)&tm->job == 0) break;
     const int sb = tm->sb, avail = tm->avail;
     const int e = warp & 3, h = warp >> 2;
+    tm->sx[h][e][lane] = pen_share<2>(l, cur, sb, avail, S, e, h, lane, RB, pen);
+    bar_team();
+    bar_team();
     tm->ov[h][4 * lane + e] = pass0_share<2, NV>(l, cur, sb, avail, e, lane, RB, s_cw, 16 * h,
                                                  16 * h + 16);
     bar_team();
@@ -922,28 +955,20 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
           for (int v = 0; v < NV; ++v) bits[e][v] = eb[v];
         }
       }
-      // penalty sums of the entrants, eight columns of each entrant per
-      // round: every column index and penalty load of a round is issued
-      // before any of them is used
-      {
-        const uint16_t* ecols = reinterpret_cast<const uint16_t*>(ra + l.ecols);
-        int lmax = 0;
-#pragma unroll
-        for (int e = 0; e < NE; ++e) lmax = max(lmax, Lx[e]);
-        for (int c0 = 0; c0 < lmax; c0 += 8) {
-          uint32_t col[NE][8];
-#pragma unroll
-          for (int e = 0; e < NE; ++e)
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-              col[e][i] = c0 + i < Lx[e] ? ecols[(size_t)e * S + c0 + i] : 0u;
-#pragma unroll
-          for (int e = 0; e < NE; ++e)
-#pragma unroll
-            for (int i = 0; i < 8; ++i)
-              if (c0 + i < Lx[e]) Sx[e] += (int32_t)pen[col[e][i]];
-        }
+      // penalty sums of the entrants: the team's job, one (entrant, half of
+      // its columns) per warp; entrant 0's first half here
+      if (lane == 0) {
+        tm->sb = sb;
+        tm->avail = avail;
+        tm->job = 1;
       }
+      __syncwarp();
+      bar_team();
+      const int s00 = pen_share<K>(l, cur, sb, avail, S, 0, 0, lane, RB, pen);
+      bar_team();
+      Sx[0] = s00 + tm->sx[1][0][lane];
+#pragma unroll
+      for (int e = 1; e < NE; ++e) Sx[e] = tm->sx[0][e][lane] + tm->sx[1][e][lane];
       pc[0] = pair_const(ln[1], ln[0], cl[1], cl[0], id[1], id[0], Sx[1], Sx[0], Lx[1], Lx[0]);
       pc[1] = pair_const(ln[3], ln[2], cl[3], cl[2], id[3], id[2], Sx[3], Sx[2], Lx[3], Lx[2]);
     }
@@ -989,14 +1014,8 @@ __device__ __forceinline__ void build_batch(const EaDev& d, const RecLayout& l, 
       for (int v = 0; v < NV; ++v) s_cw[lane * NV + v] = cw[v];
       __syncwarp();
       // the overlap pass, one (entrant, half of the earlier lanes) per warp
-      // of the CTA: post the job, take entrant 0's first half here, collect
-      // the other shares from the helpers
-      if (lane == 0) {
-        tm->sb = sb;
-        tm->avail = avail;
-        tm->job = 1;
-      }
-      __syncwarp();
+      // of the CTA: release the helpers to it (the job is posted), take
+      // entrant 0's first half here, collect the other shares
       bar_team();
       const int ov0 = pass0_share<K, NV>(l, cur, sb, avail, 0, lane, RB, s_cw, 0, 16);
       bar_team();
@@ -1501,8 +1520,8 @@ __global__ void __launch_bounds__(kBuildThreads, 1) k_build(EaDev d, int hmask, 
         bar_team();
       }
     } else if (team) {
-      if (l.nw == 4) team_helper<1>(l, cur, RB, warp, lane, &s_team, s_cw);
-      else team_helper<2>(l, cur, RB, warp, lane, &s_team, s_cw);
+      if (l.nw == 4) team_helper<1>(l, cur, RB, S, warp, lane, &s_team, s_cw, pen);
+      else team_helper<2>(l, cur, RB, S, warp, lane, &s_team, s_cw, pen);
     }
     __syncthreads();            // the consumed buffer may now be refilled
     if (s_done) {
