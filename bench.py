@@ -127,18 +127,26 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
+        lines = open(self.path).read().splitlines()
+        os.unlink(self.path)
+        return self.summarize(lines, self.bus_id, self.t0, t1)
+
+    @classmethod
+    def summarize(cls, lines, bus_id: str, t0: float, t1: float) -> dict:
+        """Median SM clock, max clock and active throttle reasons of the
+        nvidia-smi samples (CSV lines in FIELDS order) of this GPU taken
+        between t0 and t1 (all samples if none carries a usable stamp)."""
         rows = []
-        for line in open(self.path):
+        for line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) >= 9:
                 rows.append(parts)
         buses = {r[0].lower()[-7:] for r in rows}
-        if len(buses) > 1 and self.bus_id:
-            rows = [r for r in rows if r[0].lower()[-7:] == self.bus_id[-7:]]
-        os.unlink(self.path)
+        if len(buses) > 1 and bus_id:
+            rows = [r for r in rows if r[0].lower()[-7:] == bus_id.lower()[-7:]]
         # keep the samples taken inside the timed region when the stamps allow
-        inside = [r for r in rows if len(r) >= 10 and (self._when(r[9]) or 0) >= self.t0 - 0.05
-                  and (self._when(r[9]) or 0) <= t1 + 0.05]
+        inside = [r for r in rows if len(r) >= 10 and (cls._when(r[9]) or 0) >= t0 - 0.05
+                  and (cls._when(r[9]) or 0) <= t1 + 0.05]
         if inside:
             rows = inside
         sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]

@@ -1,0 +1,100 @@
+"""Host-side logic of bench.py on the CPU: the multi-rank helpers over a
+two-process gloo group, the reference arm's rank handling and JSON line, the
+clock-sample summary, and the per-rank seeding of the weak-scaling
+workloads."""
+import argparse
+import json
+import os
+import socket
+
+import numpy as np
+import pytest
+
+import bench
+
+
+def _free_port() -> int:
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, ws, port, out_dir):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws), LOCAL_RANK=str(rank))
+    import torch.distributed as dist
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        assert bench.dist_env() == (ws, rank, rank)
+        bench.barrier(ws)
+        # per-rank step times: the job's time is the slowest rank's
+        slowest = bench.aggregate_max(1.5 + 2.25 * rank, ws, device="cpu")
+        bench.barrier(ws)
+        with open(os.path.join(out_dir, f"rank{rank}.json"), "w") as f:
+            json.dump({"slowest": slowest}, f)
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_two_gloo_ranks(tmp_path):
+    """bench.py's barrier and max-over-ranks timing on a world of two."""
+    mp = pytest.importorskip("torch.multiprocessing")
+    mp.spawn(_rank_main, args=(2, _free_port(), str(tmp_path)), nprocs=2, join=True)
+    for r in range(2):
+        assert json.load(open(tmp_path / f"rank{r}.json")) == {"slowest": 3.75}
+
+
+def test_single_rank_helpers_need_no_group():
+    assert bench.aggregate_max(3.25, 1) == 3.25
+    bench.barrier(1)
+
+
+def test_reference_arm_runs_on_rank_zero_only():
+    args = argparse.Namespace(workload="eval-expression", steps=1, warmup=3, impl="reference")
+    assert bench.run_reference(args, 2, 1) is None
+    out = bench.run_reference(args, 2, 0)
+    assert out["impl"] == "reference" and out["n_gpus"] == 2 and out["value"] > 0
+    assert out["metric"] == bench.METRIC and out["unit"] == "tests/s"
+    assert out["cpu_baseline"]["kind"] == "oracle" and out["cpu_baseline"]["value"] == out["value"]
+    assert out["e2e"] == {"value": out["value"], "unit": "tests/s", "h2d_bytes_per_step": 0,
+                          "d2h_bytes_per_step": 0}
+    assert out["config"]["workload"] == "eval-expression-20000x200-P4096-L3-30"
+    json.dumps(out)
+
+
+def _row(bus, sm, mx, stamp, reasons=("Not Active",) * 4):
+    return ", ".join([bus, str(sm), str(mx), "900.0", "0x0", *reasons, stamp])
+
+
+def test_clock_summary_keeps_this_gpu_inside_the_timed_region():
+    t0 = bench.ClockSampler._when("2026/12/03 10:00:00.000")
+    t1 = bench.ClockSampler._when("2026/12/03 10:00:02.000")
+    lines = [
+        _row("00000000:0A:00.0", 1000, 2070, "2026/12/03 09:59:58.000"),      # before
+        _row("00000000:0A:00.0", 2070, 2070, "2026/12/03 10:00:00.500"),
+        _row("00000000:0A:00.0", 2060, 2070, "2026/12/03 10:00:01.000",
+             ("Not Active", "Not Active", "Not Active", "Active")),
+        _row("00000000:0A:00.0", 2070, 2070, "2026/12/03 10:00:01.500"),
+        _row("00000000:1B:00.0", 500, 2070, "2026/12/03 10:00:01.000",         # other GPU
+             ("Active", "Not Active", "Not Active", "Not Active")),
+        _row("00000000:0A:00.0", 300, 2070, "2026/12/03 10:00:09.000"),       # after
+        "malformed line",
+    ]
+    got = bench.ClockSampler.summarize(lines, "00000000:0a:00.0", t0, t1)
+    assert got == {"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": ["sw_power_cap"],
+                   "samples": 3}
+    # without usable stamps every sample of the GPU counts
+    bare = [",".join(line.split(",")[:9]) for line in lines[:4]]
+    got = bench.ClockSampler.summarize(bare, "", t0, t1)
+    assert got["samples"] == 4 and got["sm_mhz"] == 2065.0
+
+
+def test_weak_scaling_workloads_are_seeded_by_rank():
+    """Each rank times its own problem (no data-path collective)."""
+    a, b = bench.GenerationsPaper(0), bench.GenerationsPaper(1)
+    assert a.prob.A.shape == b.prob.A.shape == (1000, 100)
+    assert not np.array_equal(a.prob.A, b.prob.A)
+    assert a.params_kw(10)["seed"] == 0 and b.params_kw(10)["seed"] == 1
+    e0, e1 = bench.EvalExpression(0), bench.EvalExpression(1)
+    assert not np.array_equal(e0.prob.A, e1.prob.A)
+    assert e0.units_per_step() == e1.units_per_step() == 4096 * 20000
