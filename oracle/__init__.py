@@ -103,6 +103,10 @@ def _load():
                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                               _P, _P, _P]
             lib.or_toprank_update.restype = ctypes.c_int32
+            lib.or_screen_attempt.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                              _P, _P, ctypes.c_int32, _P, _P, _P, _P,
+                                              ctypes.c_int32, _P, _P, _P, _P, _P, _P]
+            lib.or_screen_attempt.restype = ctypes.c_int32
             lib.or_run.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.POINTER(Params),
                                    _P, _P, _P, _P, ctypes.POINTER(Stats),
                                    _P, _P, _P, _P, _P, _P, _P, _P, _P]
@@ -268,6 +272,35 @@ def make_params(**kw) -> Params:
     for k, v in d.items():
         setattr(p, k, v)
     return p
+
+
+def screen_attempt(C, g, j, seqs, f, pen, tabu=(), **kw):
+    """One attempt of Step 3 with offspring screening (make_child): attempt j
+    of generation g drawn from the population `seqs` (fitness f, penalty
+    counts pen[C]) against the tabu list `tabu` as it stood at the
+    generation's start.  Returns the candidates, their pseudo scores (V > 1),
+    the tournament outcome and the child."""
+    p = make_params(**kw)
+    V, L = max(1, p.oversample), p.len_max
+    off, cols = to_cbf(seqs)
+    toff, tcols = to_cbf(list(tabu)) if len(tabu) else (np.zeros(1, np.int32),
+                                                        np.zeros(1, np.int32))
+    f = _c(f, np.float64)
+    pen = _c(pen, np.int64)
+    cl = np.zeros(V, np.int32)
+    cc = np.zeros(V * L, np.int32)
+    sc = np.zeros(V, np.uint32)
+    oc = np.zeros(1, np.int32)
+    chl = np.zeros(1, np.int32)
+    chc = np.zeros(L, np.int32)
+    rc = _load().or_screen_attempt(ctypes.byref(p), C, g, j, _ptr(off), _ptr(cols), len(seqs),
+                                   _ptr(f), _ptr(pen), _ptr(toff), _ptr(tcols), len(tabu),
+                                   _ptr(cl), _ptr(cc), _ptr(sc), _ptr(oc), _ptr(chl), _ptr(chc))
+    if rc < 0:
+        raise ValueError("invalid parameters")
+    cands = [cc[v * L:v * L + cl[v]].tolist() for v in range(V)]
+    return {"cands": cands, "scores": sc.tolist(), "outcome": int(oc[0]),
+            "child": chc[:chl[0]].tolist()}
 
 
 def run(A, trace: bool = False, **kw):

@@ -20,9 +20,12 @@
 //                       used for every random draw of the EA)
 //   offspring screening with pseudo scores (make_child, oversample > 1) --
 //                       not in the paper: the test form of the learned
-//                       pre-screen's candidate generation and pick; parity
-//                       unpinned beyond its oversample = 1 case, which is the
-//                       plain algorithm
+//                       pre-screen's candidate generation and pick; pinned by
+//                       properties of its definition on single attempts
+//                       (or_screen_attempt: candidate 0 is the plain child,
+//                       candidates do not depend on V, scores follow the
+//                       Philox counter layout, the pick rule) and by its
+//                       oversample = 1 case, the plain algorithm
 //
 // Where the paper is silent the reading is stated next to the code.  Build
 // flags: -O2 -fno-fast-math -ffp-contract=off (IEEE binary32/binary64,
@@ -289,9 +292,17 @@ Seq mutate(const Seq& s, int32_t C, int32_t Lmin, int32_t Lmax, uint32_t r_type,
 // 8, where c = ta k + tb names the tournament outcome: ta (tb) is the first
 // position in the first (second) tournament holding its winner, tb = 0
 // without crossover.
+// What make_child saw, for the tests: every candidate, its pseudo score
+// (V > 1) and the tournament outcome c.
+struct ScreenTrace {
+  std::vector<Seq> cand;
+  std::vector<uint32_t> score;
+  int32_t outcome = 0;
+};
+
 Seq make_child(const Params& p, int32_t C, int32_t g, int32_t j, const std::vector<Seq>& prev,
                const std::vector<double>& prev_f, const std::vector<int64_t>& pen,
-               const std::set<Seq>& tabu_at_start) {
+               const std::set<Seq>& tabu_at_start, ScreenTrace* tr = nullptr) {
   const int32_t k = p.tournament_k;
   const uint32_t Pprev = (uint32_t)prev.size();
   int32_t ea[8], eb[8];
@@ -320,14 +331,22 @@ Seq make_child(const Params& p, int32_t C, int32_t g, int32_t j, const std::vect
     int32_t kind;
     Seq m = mutate(child, C, p.len_min, p.len_max, draw(p.seed, g, j, base + 2),
                    draw(p.seed, g, j, base + 3), draw(p.seed, g, j, base + 4), &kind);
-    if (V == 1) return m;
     int32_t ta = 0, tb = 0;
     while (ea[ta] != wa) ++ta;
     if (cross)
       while (eb[tb] != wb) ++tb;
     const int32_t c = ta * k + tb;
+    if (tr) tr->outcome = c;
+    if (V == 1) {
+      if (tr) tr->cand.push_back(m);
+      return m;
+    }
     cand.push_back(m);
     score.push_back(draw(p.seed, g, j, 4 * (65536 + c * V + v)) >> 8);
+  }
+  if (tr) {
+    tr->cand = cand;
+    tr->score = score;
   }
   std::vector<int32_t> order((size_t)V);
   for (int32_t v = 0; v < V; ++v) order[v] = v;
@@ -505,6 +524,51 @@ int32_t or_tournament(const int32_t* entrants, int32_t k, const int32_t* offsets
   std::vector<double> fv(f, f + P);
   std::vector<int64_t> pv(pen, pen + C);
   return tournament(entrants, k, pop, fv, pv, base);
+}
+
+// One attempt of Step 3 with offspring screening (test access to
+// make_child): attempt j of generation g drawn from the population given as
+// CBF (offsets, cols; P series) with fitness f and penalty counts pen[C],
+// the tabu list as it stood at the generation's start given as CBF (t_off,
+// t_cols; n_tabu series).  Writes the V = pp->oversample candidates
+// (cand_len[V], cand_cols[V][len_max], padded with -1), their pseudo scores
+// (V > 1), the tournament outcome c and the child.  Returns V, or -1 on
+// invalid parameters.
+int32_t or_screen_attempt(const or_params* pp, int32_t C, int32_t g, int32_t j,
+                          const int32_t* offsets, const int32_t* cols, int32_t P, const double* f,
+                          const int64_t* pen, const int32_t* t_off, const int32_t* t_cols,
+                          int32_t n_tabu, int32_t* cand_len, int32_t* cand_cols,
+                          uint32_t* scores, int32_t* outcome, int32_t* child_len,
+                          int32_t* child_cols) {
+  Params p;
+  p.pop_size = pp->pop_size; p.len_min = pp->len_min; p.len_max = pp->len_max;
+  p.iterations = pp->iterations; p.sigma = pp->sigma; p.toprank_size = pp->toprank_size;
+  p.tournament_k = pp->tournament_k; p.fitness_support = pp->fitness_support;
+  p.overlap_tau = pp->overlap_tau; p.elite_frac = pp->elite_frac;
+  p.penalty_base = pp->penalty_base; p.p_crossover = pp->p_crossover; p.seed = pp->seed;
+  p.oversample = pp->oversample < 1 ? 1 : pp->oversample;
+  if (P < 1 || p.len_min < 1 || p.len_max < p.len_min || p.len_max > C ||
+      p.tournament_k < 1 || p.tournament_k > 4)
+    return -1;
+  std::vector<Seq> prev(P);
+  for (int32_t i = 0; i < P; ++i) prev[i].assign(cols + offsets[i], cols + offsets[i + 1]);
+  std::vector<double> fv(f, f + P);
+  std::vector<int64_t> pv(pen, pen + C);
+  std::set<Seq> tabu;
+  for (int32_t i = 0; i < n_tabu; ++i) tabu.insert(Seq(t_cols + t_off[i], t_cols + t_off[i + 1]));
+  ScreenTrace tr;
+  const Seq child = make_child(p, C, g, j, prev, fv, pv, tabu, &tr);
+  const int32_t V = p.oversample, L = p.len_max;
+  for (int32_t v = 0; v < V; ++v) {
+    cand_len[v] = (int32_t)tr.cand[v].size();
+    for (int32_t c = 0; c < L; ++c)
+      cand_cols[(size_t)v * L + c] = c < (int32_t)tr.cand[v].size() ? tr.cand[v][c] : -1;
+    scores[v] = V > 1 ? tr.score[v] : 0u;
+  }
+  *outcome = tr.outcome;
+  *child_len = (int32_t)child.size();
+  for (int32_t c = 0; c < L; ++c) child_cols[c] = c < (int32_t)child.size() ? child[c] : -1;
+  return V;
 }
 
 // Top-rank update on CBF inputs; the resulting list is written as CBF with
