@@ -748,7 +748,8 @@ __device__ __forceinline__ void hs8(const uint32_t (&v)[8], uint32_t& ones, uint
 }
 
 // Named barrier 1 over the builder's CTA: warp 0 and the helper warps meet
-// there twice per batch (job posted, shares done) and once per chunk (release).
+// there four times per batch (job posted, penalty sums done, children
+// posted, overlap shares done) and once per chunk (release).
 // Eight warps: warp w takes entrant w % 4 of the overlap pass over half
 // w / 4 of the earlier lanes.
 constexpr int kBuildThreads = 256;
@@ -1325,7 +1326,8 @@ __global__ void __launch_bounds__(kBuildThreads, 1) k_build(EaDev d, int hmask, 
   __shared__ Team s_team;                // the fast path's helper-warp protocol
   // fast path: tournaments of at most 2 entrants, column sets of at most 256 bits
   const bool fast = d.k <= 2 && l.nw > 0;
-  // the helper warps take part in the overlap pass (tournaments of 2)
+  // the helper warps share the penalty sums and the overlap pass
+  // (tournaments of 2)
   const bool team = !INIT && fast && d.k == 2;
 
   const int nchunks = (d.J + kB - 1) / kB;
