@@ -1,7 +1,7 @@
 """Host-side logic of bench.py on the CPU: the multi-rank helpers over a
 two-process gloo group, the reference arm's rank handling and JSON line, the
-clock-sample summary, and the per-rank seeding of the weak-scaling
-workloads."""
+clock-sample summary, the per-rank seeding of the weak-scaling workloads,
+and the surrogate comparison's time-to-quality bookkeeping."""
 import argparse
 import json
 import os
@@ -98,3 +98,35 @@ def test_weak_scaling_workloads_are_seeded_by_rank():
     e0, e1 = bench.EvalExpression(0), bench.EvalExpression(1)
     assert not np.array_equal(e0.prob.A, e1.prob.A)
     assert e0.units_per_step() == e1.units_per_step() == 4096 * 20000
+
+
+def test_screened_comparison_scores_time_to_quality():
+    """The surrogate comparison's bookkeeping: generations and seconds (at the
+    arm's rate) to 99% of the plain run's final best, and the summary."""
+    def arm(gps, best, curve):
+        return {"generations_per_s": gps, "generations": len(curve), "final_best_fitness": best,
+                "tabu_hits": 0, "curve": curve}
+    arms = ["plain", "screened", "random_scores"]
+    rows = []
+    for seed, scale in ((0, 1.0), (1, 2.0)):
+        row = {"seed": seed,
+               "plain": arm(1000.0, 10.0 * scale, [scale * x for x in (5.0, 9.0, 9.95, 10.0)]),
+               "screened": arm(500.0, 12.0 * scale, [scale * x for x in (9.9, 11.0, 12.0, 12.0)]),
+               "random_scores": arm(1100.0, 9.0 * scale, [scale * x for x in (5.0, 6.0, 8.0, 9.0)])}
+        rows.append(bench.GenerationsScreened.score_seed(row, arms))
+    for r in rows:
+        assert r["plain"]["generations_to_99pct_of_plain_best"] == 3
+        assert r["plain"]["seconds_to_99pct_of_plain_best"] == pytest.approx(3 / 1000.0)
+        assert r["screened"]["generations_to_99pct_of_plain_best"] == 1
+        assert r["screened"]["seconds_to_99pct_of_plain_best"] == pytest.approx(1 / 500.0)
+        assert r["random_scores"]["generations_to_99pct_of_plain_best"] is None
+        assert r["random_scores"]["seconds_to_99pct_of_plain_best"] is None
+        assert r["screened_best_over_plain_best"] == pytest.approx(1.2)
+        assert "curve" not in r["plain"]
+    out = bench.GenerationsScreened.summarize(rows, arms)
+    assert out["within_1pct_every_seed"] and out["screened_best_over_plain_best_min"] == pytest.approx(1.2)
+    s = out["summary"]
+    assert s["screened"]["mean_seconds_to_99pct_of_plain_best"] == pytest.approx(0.002)
+    assert s["random_scores"]["seeds_reaching_99pct_of_plain_best"] == 0
+    assert s["random_scores"]["mean_seconds_to_99pct_of_plain_best"] is None
+    assert s["plain"]["mean_final_best_fitness"] == pytest.approx(15.0)
