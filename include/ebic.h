@@ -420,9 +420,10 @@ typedef struct ebic_surrogate_ctx* ebic_surrogate;
  * w3 N(0, 1/256), biases 0). */
 ebic_status ebic_surrogate_create(ebic_handle h, int32_t len_scale, uint64_t seed,
                                   ebic_surrogate* out);
-/* Releases the surrogate.  EBIC_ERR_STATE (and nothing is released) while a
- * run of some handle is screening with it: detach it first with
- * ebic_run_screen(h, NULL, 1, EBIC_SCREEN_OFF) or free that handle. */
+/* Releases the surrogate (NULL: nothing to do, EBIC_OK).  EBIC_ERR_STATE (and
+ * nothing is released) while a run of some handle is screening with it:
+ * detach it first with ebic_run_screen(h, NULL, 1, EBIC_SCREEN_OFF) or free
+ * that handle. */
 ebic_status ebic_surrogate_free(ebic_surrogate s);
 /* Reads (write = 0) or replaces (write != 0) the fp32 parameters, layout
  * above.  *n_params = capacity on entry (ignored when host_params is NULL),

@@ -1,6 +1,7 @@
 """CPU-side checks of the boundary: the CUDA library builds for sm_103a, loads,
-and exports every function include/ebic.h declares; the binding fails loudly
-when the library is missing."""
+and exports every function include/ebic.h declares; every entry point that
+takes a handle rejects a null one before any device work; the binding fails
+loudly when the library is missing."""
 import ctypes
 import os
 import subprocess
@@ -55,3 +56,32 @@ def test_binding_fails_loudly_without_library(tmp_path):
 def test_abi_version(libpath):
     L = ctypes.CDLL(libpath)
     assert L.ebic_abi_version() == 1
+
+
+def _null_handle_calls():
+    """(name, argtypes) of every status-returning entry point whose first
+    argument is one of the library's opaque handles."""
+    import re
+    import paper_1801_03039_gb300 as e
+    text = open(os.path.join(ROOT, "include", "ebic.h")).read()
+    names = [m.group(1) for m in re.finditer(
+        r"ebic_status\s+(ebic_\w+)\s*\(\s*(ebic_handle|ebic_batch|ebic_surrogate)\s+\w+", text)]
+    return [(n, e._SIGS[n][0]) for n in names]
+
+
+def test_null_handles_are_rejected_before_any_device_work():
+    """A null handle is an argument error with a message, whatever the
+    rest of the arguments (zeros and null pointers here; no GPU needed)."""
+    import paper_1801_03039_gb300 as e
+    L = e.lib()
+    calls = _null_handle_calls()
+    assert len(calls) >= 30
+    for name, argtypes in calls:
+        args = [0.0 if t in (ctypes.c_double, ctypes.c_float) else 0 for t in argtypes]
+        args[0] = None
+        status = getattr(L, name)(*args)
+        if name == "ebic_surrogate_free":                  # like free(NULL): nothing to do
+            assert status == 0
+            continue
+        assert status == 1, (name, status)                # EBIC_ERR_ARG
+        assert L.ebic_last_error(), name
