@@ -85,3 +85,18 @@ def test_null_handles_are_rejected_before_any_device_work():
             continue
         assert status == 1, (name, status)                # EBIC_ERR_ARG
         assert L.ebic_last_error(), name
+
+
+def test_matrix_shape_and_pointers_are_checked_on_the_host():
+    import numpy as np
+    import paper_1801_03039_gb300 as e
+    L = e.lib()
+    h = ctypes.c_void_p()
+    A = np.zeros((4, 3), np.float32)
+    p = A.ctypes.data_as(ctypes.c_void_p)
+    for args in [(None, 4, 3, ctypes.byref(h)), (p, 4, 3, None), (p, 0, 3, ctypes.byref(h)),
+                 (p, 4, 0, ctypes.byref(h)), (p, 4, 65536, ctypes.byref(h)),
+                 (p, (1 << 26) + 1, 3, ctypes.byref(h))]:
+        assert L.ebic_load_matrix(*args) == 1, args            # EBIC_ERR_ARG
+        assert L.ebic_last_error()
+    assert h.value is None                                     # nothing was created
