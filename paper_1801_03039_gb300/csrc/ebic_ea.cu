@@ -2498,9 +2498,9 @@ static ebic_status graph_launch(EaState* st, cudaStream_t s) {
     const size_t k = 2 * (size_t)(st->tlaunched % st->tslots);
     EBIC_CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(st->exec, st->tnode[0], st->tev[k]));
     EBIC_CUDA_TRY(cudaGraphExecEventRecordNodeSetEvent(st->exec, st->tnode[1], st->tev[k + 1]));
-    st->tlaunched += 1;
   }
   EBIC_CUDA_TRY(cudaGraphLaunch(st->exec, s));
+  if (st->tslots) st->tlaunched += 1;    // a slot counts once its replay is queued
   return EBIC_OK;
 }
 
