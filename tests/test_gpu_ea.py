@@ -251,6 +251,15 @@ def test_wide_matrix_generic_paths():
     run_both(A, iterations=6, len_max=8)
 
 
+def test_eight_word_bitsets():
+    """129-256 columns: the builder's fast path and Step 5's warp visit with
+    eight-word column bitsets (two 16-byte vectors per series)."""
+    rng = np.random.default_rng(11)
+    A = rng.standard_normal((400, 160)).astype(np.float32)
+    run_both(A, gens_to_check={0, 1, 6, 12}, iterations=12, pop_size=300, len_min=2,
+             len_max=10, sigma=8)
+
+
 @pytest.mark.parametrize("P,T", [(37, 3), (300, 250), (1024, 1), (2000, 50)])
 def test_population_and_list_sizes(P, T):
     """Populations that are not powers of two, lists shorter and longer than
