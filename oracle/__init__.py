@@ -103,6 +103,9 @@ def _load():
                                               ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                               _P, _P, _P]
             lib.or_toprank_update.restype = ctypes.c_int32
+            lib.or_rows_approx.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, _P, ctypes.c_int32,
+                                           ctypes.c_int32, ctypes.c_int32, _P]
+            lib.or_rows_approx.restype = ctypes.c_int32
             lib.or_screen_attempt.argtypes = [_P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                               _P, _P, ctypes.c_int32, _P, _P, _P, _P,
                                               ctypes.c_int32, _P, _P, _P, _P, _P, _P]
@@ -239,6 +242,17 @@ def rows(A, seq, mode: int = 0) -> np.ndarray:
     s = np.ascontiguousarray(seq, np.int32)
     out = np.zeros(R, np.int32)
     n = _load().or_rows(_ptr(A), R, C, _ptr(s), len(s), int(mode), _ptr(out))
+    return out[:n].copy()
+
+
+def rows_approx(A, seq, e: int, mode: int = 0) -> np.ndarray:
+    """Step 7 by approximate trends (reading: at most e adjacent pairs of a
+    row break the order): mode 0 rising, mode 1 rising or falling."""
+    A = _c(A, np.float32)
+    R, C = A.shape
+    s = np.ascontiguousarray(seq, np.int32)
+    out = np.zeros(R, np.int32)
+    n = _load().or_rows_approx(_ptr(A), R, C, _ptr(s), len(s), int(e), int(mode), _ptr(out))
     return out[:n].copy()
 
 

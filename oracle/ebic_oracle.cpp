@@ -18,6 +18,9 @@
 //   Philox-4x32-10   -- Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
 //                       as easy as 1, 2, 3", SC'11 (the counter-based generator
 //                       used for every random draw of the EA)
+//   Step 7 expansion by approximate trends (or_rows_approx) -- the reading
+//                       that at most e adjacent pairs of a row may break the
+//                       order (the paper does not define "approximate")
 //   offspring screening with pseudo scores (make_child, oversample > 1) --
 //                       not in the paper: the test form of the learned
 //                       pre-screen's candidate generation and pick; pinned by
@@ -459,6 +462,27 @@ int32_t or_rows(const float* A, int32_t R, int32_t C, const int32_t* s, int32_t 
       if (!(row[s[i]] > row[s[i + 1]])) falling = false;
     }
     if (rising || (mode == 1 && falling)) out_rows[n++] = k;
+  }
+  return n;
+}
+
+// Step 7's expansion by approximate trends (the paper leaves "approximate"
+// undefined; reading: a row follows the series approximately when at most e
+// of its L - 1 adjacent pairs break the order).  Mode 0: at most e pairs
+// that do not rise strictly; mode 1: that, or at most e pairs that do not
+// fall strictly.  e = 0 is or_rows.  Row indices ascending into out_rows;
+// returns their number.
+int32_t or_rows_approx(const float* A, int32_t R, int32_t C, const int32_t* s, int32_t L,
+                       int32_t e, int32_t mode, int32_t* out_rows) {
+  int32_t n = 0;
+  for (int32_t k = 0; k < R; ++k) {
+    const float* row = A + (size_t)k * (size_t)C;
+    int32_t not_up = 0, not_down = 0;
+    for (int32_t i = 0; i + 1 < L; ++i) {
+      if (!(row[s[i]] < row[s[i + 1]])) ++not_up;
+      if (!(row[s[i]] > row[s[i + 1]])) ++not_down;
+    }
+    if (not_up <= e || (mode == 1 && not_down <= e)) out_rows[n++] = k;
   }
   return n;
 }

@@ -71,3 +71,70 @@ def test_recovery_relevance_hand():
     rec, rel = oracle.recovery_relevance([e1], [g])
     assert rec == pytest.approx(10 / 60) and rel == pytest.approx(10 / 60)
     assert oracle.recovery_relevance([], [e1]) == (0.0, 0.0)
+
+
+# ---------------------------------------------------------------------------
+# Step 7 by approximate trends (reading: at most e adjacent pairs of a row may
+# break the order).  Over the L! orderings of L columns, the rows with exactly
+# v pairs out of order (descents) number the Eulerian number A(L, v).
+def _eulerian(n):
+    a = [1]                                   # A(1, 0) = 1
+    for m in range(2, n + 1):                 # A(m, k) = (k+1) A(m-1, k) + (m-k) A(m-1, k-1)
+        a = [(k + 1) * (a[k] if k < len(a) else 0) + (m - k) * (a[k - 1] if k >= 1 else 0)
+             for k in range(m)]
+    return a
+
+
+def _all_orderings(L):
+    import itertools
+    return np.array(list(itertools.permutations(range(L))), np.float32)
+
+
+def test_eulerian_numbers_are_the_textbook_ones():
+    assert _eulerian(4) == [1, 11, 11, 1]
+    assert _eulerian(5) == [1, 26, 66, 26, 1]
+    assert sum(_eulerian(6)) == 720
+
+
+@pytest.mark.parametrize("L", [2, 3, 4, 5, 6])
+def test_approximate_rows_count_by_descents(L):
+    A = _all_orderings(L)
+    seq = list(range(L))
+    eul = _eulerian(L)
+    for e in range(L):
+        rising = oracle.rows_approx(A, seq, e, 0)
+        assert len(rising) == sum(eul[:e + 1])
+        # rising or falling: at most e descents or at most e ascents
+        want = sum(eul[v] for v in range(L) if v <= e or (L - 1 - v) <= e)
+        assert len(oracle.rows_approx(A, seq, e, 1)) == want
+
+
+def test_approximate_rows_reduce_to_step6_and_nest():
+    rng = np.random.default_rng(3)
+    A = rng.integers(-2, 3, (300, 9)).astype(np.float32)     # many ties
+    A[rng.random(A.shape) < 0.03] = np.nan
+    for _ in range(40):
+        seq = rng.choice(9, int(rng.integers(1, 7)), replace=False).tolist()
+        for mode in (0, 1):
+            prev = oracle.rows_approx(A, seq, 0, mode)
+            assert prev.tolist() == oracle.rows(A, seq, mode).tolist()
+            for e in range(1, len(seq)):
+                cur = oracle.rows_approx(A, seq, e, mode)
+                assert set(prev.tolist()) <= set(cur.tolist())
+                assert np.all(np.diff(cur) > 0)
+                prev = cur
+            # every pair may break: every row
+            assert len(oracle.rows_approx(A, seq, max(len(seq) - 1, 0), mode)) == 300
+
+
+def test_approximate_rows_ties_and_nan_break_both_directions():
+    A = np.array([[1.0, 1.0, 1.0],          # ties: no pair rises or falls
+                  [1.0, np.nan, 3.0],       # NaN: no pair compares
+                  [1.0, 2.0, 3.0],          # rising
+                  [3.0, 2.0, 1.0],          # falling
+                  [1.0, 3.0, 2.0]], np.float32)
+    seq = [0, 1, 2]
+    assert oracle.rows_approx(A, seq, 0, 1).tolist() == [2, 3]
+    assert oracle.rows_approx(A, seq, 1, 0).tolist() == [2, 4]
+    assert oracle.rows_approx(A, seq, 1, 1).tolist() == [2, 3, 4]
+    assert oracle.rows_approx(A, seq, 2, 0).tolist() == [0, 1, 2, 3, 4]
