@@ -356,8 +356,8 @@ ebic_status ebic_run_generations(ebic_handle h, const ebic_params_t* p, int32_t*
  * EBIC_ROWS_RISING: the rows whose values rise strictly along the series (the
  * support of Step 4, as a list).  EBIC_ROWS_RISING_OR_FALLING: also the rows
  * that fall strictly along it (negative trends).  A one-column series matches
- * every row.  The expansion by "approximate" trends is not defined by the
- * paper and is not offered.
+ * every row.  Step 7's expansion by "approximate" trends, which the paper does
+ * not define, is ebic_extract_rows_approx below under a stated reading.
  *
  * offsets / cols: a CBF population as for ebic_eval_population (host).
  * row_offsets[P + 1] (host, int64) and rows (host): the row indices of series
@@ -373,6 +373,17 @@ typedef enum {
 ebic_status ebic_extract_rows(ebic_handle h, const int32_t* offsets, const int32_t* cols,
                               int32_t P, int32_t mode, int64_t* row_offsets, int32_t* rows,
                               int64_t* inout_capacity);
+/* Step 7's expansion by approximate trends, read as: a row follows a series
+ * approximately when at most max_breaks of its L - 1 adjacent pairs do not
+ * rise strictly (EBIC_ROWS_RISING_OR_FALLING: or at most max_breaks do not
+ * fall strictly).  Ties and NaN break a pair in both directions.
+ * max_breaks = 0 gives the rows of ebic_extract_rows.  Arguments, output and
+ * errors as for ebic_extract_rows; EBIC_ERR_ARG unless 0 <= max_breaks <=
+ * EBIC_MAX_EVAL_LEN. */
+ebic_status ebic_extract_rows_approx(ebic_handle h, const int32_t* offsets, const int32_t* cols,
+                                     int32_t P, int32_t max_breaks, int32_t mode,
+                                     int64_t* row_offsets, int32_t* rows,
+                                     int64_t* inout_capacity);
 
 /* Recovery and relevance, Eq. (2)-(3): a bicluster is the set of cells rows x
  * columns and the Jaccard index of two biclusters is |e & f| / |e | f| over

@@ -36,7 +36,7 @@ __all__ = [
     "ebic_surrogate_colstats", "ebic_surrogate_step", "ebic_surrogate_log", "ebic_surrogate_train",
     "ebic_surrogate_target_norm", "ebic_surrogate_predict", "ebic_run_screen",
     "SCREEN_OFF", "SCREEN_SURROGATE", "SCREEN_PSEUDO",
-    "ebic_extract_rows", "ebic_recovery_relevance", "ROWS_RISING", "ROWS_RISING_OR_FALLING",
+    "ebic_extract_rows", "ebic_extract_rows_approx", "ebic_recovery_relevance", "ROWS_RISING", "ROWS_RISING_OR_FALLING",
 ]
 
 PATH_AUTO, PATH_GATHER, PATH_BITMASK = 0, 1, 2
@@ -126,6 +126,7 @@ _SIGS = {
     "ebic_surrogate_predict": ([_P, _P, _P, _I32, ctypes.c_int64, _P, _P], _I32),
     "ebic_run_screen": ([_P, _P, _I32, _I32], _I32),
     "ebic_extract_rows": ([_P, _P, _P, _I32, _I32, _P, _P, _P], _I32),
+    "ebic_extract_rows_approx": ([_P, _P, _P, _I32, _I32, _I32, _P, _P, _P], _I32),
     "ebic_recovery_relevance": ([_I32, _P, _P, _P, _P, _I32, _P, _P, _P, _P, _P, _P, _P], _I32),
 }
 
@@ -540,21 +541,32 @@ def ebic_run_screen(h, s=None, oversample: int = 1, mode: int = SCREEN_OFF):
 
 # ---------------------------------------------------------------------------
 # Step 6 rows and Step 7 negative-trend expansion; Eq. (2)-(3)
-def ebic_extract_rows(h, offsets, cols, mode: int = ROWS_RISING):
-    """Rows matching each series of a CBF population: list of int32 arrays."""
+def _extract(call, offsets, cols):
+    """Two calls of a rows entry point: the first sizes the buffer."""
     off, po = _host(offsets, np.int32)
     c, pc = _host(cols, np.int32)
     P = len(off) - 1
     roff = np.zeros(P + 1, np.int64)
     cap = ctypes.c_int64(0)
-    st = lib().ebic_extract_rows(h, po, pc, P, int(mode), roff.ctypes.data_as(_P), None,
-                                 ctypes.byref(cap))
+    st = call(po, pc, P, roff.ctypes.data_as(_P), None, ctypes.byref(cap))
     if st != 0 and cap.value == 0 and P > 0:
         _check(st)
     rows = np.zeros(max(1, cap.value), np.int32)
-    _check(lib().ebic_extract_rows(h, po, pc, P, int(mode), roff.ctypes.data_as(_P),
-                                   rows.ctypes.data_as(_P), ctypes.byref(cap)))
+    _check(call(po, pc, P, roff.ctypes.data_as(_P), rows.ctypes.data_as(_P), ctypes.byref(cap)))
     return [rows[roff[i]:roff[i + 1]].copy() for i in range(P)]
+
+
+def ebic_extract_rows(h, offsets, cols, mode: int = ROWS_RISING):
+    """Rows matching each series of a CBF population: list of int32 arrays."""
+    return _extract(lambda po, pc, P, ro, rw, cap: lib().ebic_extract_rows(
+        h, po, pc, P, int(mode), ro, rw, cap), offsets, cols)
+
+
+def ebic_extract_rows_approx(h, offsets, cols, max_breaks: int, mode: int = ROWS_RISING):
+    """Rows following each series with at most max_breaks broken adjacent
+    pairs (Step 7 by approximate trends): list of int32 arrays."""
+    return _extract(lambda po, pc, P, ro, rw, cap: lib().ebic_extract_rows_approx(
+        h, po, pc, P, int(max_breaks), int(mode), ro, rw, cap), offsets, cols)
 
 
 def _csr(lists):

@@ -15,17 +15,20 @@ namespace ebic {
 // Rows of a series.  One CTA per series walks the column-major matrix in
 // chunks of 1,024 rows, each thread four consecutive rows (one float4 per
 // column): a row is kept when its values rise strictly along the series (or,
-// mode 1, rise or fall strictly).  The counting launch writes the number of
-// kept rows; the writing launch stores their indices, ascending, from
-// row_off[series] on (a block-wide scan orders them).
+// mode 1, rise or fall strictly).  With APPROX a row is kept when at most
+// `breaks` of its adjacent pairs do not rise strictly (mode 1: or at most
+// `breaks` do not fall strictly), counted per row.  The counting launch
+// writes the number of kept rows; the writing launch stores their indices,
+// ascending, from row_off[series] on (a block-wide scan orders them).
 // ---------------------------------------------------------------------------
 constexpr int kRowThreads = 256;
 
-template <bool WRITE>
+template <bool WRITE, bool APPROX>
 __global__ void __launch_bounds__(kRowThreads)
 k_rows(const float* __restrict__ A_c, int32_t R, int32_t R_pad, const int32_t* __restrict__ off,
-       const int32_t* __restrict__ cols, int32_t mode, int32_t* __restrict__ counts,
-       const long long* __restrict__ row_off, int32_t* __restrict__ rows) {
+       const int32_t* __restrict__ cols, int32_t mode, int32_t breaks,
+       int32_t* __restrict__ counts, const long long* __restrict__ row_off,
+       int32_t* __restrict__ rows) {
   __shared__ int s_warp[kRowThreads / 32];
   const int sid = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -37,12 +40,30 @@ k_rows(const float* __restrict__ A_c, int32_t R, int32_t R_pad, const int32_t* _
     uint32_t keep = 0u;
     if (r < R_pad) {
       uint32_t rise = 0xFu, fall = 0xFu;
+      int up_breaks[4] = {0, 0, 0, 0}, down_breaks[4] = {0, 0, 0, 0};
       float4 prev = *reinterpret_cast<const float4*>(A_c + (size_t)cols[b] * R_pad + r);
       for (int i = 1; i < L; ++i) {
         const float4 cur = *reinterpret_cast<const float4*>(A_c + (size_t)cols[b + i] * R_pad + r);
-        rise &= lt4(prev, cur);
-        fall &= gt4(prev, cur);
+        const uint32_t up = lt4(prev, cur), down = gt4(prev, cur);
+        if (APPROX) {
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            up_breaks[j] += ((up >> j) & 1u) ? 0 : 1;
+            down_breaks[j] += ((down >> j) & 1u) ? 0 : 1;
+          }
+        } else {
+          rise &= up;
+          fall &= down;
+        }
         prev = cur;
+      }
+      if (APPROX) {
+        rise = fall = 0u;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          rise |= up_breaks[j] <= breaks ? 1u << j : 0u;
+          fall |= down_breaks[j] <= breaks ? 1u << j : 0u;
+        }
       }
       const uint32_t valid = (r < R ? 1u : 0u) | (r + 1 < R ? 2u : 0u) | (r + 2 < R ? 4u : 0u) |
                              (r + 3 < R ? 8u : 0u);
@@ -183,9 +204,11 @@ bool strictly_ascending(const int32_t* v, long long n, int32_t bound) {
 
 extern "C" {
 
-ebic_status ebic_extract_rows(ebic_handle h, const int32_t* offsets, const int32_t* cols,
-                              int32_t P, int32_t mode, int64_t* row_offsets, int32_t* rows,
-                              int64_t* inout_capacity) {
+// Steps 6 / 7 for ebic_extract_rows (breaks < 0: strict trends) and
+// ebic_extract_rows_approx (at most `breaks` broken pairs per row).
+static ebic_status extract_rows(ebic_handle h, const int32_t* offsets, const int32_t* cols,
+                                int32_t P, int32_t mode, int32_t breaks, int64_t* row_offsets,
+                                int32_t* rows, int64_t* inout_capacity) {
   if (!h) return fail(EBIC_ERR_ARG, "null handle");
   if (P < 0 || P > (1 << 24)) return fail(EBIC_ERR_ARG, "P = %d outside [0, 2^24]", P);
   if (!offsets || !row_offsets || !inout_capacity || *inout_capacity < 0)
@@ -231,9 +254,14 @@ ebic_status ebic_extract_rows(ebic_handle h, const int32_t* offsets, const int32
       st = fail(EBIC_ERR_CUDA, "copy of the series failed");
       break;
     }
-    k_rows<false><<<(unsigned)P, kRowThreads, 0, s>>>(h->A_c, h->R, h->R_pad, d_off.as<int32_t>(),
-                                                     d_cols.as<int32_t>(), mode,
-                                                     d_cnt.as<int32_t>(), nullptr, nullptr);
+    if (breaks < 0)
+      k_rows<false, false><<<(unsigned)P, kRowThreads, 0, s>>>(
+          h->A_c, h->R, h->R_pad, d_off.as<int32_t>(), d_cols.as<int32_t>(), mode, 0,
+          d_cnt.as<int32_t>(), nullptr, nullptr);
+    else
+      k_rows<false, true><<<(unsigned)P, kRowThreads, 0, s>>>(
+          h->A_c, h->R, h->R_pad, d_off.as<int32_t>(), d_cols.as<int32_t>(), mode, breaks,
+          d_cnt.as<int32_t>(), nullptr, nullptr);
     count_launches(1);
     if (cudaMemcpyAsync(cnt.data(), d_cnt.ptr, (size_t)P * sizeof(int32_t),
                         cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -264,10 +292,14 @@ ebic_status ebic_extract_rows(ebic_handle h, const int32_t* offsets, const int32
         st = fail(EBIC_ERR_CUDA, "copy of the row offsets failed");
         break;
       }
-      k_rows<true><<<(unsigned)P, kRowThreads, 0, s>>>(h->A_c, h->R, h->R_pad,
-                                                      d_off.as<int32_t>(), d_cols.as<int32_t>(),
-                                                      mode, nullptr, d_roff.as<long long>(),
-                                                      d_rows.as<int32_t>());
+      if (breaks < 0)
+        k_rows<true, false><<<(unsigned)P, kRowThreads, 0, s>>>(
+            h->A_c, h->R, h->R_pad, d_off.as<int32_t>(), d_cols.as<int32_t>(), mode, 0, nullptr,
+            d_roff.as<long long>(), d_rows.as<int32_t>());
+      else
+        k_rows<true, true><<<(unsigned)P, kRowThreads, 0, s>>>(
+            h->A_c, h->R, h->R_pad, d_off.as<int32_t>(), d_cols.as<int32_t>(), mode, breaks,
+            nullptr, d_roff.as<long long>(), d_rows.as<int32_t>());
       count_launches(1);
       if (cudaMemcpyAsync(rows, d_rows.ptr, (size_t)need * sizeof(int32_t),
                           cudaMemcpyDeviceToHost, s) != cudaSuccess ||
@@ -283,6 +315,22 @@ ebic_status ebic_extract_rows(ebic_handle h, const int32_t* offsets, const int32
   for (int32_t i = 0; i <= P; ++i) row_offsets[i] = roff[i];
   *inout_capacity = need;
   return EBIC_OK;
+}
+
+ebic_status ebic_extract_rows(ebic_handle h, const int32_t* offsets, const int32_t* cols,
+                              int32_t P, int32_t mode, int64_t* row_offsets, int32_t* rows,
+                              int64_t* inout_capacity) {
+  return extract_rows(h, offsets, cols, P, mode, -1, row_offsets, rows, inout_capacity);
+}
+
+ebic_status ebic_extract_rows_approx(ebic_handle h, const int32_t* offsets, const int32_t* cols,
+                                     int32_t P, int32_t max_breaks, int32_t mode,
+                                     int64_t* row_offsets, int32_t* rows,
+                                     int64_t* inout_capacity) {
+  if (!h) return fail(EBIC_ERR_ARG, "null handle");
+  if (max_breaks < 0 || max_breaks > EBIC_MAX_EVAL_LEN)
+    return fail(EBIC_ERR_ARG, "max_breaks = %d outside [0, %d]", max_breaks, EBIC_MAX_EVAL_LEN);
+  return extract_rows(h, offsets, cols, P, mode, max_breaks, row_offsets, rows, inout_capacity);
 }
 
 ebic_status ebic_recovery_relevance(int32_t E, const int64_t* e_row_off, const int32_t* e_rows,

@@ -100,3 +100,35 @@ def test_matrix_shape_and_pointers_are_checked_on_the_host():
         assert L.ebic_load_matrix(*args) == 1, args            # EBIC_ERR_ARG
         assert L.ebic_last_error()
     assert h.value is None                                     # nothing was created
+
+
+def test_rows_binding_sizes_then_fills():
+    """The binding's two-call protocol of the rows entry points (first call
+    sizes the buffer, second fills it), against a fake that follows the
+    header's contract."""
+    import numpy as np
+    import paper_1801_03039_gb300 as e
+    want = [[0, 3, 5], [], [1, 2]]
+    calls = []
+
+    def fake(po, pc, P, ro, rw, cap):
+        need = sum(len(w) for w in want)
+        calls.append(cap._obj.value)
+        if rw is None or cap._obj.value < need:
+            cap._obj.value = need
+            return 1                                   # EBIC_ERR_ARG, size in *cap
+        roff = np.ctypeslib.as_array(ctypes.cast(ro, ctypes.POINTER(ctypes.c_int64)), (P + 1,))
+        rows = np.ctypeslib.as_array(ctypes.cast(rw, ctypes.POINTER(ctypes.c_int32)), (need,))
+        k = 0
+        for i, w in enumerate(want):
+            roff[i] = k
+            rows[k:k + len(w)] = w
+            k += len(w)
+        roff[P] = k
+        cap._obj.value = k
+        return 0
+
+    off = np.array([0, 2, 3, 5], np.int32)
+    cols = np.array([0, 1, 2, 0, 1], np.int32)
+    got = e._extract(fake, off, cols)
+    assert [g.tolist() for g in got] == want and calls == [0, 5]

@@ -1,6 +1,6 @@
-"""Step 6 rows, Step 7 negative-trend expansion and Eq. (2)-(3) on the GPU
-against the oracle (exact), and a recovery / relevance check of whole EBIC
-runs on planted biclusters."""
+"""Step 6 rows, Step 7's expansions by negative and by approximate trends and
+Eq. (2)-(3) on the GPU against the oracle (exact), and a recovery /
+relevance check of whole EBIC runs on planted biclusters."""
 import json
 import os
 
@@ -65,6 +65,40 @@ def test_rows_match_oracle(shape):
         inc, dec, _ = eb.ebic_eval_population(h, off, cols, 10, 1, want_dec=True)
         got = eb.ebic_extract_rows(h, off, cols, eb.ROWS_RISING)
         assert [len(g) for g in got] == inc.tolist()
+    finally:
+        eb.ebic_free(h)
+
+
+@pytest.mark.parametrize("shape", [(37, 6), (1000, 30), (4099, 64)])
+def test_approximate_rows_match_oracle(shape):
+    """Step 7 by approximate trends (at most e broken adjacent pairs per row)
+    against the oracle, both modes, e = 0 included (the rows of Step 6)."""
+    R, C = shape
+    rng = np.random.default_rng(R + 1)
+    if R < 100:
+        A = rng.integers(-2, 3, (R, C)).astype(np.float32)
+        A[rng.random(A.shape) < 0.05] = np.nan
+        seqs = [rng.choice(C, int(rng.integers(1, 6)), replace=False).tolist() for _ in range(60)]
+    else:
+        prob = synth.matrix_random(R, R, C, n_plants=3, plant_rows=(R // 20, R // 8),
+                                   plant_cols=(3, 10))
+        A = prob.A
+        off, cols = synth.population(R, 80, C, 1, 12, plants=prob.plants)
+        seqs = [cols[off[i]:off[i + 1]].tolist() for i in range(len(off) - 1)]
+    off, cols = _cbf(seqs)
+    h = eb.ebic_load_matrix(A)
+    try:
+        for mode in (eb.ROWS_RISING, eb.ROWS_RISING_OR_FALLING):
+            exact = eb.ebic_extract_rows(h, off, cols, mode)
+            for e in (0, 1, 2, 5):
+                got = eb.ebic_extract_rows_approx(h, off, cols, e, mode)
+                for s, g in zip(seqs, got):
+                    assert g.tolist() == oracle.rows_approx(A, s, e, mode).tolist(), (s, e, mode)
+                if e == 0:
+                    assert [g.tolist() for g in got] == [x.tolist() for x in exact]
+        for bad in (-1, 1025):
+            with pytest.raises(eb.EbicError):
+                eb.ebic_extract_rows_approx(h, off, cols, bad)
     finally:
         eb.ebic_free(h)
 
