@@ -27,8 +27,9 @@ import numpy as np
 class Plant:
     rows: np.ndarray          # planted row indices
     order: np.ndarray         # columns in increasing-value order
-    kind: str                 # "op", "shift", "scale"
+    kind: str                 # "op", "shift", "scale", or a benchmark pattern name
     reversed: bool = False
+    cols: np.ndarray = None   # the plant's columns, ascending (when order is empty)
 
 
 @dataclass
@@ -120,6 +121,78 @@ def matrix_overlap(seed: int = 0, overlap: int = 0, noise: float = 0.01) -> Prob
         r0 += 20 - overlap
         c0 += 20 - overlap
     return Problem(f"overlap-200x150-{overlap}", A.astype(np.float32), plants, sigma=10)
+
+
+PATTERNS = ("trend-preserving", "column-constant", "row-constant", "shift", "scale",
+            "shift-scale")
+PATTERN_SIZES = {"150x100": (150, 100, 3, 15), "200x150": (200, 150, 4, 20),
+                 "300x200": (300, 200, 5, 25)}
+
+
+def _plant_pattern(rng, A, pr, pc, pattern):
+    """Cells of one bicluster of the given pattern; returns its Plant (``order``:
+    the columns along which its rows rise; empty for row-constant, whose rows
+    are flat)."""
+    nr, nc = len(pr), len(pc)
+    if pattern == "trend-preserving":
+        plant = _plant_op(rng, A, pr, pc, 0.0)
+        plant.kind = pattern
+        return plant
+    cj = rng.standard_normal(nc)
+    if pattern == "column-constant":
+        A[np.ix_(pr, pc)] = np.broadcast_to(cj[None, :], (nr, nc))
+    elif pattern == "row-constant":
+        A[np.ix_(pr, pc)] = np.broadcast_to(rng.standard_normal(nr)[:, None], (nr, nc))
+        return Plant(rows=np.sort(pr), order=np.zeros(0, np.int64), kind=pattern,
+                     cols=np.sort(pc))
+    elif pattern == "shift":
+        A[np.ix_(pr, pc)] = rng.standard_normal(nr)[:, None] + cj[None, :]
+    elif pattern == "scale":
+        A[np.ix_(pr, pc)] = rng.uniform(0.5, 2.0, nr)[:, None] * cj[None, :]
+    elif pattern == "shift-scale":
+        A[np.ix_(pr, pc)] = (rng.uniform(0.5, 2.0, nr)[:, None] * cj[None, :] +
+                             rng.standard_normal(nr)[:, None])
+    else:
+        raise ValueError(pattern)
+    return Plant(rows=np.sort(pr), order=pc[np.argsort(cj, kind="stable")], kind=pattern)
+
+
+def matrix_pattern(seed: int = 0, pattern: str = "trend-preserving", size: str = "150x100",
+                   noise: float = 0.0) -> Problem:
+    """The pattern-discovery shapes of the paper's synthetic benchmark: N(0,1)
+    background with disjoint square biclusters of one pattern -- 3 of 15 x 15
+    in 150 x 100, 4 of 20 x 20 in 200 x 150, 5 of 25 x 25 in 300 x 200.
+    Patterns: trend-preserving (sorted draws along a random column order),
+    column-constant (c_j), row-constant (r_i: no column order), shift
+    (r_i + c_j), scale (r_i c_j, r_i in [0.5, 2]), shift-scale (r_i c_j + s_i).
+    N(0, noise^2) is added to every cell of the matrix afterwards (the noise
+    sweep; noise is a standard deviation)."""
+    R, C, n, w = PATTERN_SIZES[size]
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((R, C)).astype(np.float64)
+    rows = rng.permutation(R)
+    cols = rng.permutation(C)
+    plants = [_plant_pattern(rng, A, rows[b * w:(b + 1) * w], cols[b * w:(b + 1) * w], pattern)
+              for b in range(n)]
+    if noise > 0:
+        A += rng.standard_normal(A.shape) * noise
+    return Problem(f"{pattern}-{size}", A.astype(np.float32), plants, sigma=max(5, w // 2))
+
+
+def matrix_narrow(seed: int = 0, width: int = 10, noise: float = 0.0) -> Problem:
+    """The narrow-bicluster shape of the paper's benchmark: 1000 x 100, N(0,1)
+    background, three disjoint trend-preserving biclusters of 100 rows and
+    ``width`` (10, 20 or 30) columns."""
+    rng = np.random.default_rng(seed)
+    R, C = 1000, 100
+    A = rng.standard_normal((R, C)).astype(np.float64)
+    rows = rng.permutation(R)
+    cols = rng.permutation(C)
+    plants = [_plant_op(rng, A, rows[b * 100:(b + 1) * 100], cols[b * width:(b + 1) * width], 0.0)
+              for b in range(3)]
+    if noise > 0:
+        A += rng.standard_normal(A.shape) * noise
+    return Problem(f"narrow-1000x100-{width}", A.astype(np.float32), plants, sigma=50)
 
 
 def matrix_expression(seed: int = 0, R: int = 20000, C: int = 200, n_plants: int = 10,
