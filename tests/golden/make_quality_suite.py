@@ -1,0 +1,90 @@
+"""Writes quality_suite.json: recovery and relevance (Eq. (2)-(3)) of whole
+EBIC searches on the seeded synthetic benchmark shapes (the pattern suite, the
+narrow biclusters and a noise sweep), computed with the CPU oracle only --
+the search (Steps 1-5), the rows of the found biclusters with the
+negative-trend expansion (Steps 6-7) and the scores.  The device path is
+bit-identical to the oracle on these searches, so the stored figures are also
+the device's.  Found biclusters: the best top-rank series, as many as there
+are planted biclusters.
+
+    python tests/golden/make_quality_suite.py [--generations 2000] [--jobs 16]
+"""
+import argparse
+import json
+import os
+import sys
+from concurrent.futures import ProcessPoolExecutor
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(os.path.dirname(HERE))
+sys.path.insert(0, ROOT)
+
+
+def cases():
+    out = []
+    for size in ("150x100", "200x150", "300x200"):
+        for pattern in ("trend-preserving", "column-constant", "row-constant", "shift", "scale",
+                        "shift-scale"):
+            out.append({"suite": "pattern", "pattern": pattern, "size": size, "noise": 0.0})
+    for width in (10, 20, 30):
+        out.append({"suite": "narrow", "width": width, "noise": 0.0})
+    for noise in (0.05, 0.1, 0.25):
+        out.append({"suite": "pattern", "pattern": "trend-preserving", "size": "200x150",
+                    "noise": noise})
+    return out
+
+
+def problem(case):
+    from paper_1801_03039_gb300 import synth
+    if case["suite"] == "narrow":
+        return synth.matrix_narrow(0, case["width"], case["noise"])
+    return synth.matrix_pattern(0, case["pattern"], case["size"], case["noise"])
+
+
+def params(case, prob, generations):
+    width = max(len(pl.cols if pl.cols is not None else pl.order) for pl in prob.plants)
+    return dict(pop_size=600, len_min=3, len_max=min(prob.A.shape[1], width + 5),
+                iterations=generations, sigma=prob.sigma, toprank_size=100, tournament_k=2,
+                overlap_tau=0.5, elite_frac=0.25, penalty_base=1.2, p_crossover=0.5, seed=0)
+
+
+def run_case(args):
+    case, generations = args
+    import numpy as np
+    import oracle
+    prob = problem(case)
+    kw = params(case, prob, generations)
+    res = oracle.run(prob.A, **kw)
+    expected = [(np.sort(pl.rows), np.sort(pl.cols if pl.cols is not None else pl.order))
+                for pl in prob.plants]
+    top = res["toprank"][:len(expected)]
+    found = [(oracle.rows(prob.A, t, 1), np.sort(np.asarray(t, np.int64))) for t in top]
+    rec, rel = oracle.recovery_relevance(expected, found)
+    return {**case, "problem": prob.name, "params": kw,
+            "generations_done": res["stats"]["generations_done"],
+            "stop_reason": res["stats"]["stop_reason"], "recovery": rec, "relevance": rel}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--generations", type=int, default=2000)
+    ap.add_argument("--jobs", type=int, default=os.cpu_count() or 1)
+    a = ap.parse_args()
+    import oracle
+    oracle.build()
+    todo = [(c, a.generations) for c in cases()]
+    import multiprocessing as mp
+    with ProcessPoolExecutor(a.jobs, mp_context=mp.get_context("spawn")) as ex:
+        rows = list(ex.map(run_case, todo))
+    out = {"generator": "tests/golden/make_quality_suite.py", "generations": a.generations,
+           "cases": rows}
+    with open(os.path.join(HERE, "quality_suite.json"), "w") as f:
+        json.dump(out, f, indent=1)
+    for r in rows:
+        name = r["problem"] + (f" noise {r['noise']}" if r["noise"] else "")
+        print(f"{name:40s} recovery {r['recovery']:.3f} relevance {r['relevance']:.3f} "
+              f"({r['generations_done']} generations, stop {r['stop_reason']})")
+
+
+if __name__ == "__main__":
+    main()
