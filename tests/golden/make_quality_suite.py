@@ -2,7 +2,9 @@
 EBIC searches on the seeded synthetic benchmark shapes (the pattern suite, the
 narrow biclusters and a noise sweep), computed with the CPU oracle only --
 the search (Steps 1-5), the rows of the found biclusters with the
-negative-trend expansion (Steps 6-7) and the scores.  The device path is
+negative-trend expansion (Steps 6-7) and the scores; also the scores with
+the expansion by approximate trends (at most 1 or 2 broken adjacent pairs per
+row) of the same found series.  The device path is
 bit-identical to the oracle on these searches, so the stored figures are also
 the device's.  Found biclusters: the best top-rank series, as many as there
 are planted biclusters.
@@ -60,9 +62,16 @@ def run_case(args):
     top = res["toprank"][:len(expected)]
     found = [(oracle.rows(prob.A, t, 1), np.sort(np.asarray(t, np.int64))) for t in top]
     rec, rel = oracle.recovery_relevance(expected, found)
+    # the same found series expanded by approximate trends (at most e broken
+    # adjacent pairs per row)
+    approx = {}
+    for e in (1, 2):
+        fe = [(oracle.rows_approx(prob.A, t, e, 1), np.sort(np.asarray(t, np.int64))) for t in top]
+        approx[str(e)] = oracle.recovery_relevance(expected, fe)
     return {**case, "problem": prob.name, "params": kw,
             "generations_done": res["stats"]["generations_done"],
-            "stop_reason": res["stats"]["stop_reason"], "recovery": rec, "relevance": rel}
+            "stop_reason": res["stats"]["stop_reason"], "recovery": rec, "relevance": rel,
+            "approximate_trends": approx}
 
 
 def main():

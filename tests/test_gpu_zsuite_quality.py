@@ -1,8 +1,9 @@
 """Whole EBIC searches on the seeded benchmark shapes (the paper's pattern
 suite, narrow biclusters, a noise sweep) on the GPU: the search, the rows of
-the found biclusters with the negative-trend expansion and Eq. (2)-(3) give
-the recovery and relevance the oracle gives (tests/golden/quality_suite.json,
-written by make_quality_suite.py from the oracle only)."""
+the found biclusters with the negative-trend expansion (and with the
+approximate-trend expansion) and Eq. (2)-(3) give the recovery and relevance
+the oracle gives (tests/golden/quality_suite.json, written by
+make_quality_suite.py from the oracle only)."""
 import json
 import os
 
@@ -48,9 +49,17 @@ def test_search_quality_matches_the_oracle(case):
         rows = eb.ebic_extract_rows(h, off, flat, eb.ROWS_RISING_OR_FALLING)
         found = [(r, np.sort(np.asarray(t))) for r, t in zip(rows, top)]
         rec, rel = eb.ebic_recovery_relevance(expected, found)
+        approx = {}
+        for e in case["approximate_trends"]:
+            rows_e = eb.ebic_extract_rows_approx(h, off, flat, int(e), eb.ROWS_RISING_OR_FALLING)
+            approx[e] = eb.ebic_recovery_relevance(
+                expected, [(r, np.sort(np.asarray(t))) for r, t in zip(rows_e, top)])
     finally:
         eb.ebic_free(h)
     assert st["generations_done"] == case["generations_done"]
     assert st["stop_reason"] == case["stop_reason"]
     assert rec == pytest.approx(case["recovery"], rel=1e-12, abs=1e-15)
     assert rel == pytest.approx(case["relevance"], rel=1e-12, abs=1e-15)
+    for e, (arec, arel) in case["approximate_trends"].items():
+        assert approx[e][0] == pytest.approx(arec, rel=1e-12, abs=1e-15), e
+        assert approx[e][1] == pytest.approx(arel, rel=1e-12, abs=1e-15), e
