@@ -10,6 +10,11 @@ the device's.  Found biclusters: the best top-rank series, as many as there
 are planted biclusters.
 
     python tests/golden/make_quality_suite.py [--generations 2000] [--jobs 16]
+        [--datasets 1]
+
+With --datasets n > 1 every case is run on datasets (generator seeds)
+0 .. n-1 and quality_suite_<n>datasets.json gets the per-dataset figures
+and their means (the paper averages five datasets per case).
 """
 import argparse
 import json
@@ -22,7 +27,11 @@ ROOT = os.path.dirname(os.path.dirname(HERE))
 sys.path.insert(0, ROOT)
 
 
-def cases():
+def cases(datasets=1):
+    return [dict(c, dataset=d) for c in _cases() for d in range(datasets)]
+
+
+def _cases():
     out = []
     for size in ("150x100", "200x150", "300x200"):
         for pattern in ("trend-preserving", "column-constant", "row-constant", "shift", "scale",
@@ -38,9 +47,10 @@ def cases():
 
 def problem(case):
     from paper_1801_03039_gb300 import synth
+    seed = case.get("dataset", 0)
     if case["suite"] == "narrow":
-        return synth.matrix_narrow(0, case["width"], case["noise"])
-    return synth.matrix_pattern(0, case["pattern"], case["size"], case["noise"])
+        return synth.matrix_narrow(seed, case["width"], case["noise"])
+    return synth.matrix_pattern(seed, case["pattern"], case["size"], case["noise"])
 
 
 def params(case, prob, generations):
@@ -78,16 +88,26 @@ def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--generations", type=int, default=2000)
     ap.add_argument("--jobs", type=int, default=os.cpu_count() or 1)
+    ap.add_argument("--datasets", type=int, default=1)
     a = ap.parse_args()
     import oracle
     oracle.build()
-    todo = [(c, a.generations) for c in cases()]
+    todo = [(c, a.generations) for c in cases(a.datasets)]
     import multiprocessing as mp
     with ProcessPoolExecutor(a.jobs, mp_context=mp.get_context("spawn")) as ex:
         rows = list(ex.map(run_case, todo))
     out = {"generator": "tests/golden/make_quality_suite.py", "generations": a.generations,
-           "cases": rows}
-    with open(os.path.join(HERE, "quality_suite.json"), "w") as f:
+           "datasets": a.datasets, "cases": rows}
+    if a.datasets > 1:
+        means = {}
+        for r in rows:
+            key = r["problem"] + (f" noise {r['noise']}" if r["noise"] else "")
+            m = means.setdefault(key, {"recovery": [], "relevance": []})
+            m["recovery"].append(r["recovery"])
+            m["relevance"].append(r["relevance"])
+        out["means"] = {k: {q: sum(v) / len(v) for q, v in m.items()} for k, m in means.items()}
+    name = "quality_suite.json" if a.datasets == 1 else f"quality_suite_{a.datasets}datasets.json"
+    with open(os.path.join(HERE, name), "w") as f:
         json.dump(out, f, indent=1)
     for r in rows:
         name = r["problem"] + (f" noise {r['noise']}" if r["noise"] else "")

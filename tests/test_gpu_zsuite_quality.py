@@ -25,9 +25,10 @@ def built():
 
 
 def _problem(case):
+    seed = case.get("dataset", 0)
     if case["suite"] == "narrow":
-        return synth.matrix_narrow(0, case["width"], case["noise"])
-    return synth.matrix_pattern(0, case["pattern"], case["size"], case["noise"])
+        return synth.matrix_narrow(seed, case["width"], case["noise"])
+    return synth.matrix_pattern(seed, case["pattern"], case["size"], case["noise"])
 
 
 def _name(case):
