@@ -1,5 +1,5 @@
 """Whole EBIC searches on the seeded benchmark shapes (the paper's pattern
-suite, narrow biclusters, a noise sweep) on the GPU: the search, the rows of
+suite, narrow and overlapping biclusters, a noise sweep) on the GPU: the search, the rows of
 the found biclusters with the negative-trend expansion (and with the
 approximate-trend expansion) and Eq. (2)-(3) give the recovery and relevance
 the oracle gives (tests/golden/quality_suite.json, written by
@@ -28,6 +28,8 @@ def _problem(case):
     seed = case.get("dataset", 0)
     if case["suite"] == "narrow":
         return synth.matrix_narrow(seed, case["width"], case["noise"])
+    if case["suite"] == "overlap":
+        return synth.matrix_overlap(seed, case["overlap"], case["noise"])
     return synth.matrix_pattern(seed, case["pattern"], case["size"], case["noise"])
 
 

@@ -1,5 +1,6 @@
 """The stored quality-suite figures on the CPU: the five-dataset file agrees
 with the single-dataset file on dataset 0, its means are the means of its
+cases, the 20,000-generation file (the paper's run length) covers the same
 cases, and every stored case names the seeded problem and the search
 parameters that make_quality_suite.py derives for it today."""
 import json
@@ -19,6 +20,7 @@ def _load(name):
 
 ONE = _load("quality_suite.json")
 FIVE = _load("quality_suite_5datasets.json")
+ONE_20K = _load("quality_suite_20000gens.json")
 
 
 def _key(c):
@@ -43,29 +45,39 @@ def test_dataset_zero_is_the_single_dataset_file():
             assert a[k] == b[k], (a["problem"], k)
 
 
-def test_means_are_the_means_of_the_cases():
+def test_the_longer_runs_cover_the_same_cases():
+    assert ONE_20K["generations"] == 20000 and ONE_20K.get("datasets", 1) == 1
+    assert [c["problem"] for c in ONE_20K["cases"]] == [c["problem"] for c in ONE["cases"]]
+    for c in ONE_20K["cases"]:
+        assert c["params"]["iterations"] == 20000
+        assert c["generations_done"] == 20000 or c["stop_reason"] != 0
+
+
+@pytest.mark.parametrize("gold", [FIVE])
+def test_means_are_the_means_of_the_cases(gold):
+    assert len(gold["cases"]) == len(mqs.cases(5))
     groups = {}
-    for c in FIVE["cases"]:
+    for c in gold["cases"]:
         groups.setdefault(_key(c), []).append(c)
-    assert set(groups) == set(FIVE["means"])
+    assert set(groups) == set(gold["means"])
     for k, cs in groups.items():
         assert len(cs) == 5 and sorted(c["dataset"] for c in cs) == list(range(5))
         for q in ("recovery", "relevance"):
-            assert FIVE["means"][k][q] == pytest.approx(sum(c[q] for c in cs) / 5, rel=1e-12)
+            assert gold["means"][k][q] == pytest.approx(sum(c[q] for c in cs) / 5, rel=1e-12)
 
 
-def test_scores_are_fractions_and_relevance_bounds_recovery_on_clean_data():
-    for c in FIVE["cases"]:
+def test_scores_are_fractions():
+    for c in FIVE["cases"] + ONE_20K["cases"]:
         for rec, rel in [(c["recovery"], c["relevance"]), *c["approximate_trends"].values()]:
             assert 0.0 <= rec <= 1.0 and 0.0 <= rel <= 1.0
 
 
-@pytest.mark.parametrize("dataset", [0, 3])
-def test_cases_name_today_s_problems_and_parameters(dataset):
+@pytest.mark.parametrize("gold,dataset", [(FIVE, 0), (FIVE, 3), (ONE_20K, 0)])
+def test_cases_name_today_s_problems_and_parameters(gold, dataset):
     """The stored problem names and parameters are what the generator and the
     script produce now, so a change to either shows up here first."""
-    stored = [c for c in FIVE["cases"] if c["dataset"] == dataset]
+    stored = [c for c in gold["cases"] if c["dataset"] == dataset]
     for case in stored:
         prob = mqs.problem(case)
         assert prob.name == case["problem"]
-        assert mqs.params(case, prob, FIVE["generations"]) == case["params"]
+        assert mqs.params(case, prob, gold["generations"]) == case["params"]

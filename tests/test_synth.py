@@ -57,3 +57,24 @@ def test_noise_is_added_and_seeds_differ():
     # with noise the plants are only approximately ordered
     pl = b.plants[0]
     assert len(oracle.rows(b.A, pl.order.tolist(), 0)) < len(pl.rows)
+
+
+@pytest.mark.parametrize("overlap", [0, 3, 6, 9])
+def test_overlap_plants(overlap):
+    """Three 20 x 20 plants in 200 x 150, each sharing exactly `overlap` rows
+    and columns with the next and none with the one after; the last plant is
+    not overwritten, so all its rows rise along its order, and an earlier
+    plant keeps its order on the columns no later plant touches."""
+    prob = synth.matrix_overlap(4, overlap, noise=0.0)
+    assert prob.A.shape == (200, 150) and len(prob.plants) == 3
+    rs = [set(pl.rows.tolist()) for pl in prob.plants]
+    cs = [set(pl.order.tolist()) for pl in prob.plants]
+    assert all(len(r) == 20 for r in rs) and all(len(c) == 20 for c in cs)
+    for a, b in ((0, 1), (1, 2)):
+        assert len(rs[a] & rs[b]) == overlap and len(cs[a] & cs[b]) == overlap
+    assert not (rs[0] & rs[2]) and not (cs[0] & cs[2])
+    last = prob.plants[2]
+    assert rs[2] <= set(oracle.rows(prob.A, last.order.tolist(), 0).tolist())
+    first = prob.plants[0]
+    free = [c for c in first.order.tolist() if c not in cs[1]]
+    assert rs[0] <= set(oracle.rows(prob.A, free, 0).tolist())
