@@ -262,6 +262,15 @@ class EvalExpression:
         return vec_steps * 16 + io, ("16 B per (series, 128-row block, AND step) while the "
                                      "block is alive + CBF in + inc/fitness out")
 
+    def full_table_bytes(self) -> int:
+        """The same count without the early exit: every series reads the whole
+        table row (R padded to 128 rows, one bit per row) of each of its L - 1
+        pairs; plus the CBF and the outputs."""
+        R = self.prob.A.shape[0]
+        row_bytes = (R + 127) // 128 * 16
+        steps = int(np.maximum(np.diff(self.off.astype(np.int64)) - 1, 0).sum())
+        return steps * row_bytes + self.off.nbytes + self.cols.nbytes + self.P * (4 + 8)
+
     # -- CPU oracle ----------------------------------------------------------
     def oracle_sample(self, oracle, budget_s: float, nthreads: int):
         """Times the oracle on the first n series (all rows), n sized to ~budget_s."""
@@ -758,6 +767,7 @@ def roofline(wl, gens, extra, per_step_ms, peaks):
         return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": achieved / peaks["hbm_gbs"], "traffic": read_traffic(wl.name),
                 "algorithmic_bytes": alg_bytes, "algorithmic_def": alg_def,
+                "bytes_without_early_exit": wl.full_table_bytes(),
                 "kernel": "k_support_bitmask_warp",
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})"}
     kern = extra["kernel_us"]

@@ -130,3 +130,20 @@ def test_screened_comparison_scores_time_to_quality():
     assert s["random_scores"]["seeds_reaching_99pct_of_plain_best"] == 0
     assert s["random_scores"]["mean_seconds_to_99pct_of_plain_best"] is None
     assert s["plain"]["mean_final_best_fitness"] == pytest.approx(15.0)
+
+
+def test_byte_counts_of_the_fitness_pass():
+    """The roofline's byte counts on a hand-sized population: without the
+    early exit every AND step reads a whole table row; with it, only the
+    128-row blocks still alive, so never more."""
+    wl = bench.EvalExpression(0)
+    R = wl.prob.A.shape[0]
+    row = (R + 127) // 128 * 16                        # 157 blocks x 16 B at R = 20,000
+    assert row == 157 * 16
+    wl.off = np.array([0, 3, 4, 9], np.int32)          # lengths 3, 1, 5 -> 2 + 0 + 4 steps
+    wl.cols = np.array([0, 1, 2, 7, 3, 4, 5, 6, 8], np.int32)
+    wl.P = 3
+    io = wl.off.nbytes + wl.cols.nbytes + 3 * 12
+    assert wl.full_table_bytes() == 6 * row + io
+    alg, _ = wl.algorithmic_bytes()
+    assert io + 157 * 16 <= alg <= wl.full_table_bytes()   # the first step reads every block
