@@ -95,6 +95,24 @@ def run_case(args):
             "approximate_trends": approx}
 
 
+def means(rows):
+    """Per case (problem and noise), the means over its datasets of recovery,
+    relevance and the approximate-trend scores."""
+    groups = {}
+    for r in rows:
+        groups.setdefault(r["problem"] + (f" noise {r['noise']}" if r["noise"] else ""),
+                          []).append(r)
+    out = {}
+    for key, rs in groups.items():
+        n = len(rs)
+        out[key] = {"recovery": sum(r["recovery"] for r in rs) / n,
+                    "relevance": sum(r["relevance"] for r in rs) / n,
+                    "approximate_trends": {
+                        e: [sum(r["approximate_trends"][e][q] for r in rs) / n for q in (0, 1)]
+                        for e in rs[0]["approximate_trends"]}}
+    return out
+
+
 def _case_key(c):
     return tuple(sorted((k, c[k]) for k in ("suite", "pattern", "size", "width", "overlap",
                                               "noise") if k in c)) + (c.get("dataset", 0),)
@@ -137,13 +155,7 @@ def main():
     out = {"generator": "tests/golden/make_quality_suite.py", "generations": a.generations,
            "datasets": a.datasets, "cases": rows}
     if a.datasets > 1:
-        means = {}
-        for r in rows:
-            key = r["problem"] + (f" noise {r['noise']}" if r["noise"] else "")
-            m = means.setdefault(key, {"recovery": [], "relevance": []})
-            m["recovery"].append(r["recovery"])
-            m["relevance"].append(r["relevance"])
-        out["means"] = {k: {q: sum(v) / len(v) for q, v in m.items()} for k, m in means.items()}
+        out["means"] = means(rows)
     with open(path, "w") as f:
         json.dump(out, f, indent=1)
     if os.path.exists(partial):

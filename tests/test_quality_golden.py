@@ -64,6 +64,10 @@ def test_means_are_the_means_of_the_cases(gold):
         assert len(cs) == 5 and sorted(c["dataset"] for c in cs) == list(range(5))
         for q in ("recovery", "relevance"):
             assert gold["means"][k][q] == pytest.approx(sum(c[q] for c in cs) / 5, rel=1e-12)
+        for e, pair in gold["means"][k]["approximate_trends"].items():
+            for j in (0, 1):
+                want = sum(c["approximate_trends"][e][j] for c in cs) / 5
+                assert pair[j] == pytest.approx(want, rel=1e-12), (k, e)
 
 
 def test_scores_are_fractions():
