@@ -1,6 +1,6 @@
-"""The stored quality-suite figures on the CPU: the five-dataset file agrees
-with the single-dataset file on dataset 0, its means are the means of its
-cases, the 20,000-generation file (the paper's run length) covers the same
+"""The stored quality-suite figures on the CPU: each five-dataset file agrees
+with its single-dataset file on dataset 0, the means are the means of the
+cases, the 20,000-generation files (the paper's run length) cover the same
 cases, and every stored case names the seeded problem and the search
 parameters that make_quality_suite.py derives for it today."""
 import json
@@ -21,6 +21,7 @@ def _load(name):
 ONE = _load("quality_suite.json")
 FIVE = _load("quality_suite_5datasets.json")
 ONE_20K = _load("quality_suite_20000gens.json")
+FIVE_20K = _load("quality_suite_5datasets_20000gens.json")
 
 
 def _key(c):
@@ -47,13 +48,18 @@ def test_dataset_zero_is_the_single_dataset_file():
 
 def test_the_longer_runs_cover_the_same_cases():
     assert ONE_20K["generations"] == 20000 and ONE_20K.get("datasets", 1) == 1
+    assert FIVE_20K["generations"] == 20000 and FIVE_20K["datasets"] == 5
     assert [c["problem"] for c in ONE_20K["cases"]] == [c["problem"] for c in ONE["cases"]]
-    for c in ONE_20K["cases"]:
+    for c in ONE_20K["cases"] + FIVE_20K["cases"]:
         assert c["params"]["iterations"] == 20000
         assert c["generations_done"] == 20000 or c["stop_reason"] != 0
+    zero = [c for c in FIVE_20K["cases"] if c["dataset"] == 0]
+    for a, b in zip(ONE_20K["cases"], zero):
+        for k in ("problem", "noise", "params", "recovery", "relevance", "approximate_trends"):
+            assert a[k] == b[k], (a["problem"], k)
 
 
-@pytest.mark.parametrize("gold", [FIVE])
+@pytest.mark.parametrize("gold", [FIVE, FIVE_20K], ids=["10000", "20000"])
 def test_means_are_the_means_of_the_cases(gold):
     assert len(gold["cases"]) == len(mqs.cases(5))
     groups = {}
@@ -71,12 +77,12 @@ def test_means_are_the_means_of_the_cases(gold):
 
 
 def test_scores_are_fractions():
-    for c in FIVE["cases"] + ONE_20K["cases"]:
+    for c in FIVE["cases"] + FIVE_20K["cases"]:
         for rec, rel in [(c["recovery"], c["relevance"]), *c["approximate_trends"].values()]:
             assert 0.0 <= rec <= 1.0 and 0.0 <= rel <= 1.0
 
 
-@pytest.mark.parametrize("gold,dataset", [(FIVE, 0), (FIVE, 3), (ONE_20K, 0)])
+@pytest.mark.parametrize("gold,dataset", [(FIVE, 0), (FIVE, 3), (FIVE_20K, 4)])
 def test_cases_name_today_s_problems_and_parameters(gold, dataset):
     """The stored problem names and parameters are what the generator and the
     script produce now, so a change to either shows up here first."""
