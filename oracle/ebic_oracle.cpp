@@ -37,9 +37,12 @@
 // Pins (tests/test_oracle_*.py): brute force and sort-based support on tiny
 // matrices, the closed-form sum over all L-tuples, reversal/complement
 // invariants, planted rows, hand values of Eq. (1), the CBF example of Fig. 3,
-// Philox known-answer vectors, operator properties and hand-built top-rank
-// cases.  The full EA trajectory has no external pin beyond these parts
-// ("parity unpinned" for the trajectory as a whole; see the design notes).
+// Philox known-answer vectors, operator properties, hand-built top-rank
+// cases, and one generation of Steps 2-3 listed attempt by attempt with the
+// crowding counts each tournament sees (elites count, accepted children count
+// before the next attempt, tabu hits do not).  The full EA trajectory has no
+// external pin beyond these parts ("parity unpinned" for the trajectory as a
+// whole).
 
 #include <algorithm>
 #include <cmath>
