@@ -39,7 +39,7 @@
 extern "C" {
 #endif
 
-#define EBIC_ABI_VERSION 1
+#define EBIC_ABI_VERSION 2
 #define EBIC_MAX_EVAL_LEN 1024 /* longest series accepted by evaluation */
 #define EBIC_MAX_EA_LEN 64     /* longest series the EA builds (len_max) */
 #define EBIC_MAX_TOURNAMENT 4  /* largest tournament_k */
@@ -123,20 +123,37 @@ ebic_status ebic_set_path(ebic_handle h, int32_t path);
  * field 0 = automatic).  Results never depend on these.
  *   kernel: bitmask path only -- 1 = one lane per 16-byte vector of a table
  *     entry (entries of at most 32 vectors, i.e. up to 4,096 rows), 2 = one
- *     warp per series part, 0 = lane kernel up to 2,048 rows, else warp kernel.
+ *     warp per series part, 3 = staged: a persistent kernel in which one
+ *     scout warp per group of warps copies the first dense_steps table rows
+ *     of each series part into shared memory with bulk copies (the rows every
+ *     128-row block still needs) and the group's other warps AND them and
+ *     walk the remaining steps with per-vector loads and early exit; rising
+ *     counts only (support mode EBIC_SUPPORT_INC, no falling counts), else
+ *     the warp kernel runs.  0 = lane kernel up to 2,048 rows, else warp
+ *     kernel.
  *   vecs_per_part_bitmask / vecs_per_part_gather: 16-byte vectors of a table
  *     entry / of a column that one warp walks before the rest of the series
  *     goes to another warp (rounded to a multiple of 32).
  *   batch_steps: AND steps fetched between two early-exit tests (4 or 8).
  *   vecs_per_lane: 16-byte vectors each lane of the warp kernel carries
  *     (1, 2 or 4; 4 only with batch_steps 4).  Series that need the falling
- *     count use batch_steps 4 and one vector per lane. */
+ *     count use batch_steps 4 and one vector per lane.
+ *   dense_steps (kernel 3): AND steps staged by bulk copies, 1..8 (0 = 4).
+ *   stages (kernel 3): items in flight per group, 2..4 (0 = 2).
+ *   groups (kernel 3): at most this many groups of warps per CTA (0 = as many
+ *     as fit one CTA per SM).
+ *   vecs_per_lane also sets, for kernel 3, the 16-byte vectors each
+ *     consumer thread carries: 1 or 2 (0 = 2 for table entries over 64
+ *     vectors). */
 typedef struct {
   int32_t kernel;
   int32_t vecs_per_part_bitmask;
   int32_t vecs_per_part_gather;
   int32_t batch_steps;
   int32_t vecs_per_lane;
+  int32_t dense_steps;
+  int32_t stages;
+  int32_t groups;
 } ebic_eval_tuning_t;
 /* NULL restores the automatic choice. */
 ebic_status ebic_set_eval_tuning(ebic_handle h, const ebic_eval_tuning_t* tuning);

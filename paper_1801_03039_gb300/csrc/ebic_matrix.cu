@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "ebic_internal.cuh"
+#include "ebic_staged.cuh"
 #include "ebic_support.cuh"
 
 namespace ebic {
@@ -303,6 +304,64 @@ int32_t resolve_path(ebic_ctx* h) {
   return h->LT ? EBIC_PATH_BITMASK : EBIC_PATH_GATHER;
 }
 
+// Geometry of the staged kernel for this handle and tuning; false if it
+// cannot run here (a group does not fit one CTA).  Parts hold at most 256
+// vectors; a consumer thread carries `vecs_per_lane` of them (1 or 2; 0 =
+// 2 for parts over 64 vectors).
+static bool staged_geometry(const ebic_ctx* h, const ebic_eval_tuning_t& tu, int32_t P,
+                            StagedGeom* out) {
+  StagedGeom g{};
+  const int32_t V = h->W >> 2;
+  const int32_t parts = (V + 255) / 256;
+  g.vpp = (V + parts - 1) / parts;
+  g.items_per = parts;
+  g.nvt = tu.vecs_per_lane == 1 ? 1 : (tu.vecs_per_lane == 2 ? 2 : (g.vpp > 64 ? 2 : 1));
+  g.gw = (g.vpp + 32 * g.nvt - 1) / (32 * g.nvt);
+  g.dense = tu.dense_steps > 0 ? tu.dense_steps : 4;
+  g.ns = tu.stages > 0 ? tu.stages : 2;
+  g.data_bytes = (g.dense * g.vpp * 16 + 127) / 128 * 128;
+  g.stage_bytes = (g.data_bytes + (int32_t)sizeof(StagedHdr) + 127) / 128 * 128;
+  int32_t groups = 0;
+  for (int32_t n = 1; n <= 15; ++n) {
+    StagedGeom t = g;
+    t.groups = n;
+    if (n * (g.gw + 1) * 32 > 1024 || staged_smem_bytes(t) > 227 * 1024) break;
+    groups = n;
+  }
+  if (tu.groups > 0) groups = std::min(groups, tu.groups);
+  if (groups < 1 || (int64_t)P * parts >= (1ll << 31)) return false;
+  g.groups = groups;
+  *out = g;
+  return true;
+}
+
+// Queues the staged kernel (rising counts only): one CTA per SM, capped by
+// the items.
+template <bool CHECK, class Pop, int NVT>
+static ebic_status launch_staged(ebic_ctx* h, const Pop& pop, const EvalArgs& a,
+                                 const StagedGeom& g0, cudaStream_t s) {
+  StagedGeom g = g0;
+  const size_t smem = staged_smem_bytes(g);
+  const int threads = g.groups * (g.gw + 1) * 32;
+  auto kern = k_support_staged<CHECK, Pop, NVT>;
+  EBIC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)smem));
+  int per_sm = 0;
+  EBIC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+  if (per_sm < 1) return fail(EBIC_ERR_CUDA, "staged kernel: no CTA fits an SM");
+  const int64_t n_items = (int64_t)a.P * g.items_per;
+  const int64_t grid = std::min<int64_t>((int64_t)h->sm_count * per_sm,
+                                         (n_items + g.groups - 1) / g.groups);
+  g.n_scouts = (int32_t)(grid * g.groups);
+  if (g.items_per > 1)
+    EBIC_TRY(h->tickets.reserve_zeroed((size_t)a.P * 2 * sizeof(unsigned long long), s));
+  count_launches(1);
+  kern<<<(unsigned)grid, threads, smem, s>>>(h->LT, h->C, h->W, h->R, pop, a, g,
+                                             h->tickets.as<uint32_t>(), h->LN, h->d_err);
+  EBIC_CUDA_TRY(cudaGetLastError());
+  return EBIC_OK;
+}
+
 template <bool CHECK, class Pop>
 static ebic_status eval_any(ebic_ctx* h, const Pop& pop, EvalArgs a, cudaStream_t s) {
   if (a.P <= 0) return EBIC_OK;
@@ -310,6 +369,12 @@ static ebic_status eval_any(ebic_ctx* h, const Pop& pop, EvalArgs a, cudaStream_
   if (dec && !a.dec) return fail(EBIC_ERR_ARG, "internal: dec output required");
   const int32_t path = resolve_path(h);
   if (path == EBIC_PATH_BITMASK && !h->LT) EBIC_TRY(build_pair_table(h, s));
+  if (path == EBIC_PATH_BITMASK && h->tuning.kernel == 3 && !dec && !a.dec) {
+    StagedGeom g;
+    if (staged_geometry(h, h->tuning, a.P, &g))
+      return g.nvt == 2 ? launch_staged<CHECK, Pop, 2>(h, pop, a, g, s)
+                        : launch_staged<CHECK, Pop, 1>(h, pop, a, g, s);
+  }
   int32_t vpi = 0, ipc = 1;
   bool lane_kernel = false;
   int32_t VP = 1;
@@ -379,14 +444,19 @@ static ebic_status autotune_any(ebic_ctx* h, const Pop& pop, const EvalArgs& a, 
   const bool dec = a.want_dec != 0 || a.mode == EBIC_SUPPORT_INC_PLUS_DEC;
   if (path == EBIC_PATH_BITMASK) {
     const int32_t V = h->W >> 2;
-    if (V <= 32) cands.push_back({1, 0, 0, 0, 0});
+    if (V <= 32) cands.push_back({1, 0, 0, 0, 0, 0, 0, 0});
+    if (!dec && V > 32) {
+      for (int32_t nvt : {1, 2})
+        for (int32_t dense : {4, 6}) cands.push_back({3, 0, 0, 0, nvt, dense, 2, 0});
+      cands.push_back({3, 0, 0, 0, 0, 4, 3, 0});
+    }
     const int32_t parts[] = {32, 64, 128, 256, 0};
     for (int32_t vp : parts) {
       if (vp > 0 && vp / 2 >= V) continue;
-      cands.push_back({2, vp, 0, 8, 1});
+      cands.push_back({2, vp, 0, 8, 1, 0, 0, 0});
       if (!dec) {
-        cands.push_back({2, vp, 0, 4, 1});
-        cands.push_back({2, vp, 0, 4, 2});
+        cands.push_back({2, vp, 0, 4, 1, 0, 0, 0});
+        cands.push_back({2, vp, 0, 4, 2, 0, 0, 0});
       }
     }
   } else {
@@ -394,7 +464,7 @@ static ebic_status autotune_any(ebic_ctx* h, const Pop& pop, const EvalArgs& a, 
     const int32_t parts[] = {32, 64, 128, 256, 512, 1024, 0};
     for (int32_t vp : parts) {
       if (vp > 0 && vp / 2 >= V) continue;
-      cands.push_back({0, 0, vp, 0, 0});
+      cands.push_back({0, 0, vp, 0, 0, 0, 0, 0});
     }
   }
   cudaEvent_t e0, e1;
@@ -520,6 +590,7 @@ static ebic_status place(ebic_ctx* h, const float* rowmajor_dev, cudaStream_t s)
   EBIC_CUDA_TRY(cudaMalloc(&h->A_c, (size_t)h->C * h->R_pad * sizeof(float)));
   EBIC_CUDA_TRY(cudaMalloc(&h->d_err, sizeof(int)));
   EBIC_CUDA_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+  EBIC_CUDA_TRY(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
   // LN[m] = log(m) with the host C library, m = 0 .. 2R + 1.
   const size_t nln = 2 * (size_t)h->R + 2;
   EBIC_CUDA_TRY(cudaMalloc(&h->LN, nln * sizeof(double)));
@@ -729,7 +800,12 @@ ebic_status ebic_set_eval_tuning(ebic_handle h, const ebic_eval_tuning_t* t) {
   if (!h) return fail(EBIC_ERR_ARG, "null handle");
   ebic_eval_tuning_t z{};
   if (!t) t = &z;
-  if (t->kernel < 0 || t->kernel > 2) return fail(EBIC_ERR_ARG, "kernel must be 0, 1 or 2");
+  if (t->kernel < 0 || t->kernel > 3) return fail(EBIC_ERR_ARG, "kernel must be 0, 1, 2 or 3");
+  if (t->dense_steps < 0 || t->dense_steps > kStagedMaxDense)
+    return fail(EBIC_ERR_ARG, "dense_steps must be 0 .. %d", kStagedMaxDense);
+  if (!(t->stages == 0 || (t->stages >= 2 && t->stages <= 4)))
+    return fail(EBIC_ERR_ARG, "stages must be 0 or 2 .. 4");
+  if (t->groups < 0 || t->groups > 15) return fail(EBIC_ERR_ARG, "groups must be 0 .. 15");
   if (t->vecs_per_part_bitmask < 0 || t->vecs_per_part_gather < 0)
     return fail(EBIC_ERR_ARG, "negative part size");
   if (!(t->batch_steps == 0 || t->batch_steps == 4 || t->batch_steps == 8))

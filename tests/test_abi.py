@@ -55,7 +55,7 @@ def test_binding_fails_loudly_without_library(tmp_path):
 
 def test_abi_version(libpath):
     L = ctypes.CDLL(libpath)
-    assert L.ebic_abi_version() == 1
+    assert L.ebic_abi_version() == 2
 
 
 def _null_handle_calls():

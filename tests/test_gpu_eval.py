@@ -210,7 +210,8 @@ def test_device_variant_flags_invalid_series(path):
                                   dict(kernel=2, batch_steps=4, vecs_per_lane=2),
                                   dict(kernel=2, batch_steps=8, vecs_per_lane=2),
                                   dict(kernel=2, batch_steps=4, vecs_per_lane=4,
-                                       vecs_per_part_bitmask=64)])
+                                       vecs_per_part_bitmask=64),
+                                  dict(kernel=3), dict(kernel=3, dense_steps=2, stages=2)])
 def test_launch_shapes_do_not_change_results(shape, tune):
     # lane-per-vector kernel, warp kernel, and forced splits of each series
     R, C = shape
@@ -295,5 +296,126 @@ def test_autotuner_keeps_results_exact(which):
             inc2, _, fit2 = eb.ebic_eval_population(h, off, cols, sig)
             assert_bits_equal(inc2, oinc, "inc after tuning")
             assert_bits_equal(fit2, ofit, "fit after tuning")
+    finally:
+        eb.ebic_free(h)
+
+
+# ---------------------------------------------------------------------------
+# The staged kernel (launch shape kernel 3): dense AND steps brought into
+# shared memory by bulk copies, the rest by per-vector loads.  Rising counts.
+# ---------------------------------------------------------------------------
+STAGED = [dict(kernel=3), dict(kernel=3, dense_steps=1, stages=2),
+          dict(kernel=3, dense_steps=8, stages=4, groups=1),
+          dict(kernel=3, dense_steps=3, stages=3, groups=2, vecs_per_lane=1),
+          dict(kernel=3, dense_steps=5, stages=2, vecs_per_lane=2),
+          dict(kernel=3, vecs_per_lane=1)]
+
+
+def _staged_case(name):
+    rng = np.random.default_rng(sum(map(ord, name)))
+    if name == "tiny":
+        prob = synth.matrix_tiny(seed=0)
+        return prob.A, *synth.population(0, 100, 20, 2, 6, plants=prob.plants), 10
+    if name == "ragged_4097x30":
+        prob = synth.matrix_random(41, 4097, 30, n_plants=3, plant_rows=(200, 500),
+                                   plant_cols=(3, 8))
+        return prob.A, *synth.population(9, 257, 30, 2, 12, plants=prob.plants), 40
+    if name == "windows_3000x60_L30_45":
+        prob = synth.matrix_random(7, 3000, 60, n_plants=2, plant_rows=(300, 600),
+                                   plant_cols=(40, 50))
+        return prob.A, *synth.population(8, 300, 60, 30, 45, plants=prob.plants), 30
+    if name == "long_300x1100":
+        A = rng.standard_normal((300, 1100)).astype(np.float32)
+        A[:40] = np.sort(A[:40], axis=1)                 # rows rising along 0, 1, 2, ...
+        seqs = [[5], [5, 5], [0, 1, 0], list(range(1024)), list(range(65)), list(range(66)),
+                list(range(64)), rng.permutation(1100)[:1024].tolist(),
+                list(range(1023, -1, -1)), [7] * 1024, list(range(0, 1100, 11))]
+        off, cols = oracle.to_cbf(seqs)
+        return A, off, cols, 3
+    if name == "parts_60000x12":
+        prob = synth.matrix_random(5, 60000, 12, n_plants=2, plant_rows=(3000, 6000),
+                                   plant_cols=(3, 6))
+        return prob.A, *synth.population(4, 37, 12, 1, 5, plants=prob.plants, frac_planted=0.6), 100
+    if name == "ties_nan":
+        A = rng.integers(-2, 3, (5000, 10)).astype(np.float32)
+        A[rng.random(A.shape) < 0.05] = np.nan
+        A[rng.random(A.shape) < 0.1] = -0.0
+        return A, *synth.population(3, 500, 10, 1, 6, duplicates=True), 7
+    raise KeyError(name)
+
+
+@pytest.mark.parametrize("tune", STAGED)
+@pytest.mark.parametrize("case", ["tiny", "ragged_4097x30", "windows_3000x60_L30_45",
+                                  "long_300x1100", "parts_60000x12", "ties_nan"])
+def test_staged_kernel_exact(case, tune):
+    A, off, cols, sigma = _staged_case(case)
+    oinc, _, ofit = oracle_eval(A, off, cols, sigma)
+    h = eb.ebic_load_matrix(A)
+    try:
+        eb.ebic_set_path(h, eb.PATH_BITMASK)
+        eb.ebic_set_eval_tuning(h, **tune)
+        for rep in range(3):               # the work counter is back to zero after each launch
+            inc, _, fit = eb.ebic_eval_population(h, off, cols, sigma, want_dec=False)
+            eb.ebic_check_device_error(h)
+            assert_bits_equal(inc, oinc, f"inc {case} {tune} launch {rep}")
+            assert_bits_equal(fit, ofit, f"fit {case} {tune} launch {rep}")
+    finally:
+        eb.ebic_free(h)
+
+
+@pytest.mark.parametrize("tune", STAGED[:2])
+def test_staged_kernel_expression_full(tune):
+    """The expression-shaped workload at full size, 20,000 x 200, P = 4,096."""
+    prob = synth.matrix_expression(seed=0)
+    off, cols = synth.population(2, 4096, 200, 3, 30, plants=prob.plants)
+    oinc, _, ofit = oracle_eval(prob.A, off, cols, 50)
+    h = eb.ebic_load_matrix(prob.A)
+    try:
+        eb.ebic_set_path(h, eb.PATH_BITMASK)
+        eb.ebic_set_eval_tuning(h, **tune)
+        for _ in range(2):
+            inc, _, fit = eb.ebic_eval_population(h, off, cols, 50, want_dec=False)
+            assert_bits_equal(inc, oinc, "inc")
+            assert_bits_equal(fit, ofit, "fit")
+    finally:
+        eb.ebic_free(h)
+
+
+def test_staged_kernel_flags_invalid_series():
+    torch = pytest.importorskip("torch")
+    A = np.random.default_rng(1).standard_normal((5000, 6)).astype(np.float32)
+    h = eb.ebic_load_matrix(A)
+    eb.ebic_set_path(h, eb.PATH_BITMASK)
+    eb.ebic_set_eval_tuning(h, kernel=3)
+    dev = torch.device("cuda:0")
+    off = torch.tensor([0, 2, 4, 6, 99], dtype=torch.int32, device=dev)
+    cols = torch.tensor([0, 1, 2, 6, 3, 4], dtype=torch.int32, device=dev)
+    inc = torch.full((4,), 7, dtype=torch.int32, device=dev)
+    fit = torch.full((4,), 7.0, dtype=torch.float64, device=dev)
+    eb.ebic_eval_population_dev(h, off, cols, 4, 6, 3, 0, inc, None, fit)
+    with pytest.raises(eb.EbicError) as e:
+        eb.ebic_check_device_error(h)
+    assert e.value.status == 7
+    got = inc.cpu().numpy()
+    oinc, _, ofit = oracle_eval(A, np.array([0, 2, 4]), np.array([0, 1, 3, 4]), 3)
+    assert got[1] == 0 and got[3] == 0 and fit.cpu().numpy()[1] == 0.0
+    assert got[0] == oinc[0] and got[2] == oinc[1]
+    # a valid launch afterwards is exact (the work counter was reset)
+    off2, cols2 = synth.population(3, 200, 6, 2, 5)
+    oinc2, _, ofit2 = oracle_eval(A, off2, cols2, 3)
+    inc2, _, fit2 = eb.ebic_eval_population(h, off2, cols2, 3, want_dec=False)
+    assert_bits_equal(inc2, oinc2, "inc")
+    assert_bits_equal(fit2, ofit2, "fit")
+    eb.ebic_check_device_error(h)
+    eb.ebic_free(h)
+
+
+def test_staged_kernel_rejects_bad_tuning():
+    h = eb.ebic_load_matrix(synth.matrix_tiny(seed=0).A)
+    try:
+        for bad in (dict(kernel=3, dense_steps=9), dict(kernel=3, stages=1),
+                    dict(kernel=3, stages=5), dict(kernel=3, groups=16)):
+            with pytest.raises(eb.EbicError):
+                eb.ebic_set_eval_tuning(h, **bad)
     finally:
         eb.ebic_free(h)
