@@ -7,23 +7,29 @@
 Prints ONE JSON line (rank 0).  Workloads (seeded synthetic inputs, see
 paper_1801_03039_gb300/synth.py):
 
-  generations-paper (default) 1,000 x 100 N(0,1) matrix with shift, scale
-                   and order-preserving 50 x 10 plants; population 600 of
-                   length 3-20.  A step is one generation of Steps 2-5, run on
-                   the device as a replayed CUDA graph.
+  eval-expression  (default) 20,000 x 200 log-normal matrix with 10 planted
+                   overlapping order-preserving biclusters; a population of
+                   4,096 series of length 3-30.  A step is one fitness pass
+                   (support + Eq. (1)) of the whole population through the C ABI
+                   on device buffers.  The line also carries, as sub-objects,
+                   the generation workload below (rank 0) and an L2 probe.
+  generations-paper 1,000 x 100 N(0,1) matrix with shift, scale and
+                   order-preserving 50 x 10 plants; population 600 of length
+                   3-20.  A step is one generation of Steps 2-5, run on the
+                   device as a replayed CUDA graph.
   generations-screened  the generations-paper run with offspring screening
                    (8 candidate children per attempt, best surrogate score
                    goes on); the surrogate is trained first on pairs logged
                    from plain runs of other seeds.  Reports the plain-vs-
                    screened comparison and the held-out ranking quality.
-  eval-expression  20,000 x 200 log-normal matrix with 10 planted overlapping
-                   order-preserving biclusters; a population of 4,096 series of
-                   length 3-30.  A step is one fitness pass (support + Eq. (1))
-                   of the whole population through the C ABI on device buffers.
+  eval-batch       64 independent problems of uneven size in one persistent
+                   launch (graph replay).
 
 Timing: W untimed warm-up steps, then K steps, each timed with CUDA events on
-the launching stream; L2 is flushed (a 512 MiB buffer is overwritten) before
-every timed step, outside the timed interval.  SM clocks and throttle reasons
+the launching stream.  Before every timed step the L2 is flushed outside the
+timed interval: a 512 MiB buffer is overwritten and then a second 512 MiB
+buffer is read, so that the L2 holds no line of the workload and no dirty line
+whose write-back would land in the timed step.  SM clocks and throttle reasons
 are sampled with nvidia-smi during the timed steps.  With torchrun (N > 1)
 every rank runs its own independent problem (seeded by its rank; no
 collective on the data path) and rank 0 reports the whole-job aggregate over
@@ -167,12 +173,61 @@ def load_peaks() -> dict:
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
+class L2Flush:
+    """Leaves the L2 without any line of the workload and without dirty lines:
+    a 512 MiB buffer is overwritten, then a second 512 MiB buffer is read."""
+
+    def __init__(self, torch):
+        self.w = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+        self.r = torch.zeros(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+        self.desc = ("flushed before every timed step: a 512 MiB buffer overwritten, then a "
+                     "second 512 MiB buffer read (no workload line and no dirty line left in L2)")
+
+    def __call__(self, i: int):
+        self.w.fill_(i)
+        self.r.max()
+
+
+def support_bytes(A, offsets, cols, path: str) -> int:
+    """Algorithmic bytes of one support pass over a CBF population, with the
+    early exit of the kernels (the rows of a series that stop rising are not
+    read again):
+      bitmask  16 B per (series, 128-row block, AND step) taken while the block
+               still holds a rising row (every block at step 0);
+      gather   16 B per (series, 4-row group, column read) while the group
+               still holds a rising row: the first column and every step.
+    Rows are padded to a multiple of 128, as on the device."""
+    A = np.asarray(A, np.float32)
+    R = A.shape[0]
+    Rp = (R + 127) // 128 * 128
+    At = np.ascontiguousarray(A.T)
+    unit = 128 if path == "bitmask" else 4
+    total = 0
+    for i in range(len(offsets) - 1):
+        s = cols[offsets[i]:offsets[i + 1]]
+        L = len(s)
+        if L < 2:
+            continue
+        groups = Rp // unit
+        total += groups * (0 if path == "bitmask" else 1)          # the gather's first column
+        rows = np.arange(R)
+        for t in range(L - 1):
+            total += groups
+            a, b = At[s[t]], At[s[t + 1]]
+            rows = rows[a[rows] < b[rows]]
+            if rows.size == 0:
+                break
+            g = rows // unit
+            groups = int(np.count_nonzero(np.diff(g))) + 1
+    return 16 * total
+
+
 # ---------------------------------------------------------------------------
 # workload: one fitness pass over an expression-shaped matrix
 # ---------------------------------------------------------------------------
 class EvalExpression:
     name = "eval-expression"
-    DEFAULT_STEPS = 20000          # about 0.5 s of timed passes
+    DEFAULT_STEPS = 5000           # 0.1 s of timed passes (plus the flushes)
     R, C, P, LMIN, LMAX, SIGMA = 20000, 200, 4096, 3, 30, 50
 
     def __init__(self, rank: int):
@@ -187,7 +242,8 @@ class EvalExpression:
                 "series_len": [self.LMIN, self.LMAX], "sigma": self.SIGMA,
                 "support_path": "bitmask", "support_mode": "inc",
                 "launch_shape": getattr(self, "tuning", None),
-                "l2": "flushed before every timed step (512 MiB overwrite)"}
+                "launch_shape_source": getattr(self, "tuning_source", None),
+                "l2": getattr(self, "l2_desc", None)}
 
     def units_per_step(self) -> int:          # candidate x row tests per step
         return self.P * self.R
@@ -201,10 +257,18 @@ class EvalExpression:
         self.d_cols = torch.from_numpy(self.cols).to(dev)
         self.d_inc = torch.zeros(self.P, dtype=torch.int32, device=dev)
         self.d_fit = torch.zeros(self.P, dtype=torch.float64, device=dev)
-        # one-time autotuning of the launch shape on this population (untimed)
-        self.tuning, self.tuned_us = eb.ebic_autotune_eval(
-            self.h, self.d_off, self.d_cols, self.P, len(self.cols), self.SIGMA,
-            eb.SUPPORT_INC, self.d_inc, None, self.d_fit)
+        if getattr(self, "forced_tuning", None):
+            eb.ebic_set_eval_tuning(self.h, **self.forced_tuning)
+            self.tuning = eb.ebic_get_eval_tuning(self.h)
+            self.tuning_source = "set by --tuning"
+        else:
+            # one-time autotuning of the launch shape on this population
+            # (untimed), each candidate timed with the L2 emptied first, as the
+            # timed steps are
+            self.tuning, self.tuned_us = eb.ebic_autotune_eval(
+                self.h, self.d_off, self.d_cols, self.P, len(self.cols), self.SIGMA,
+                eb.SUPPORT_INC, self.d_inc, None, self.d_fit, flags=eb.TUNE_COLD_L2)
+            self.tuning_source = "ebic_autotune_eval with EBIC_TUNE_COLD_L2"
         torch.cuda.synchronize()
 
     def step_gpu(self, torch, eb, stream):
@@ -227,40 +291,12 @@ class EvalExpression:
                 "d2h_bytes_per_step": int(inc.nbytes + fit.nbytes)}
 
     def algorithmic_bytes(self) -> tuple[int, str]:
-        """Bytes the early-exit bitmask algorithm reads per pass: for every series
-        and every 128-row block, one 16-byte table vector per AND step taken while
-        the block's running AND is not yet zero; plus the CBF and the outputs."""
-        A = self.prob.A
-        R, C = A.shape
-        Rp = (R + 127) // 128 * 128
-        nblk = Rp // 128
-        cache = {}
-
-        def pair_bits(x, y):
-            k = (x, y)
-            if k not in cache:
-                b = np.zeros(Rp, bool)
-                b[:R] = A[:, x] < A[:, y]
-                cache[k] = np.packbits(b.reshape(nblk, 128), axis=1)   # nblk x 16 bytes
-            return cache[k]
-
-        vec_steps = 0
-        for i in range(self.P):
-            s = self.cols[self.off[i]:self.off[i + 1]]
-            if len(s) < 2:
-                continue
-            m = None
-            alive = np.ones(nblk, bool)
-            for t in range(len(s) - 1):
-                vec_steps += int(alive.sum())
-                b = pair_bits(int(s[t]), int(s[t + 1]))
-                m = b if m is None else (m & b)
-                alive = m.any(axis=1)
-                if not alive.any():
-                    break
+        """Bytes the early-exit bitmask algorithm reads per pass (support_bytes)
+        plus the CBF in and the rising counts and fitness out."""
         io = self.off.nbytes + self.cols.nbytes + self.P * (4 + 8)
-        return vec_steps * 16 + io, ("16 B per (series, 128-row block, AND step) while the "
-                                     "block is alive + CBF in + inc/fitness out")
+        return (support_bytes(self.prob.A, self.off, self.cols, "bitmask") + io,
+                "16 B per (series, 128-row block, AND step) while the block holds a rising "
+                "row + CBF in + inc/fitness out")
 
     def full_table_bytes(self) -> int:
         """The same count without the early exit: every series reads the whole
@@ -273,7 +309,9 @@ class EvalExpression:
 
     # -- CPU oracle ----------------------------------------------------------
     def oracle_sample(self, oracle, budget_s: float, nthreads: int):
-        """Times the oracle on the first n series (all rows), n sized to ~budget_s."""
+        """Times the oracle on the first n series (all rows), n sized to about a
+        quarter of budget_s; once n is the whole population, whole passes are
+        repeated until budget_s is spent.  Returns (series evaluated, seconds)."""
         n = 64
         while True:
             off = self.off[:n + 1]
@@ -284,7 +322,13 @@ class EvalExpression:
             if dt > budget_s / 4 or n >= self.P:
                 break
             n = min(self.P, n * 4)
-        return n, dt
+        done = n
+        while dt < budget_s and n >= self.P:
+            t0 = time.perf_counter()
+            oracle.support(self.prob.A, self.off, self.cols, nthreads=nthreads)
+            dt += time.perf_counter() - t0
+            done += n
+        return done, dt
 
 
 class GenerationsPaper:
@@ -312,7 +356,7 @@ class GenerationsPaper:
                 "tournament_k": 2, "overlap_tau": 0.5, "elite_frac": 0.25, "penalty_base": 1.2,
                 "p_crossover": 0.5, "step": "one generation (Steps 2-5) as a replayed CUDA graph",
                 "launch_shape": getattr(self, "tuning", None),
-                "l2": "flushed before every timed step (512 MiB overwrite)"}
+                "l2": getattr(self, "l2_desc", None)}
 
     def units_per_step(self) -> int:
         return self.P * self.R
@@ -591,7 +635,7 @@ class EvalBatch:
                 "series_total": self.P, "series_len": [3, 30],
                 "paths": getattr(self, "paths", None),
                 "step": "one persistent launch over all problems (CUDA graph replay)",
-                "l2": "flushed before every timed step (512 MiB overwrite)"}
+                "l2": getattr(self, "l2_desc", None)}
 
     def units_per_step(self) -> int:
         return sum((len(it.offsets) - 1) * it.problem.A.shape[0] for it in self.items)
@@ -612,6 +656,7 @@ class EvalBatch:
         self.b = eb.ebic_batch_create(self.handles, bitems, eb.BATCH_BUILD_TABLES |
                                       eb.BATCH_AUTOTUNE | eb.BATCH_GRAPH)
         d = [eb.ebic_batch_describe(self.b, k) for k in range(len(self.items))]
+        self.path_of = [x["path"] for x in d]
         self.paths = {"bitmask": sum(x["path"] == 2 for x in d),
                       "gather": sum(x["path"] == 1 for x in d),
                       "work_items": d[0]["work_items"], "grid": d[0]["grid"]}
@@ -649,6 +694,19 @@ class EvalBatch:
         return {"value": self.units_per_step() * steps / dt, "unit": "tests/s",
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)}
 
+    def algorithmic_bytes(self, paths) -> tuple[int, str]:
+        """Sum over the problems of support_bytes on each problem's path (as the
+        batch autotuner chose it), plus every CBF in and the counts and fitness
+        out."""
+        total = 0
+        for it, path in zip(self.items, paths):
+            total += support_bytes(it.problem.A, it.offsets, it.cols,
+                                   "bitmask" if path == 2 else "gather")
+            total += it.offsets.nbytes + it.cols.nbytes + (len(it.offsets) - 1) * 12
+        return total, ("per problem as the single-problem pass: bitmask 16 B per (series, "
+                       "128-row block, AND step) while alive, gather 16 B per (series, 4-row "
+                       "group, column read) while alive; + CBF in + inc/fitness out")
+
     def oracle_sample(self, oracle, budget_s: float, nthreads: int):
         it = max(self.items, key=lambda x: x.problem.A.shape[0])
         n = 16
@@ -669,6 +727,99 @@ WORKLOADS = {"eval-expression": EvalExpression, "generations-paper": Generations
 
 
 # ---------------------------------------------------------------------------
+def time_workload(torch, eb, wl, steps: int, warmup: int, flush, clocks=None, ws: int = 1):
+    """W warm-up steps, then `steps` steps each timed with CUDA events on the
+    launching stream, the L2 flushed before each outside the timed interval.
+    Returns (per-step ms list, this library's kernel launches in the timed
+    region, clock summary or None)."""
+    gens = isinstance(wl, GenerationsPaper)
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        wl.step_gpu(torch, eb, stream)
+    torch.cuda.synchronize()
+    if gens:
+        eb.ebic_read_kernel_timing(wl.h, reset=True)   # drop the warm-up replays
+    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    l0 = eb.ebic_kernel_launches()
+    for i in range(steps):
+        flush(i)
+        events[i][0].record(stream)
+        wl.step_gpu(torch, eb, stream)
+        events[i][1].record(stream)
+    torch.cuda.synchronize()
+    launches = eb.ebic_kernel_launches() - l0
+    clk = clocks.stop() if clocks else None
+    return [x.elapsed_time(y) for x, y in events], launches, clk
+
+
+def warm_pass_us(torch, eb, wl, steps: int = 200) -> float:
+    """Mean event time of the fitness pass with the workload left in L2 (no
+    flush): the table (100 MB) fits the 126 MB L2."""
+    stream = torch.cuda.current_stream()
+    for _ in range(5):
+        wl.step_gpu(torch, eb, stream)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    for i in range(steps):
+        ev[i][0].record(stream)
+        wl.step_gpu(torch, eb, stream)
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    return 1e3 * statistics.mean(x.elapsed_time(y) for x, y in ev)
+
+
+def l2_probe(torch, eb, local: int) -> dict:
+    """L2 size (device properties) and the read bandwidth of a buffer of half
+    of it and of one of 2 GiB (the library's read probe, best of 20 passes)."""
+    props = torch.cuda.get_device_properties(local)
+    l2 = int(getattr(props, "L2_cache_size", 0) or 0)
+    out = {"l2_bytes": l2}
+    for name, nbytes in (("l2_read", (l2 // 2) // 16 * 16 if l2 else 32 << 20),
+                         ("hbm_read", 2 << 30)):
+        buf = torch.ones(nbytes // 4, dtype=torch.int32, device="cuda")
+        us = eb.ebic_probe_read_bandwidth(buf, nbytes, 20, torch.cuda.current_stream())
+        out[f"{name}_gbs"] = nbytes / us / 1e3
+        out[f"{name}_buffer_bytes"] = nbytes
+        del buf
+    out["method"] = ("ebic_probe_read_bandwidth: one kernel reads every 16-byte vector of the "
+                     "buffer once; a warm-up pass, then the fastest of 20 passes by CUDA events")
+    return out
+
+
+def generations_block(torch, eb, args, flush, rank: int) -> dict:
+    """The 1000 x 100 generation workload (configs' paper-scale case) measured
+    in the same run: 1,000 timed generations with the L2 flushed before each,
+    the per-kernel breakdown, Step 3's builder against one SM's issue rate,
+    the host-API run, and the sequential oracle."""
+    wl = GenerationsPaper(rank)
+    wl.l2_desc = flush.desc
+    steps = GenerationsPaper.DEFAULT_STEPS
+    wl.setup_gpu(torch, eb, capacity=args.warmup + steps + 16)
+    per_step_ms, launches, _ = time_workload(torch, eb, wl, steps, args.warmup, flush)
+    kb_us, kb_n = eb.ebic_read_kernel_timing(wl.h)
+    if kb_n != steps:
+        raise RuntimeError(f"k_build timed {kb_n} times in {steps} steps")
+    st = wl.check_gpu(torch, eb, args.warmup + steps)
+    kern = {k: round(v, 2) for k, v in wl.profile_gpu(eb).items()}
+    total_s = sum(per_step_ms) / 1e3
+    out = {"workload": wl.config()["workload"], "config": wl.config(),
+           "steps": steps, "warmup": args.warmup,
+           "generations_per_s": steps / total_s,
+           "value": wl.units_per_step() * steps / total_s, "unit": "tests/s",
+           "ms_per_step": 1e3 * total_s / steps, "gpu_launches": int(launches),
+           "run_stats": st, "kernel_us": kern, "k_build_us_timed": kb_us}
+    out["roofline"] = kbuild_roofline(kb_us, kern, load_peaks())
+    out["e2e"] = wl.e2e_gpu(torch, eb, steps)
+    out["cpu_baseline"] = cpu_baseline(wl, budget_s=8.0)
+    eb.ebic_free(wl.h)
+    return out
+
+
 def run_ours(args, ws, rank, local):
     import torch
     import paper_1801_03039_gb300 as eb
@@ -678,37 +829,20 @@ def run_ours(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     eb.build()
     wl = WORKLOADS[args.workload](rank)
+    if getattr(args, "tuning", None):
+        wl.forced_tuning = json.loads(args.tuning)
+    flush = L2Flush(torch)
+    wl.l2_desc = flush.desc
     gens = isinstance(wl, GenerationsPaper)
     if gens:
         wl.setup_gpu(torch, eb, capacity=args.warmup + args.steps + 16)
     else:
         wl.setup_gpu(torch, eb)
-    stream = torch.cuda.current_stream()
-    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
-    for i in range(args.warmup):
-        wl.step_gpu(torch, eb, stream)
-    torch.cuda.synchronize()
-    if gens:
-        eb.ebic_read_kernel_timing(wl.h, reset=True)   # drop the warm-up replays
-    events = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(args.steps)]
     props = torch.cuda.get_device_properties(local)
     bus = getattr(props, "pci_bus_id", None)
     clocks = ClockSampler(bus if isinstance(bus, str) else None) if rank == 0 else None
-    barrier(ws)
-    torch.cuda.synchronize()
-    if clocks:
-        clocks.start()
-    l0 = eb.ebic_kernel_launches()
-    for i in range(args.steps):
-        flush.fill_(i)
-        events[i][0].record(stream)
-        wl.step_gpu(torch, eb, stream)
-        events[i][1].record(stream)
-    torch.cuda.synchronize()
-    launches = eb.ebic_kernel_launches() - l0
-    clk = clocks.stop() if clocks else None
-    per_step_ms = [a.elapsed_time(b) for a, b in events]
+    per_step_ms, launches, clk = time_workload(torch, eb, wl, args.steps, args.warmup, flush,
+                                               clocks, ws)
     total_s = sum(per_step_ms) / 1e3
     extra = {}
     if gens:
@@ -716,10 +850,8 @@ def run_ours(args, ws, rank, local):
         if kb_n != args.steps:
             raise RuntimeError(f"k_build timed {kb_n} times in {args.steps} steps")
         extra["k_build_us_timed"] = kb_us
-        st = wl.check_gpu(torch, eb, args.warmup + args.steps)
-        extra["run_stats"] = st
-        kern = wl.profile_gpu(eb)
-        extra["kernel_us"] = {k: round(v, 2) for k, v in kern.items()}
+        extra["run_stats"] = wl.check_gpu(torch, eb, args.warmup + args.steps)
+        extra["kernel_us"] = {k: round(v, 2) for k, v in wl.profile_gpu(eb).items()}
         if isinstance(wl, GenerationsScreened):
             extra["surrogate"] = wl.compare()
     barrier(ws)
@@ -728,10 +860,16 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         e2e_val = aggregate_max(1.0 / e2e["value"], ws, device=torch.device("cuda", local))
         e2e["value"] = ws / e2e_val
+    peaks = load_peaks()
+    warm_us = warm_pass_us(torch, eb, wl) if isinstance(wl, EvalExpression) else None
+    probe = l2_probe(torch, eb, local) if rank == 0 and not gens else None
+    gen_block = None
+    if rank == 0 and isinstance(wl, EvalExpression):
+        gen_block = generations_block(torch, eb, args, flush, rank)
+    barrier(ws)
     if rank != 0:
         return None
     value = ws * wl.units_per_step() * args.steps / slowest
-    peaks = load_peaks()
     out = {
         "metric": METRIC, "value": value, "unit": "tests/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
@@ -745,55 +883,80 @@ def run_ours(args, ws, rank, local):
     if gens:
         out["generations_per_s"] = ws * args.steps / slowest
     out.update(extra)
-    extra["sm_mhz"] = clk.get("sm_mhz") if clk else None
-    out["roofline"] = roofline(wl, gens, extra, per_step_ms, peaks)
-    out.pop("sm_mhz", None)
+    if gens:
+        out["roofline"] = kbuild_roofline(extra["k_build_us_timed"], extra["kernel_us"], peaks)
+    elif isinstance(wl, EvalBatch):
+        out["roofline"] = hbm_roofline(wl, per_step_ms, peaks, *wl.algorithmic_bytes(wl.path_of),
+                                       kernel="k_support_batch")
+    else:
+        out["roofline"] = hbm_roofline(wl, per_step_ms, peaks, *wl.algorithmic_bytes(),
+                                       kernel=kernel_name(wl.tuning),
+                                       full=wl.full_table_bytes(), warm_us=warm_us, probe=probe)
+    if probe is not None:
+        out["l2_probe"] = probe
+    if gen_block is not None:
+        out["generations"] = gen_block
     out["clocks"] = clk
     if ws == 1:
         out["cpu_baseline"] = cpu_baseline(wl, budget_s=12.0)
     return out
 
 
-def roofline(wl, gens, extra, per_step_ms, peaks):
-    if isinstance(wl, EvalBatch):
-        return {"kernel": "k_support_batch", "bound": "hbm", "achieved": None,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": None, "traffic": None,
-                "note": "mixed bitmask / gather problems: no algorithmic-byte model; the "
-                        "per-problem kernels' rooflines are those of the single-problem workloads"}
-    if not gens:
-        alg_bytes, alg_def = wl.algorithmic_bytes()
-        kernel_s = statistics.mean(per_step_ms) / 1e3
-        achieved = alg_bytes / kernel_s / 1e9
-        return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": read_traffic(wl.name),
-                "algorithmic_bytes": alg_bytes, "algorithmic_def": alg_def,
-                "bytes_without_early_exit": wl.full_table_bytes(),
-                "kernel": "k_support_bitmask_warp",
-                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']})"}
-    kern = extra["kernel_us"]
+def kernel_name(tuning) -> str:
+    k = (tuning or {}).get("kernel", 0)
+    return {3: "k_support_staged", 1: "k_support_bitmask_lane"}.get(k, "k_support_bitmask_warp")
+
+
+def hbm_roofline(wl, per_step_ms, peaks, alg_bytes, alg_def, kernel, full=None, warm_us=None,
+                 probe=None):
+    """Achieved = algorithmic bytes per launch / mean CUDA-event time of a step
+    (one launch), against the measured HBM copy bandwidth."""
+    kernel_s = statistics.mean(per_step_ms) / 1e3
+    achieved = alg_bytes / kernel_s / 1e9
+    out = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+           "frac": achieved / peaks["hbm_gbs"], "traffic": read_traffic(wl.name, kernel),
+           "algorithmic_bytes": alg_bytes, "algorithmic_def": alg_def, "kernel": kernel,
+           "duration_us": 1e3 * statistics.mean(per_step_ms),
+           "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']}; burst copy, "
+                          "the kernel is timed alone)"}
+    if full is not None:
+        out["bytes_without_early_exit"] = full
+    if warm_us is not None:
+        out["warm_l2"] = {"duration_us": warm_us, "achieved": alg_bytes / warm_us / 1e3,
+                          "unit": "GB/s", "note": "no flush between passes: the 100 MB table "
+                                                  "stays in L2"}
+        if probe and probe.get("l2_read_gbs"):
+            out["warm_l2"]["peak"] = probe["l2_read_gbs"]
+            out["warm_l2"]["frac"] = out["warm_l2"]["achieved"] / probe["l2_read_gbs"]
+            out["warm_l2"]["peak_source"] = "l2_probe.l2_read_gbs (measured in this run)"
+    return out
+
+
+def kbuild_roofline(kb_us, kern, peaks):
     dom = max(kern, key=kern.get)
     if dom != "k_build":
         return {"dominant_kernel": dom, "kernel_us": kern}
     # The Step 3 builder is sequential and runs in one CTA (one SM).  Its
     # bound is that SM's issue rate: four warp-instructions per cycle (one
     # per sub-partition) at the SM clock.  Work per launch = the kernel's
-    # warp-instructions, the mean over the launches of a 1,000-generation run
-    # (ncu count committed under profiles/ for this kernel build).  Duration:
-    # the mean of the CUDA events that bracket k_build inside the replayed
-    # graph, over the timed steps.
+    # warp-instructions, from ncu samples of single launches across a
+    # 1,000-generation run (committed under profiles/).  Duration: the mean
+    # of the CUDA events that bracket k_build inside the replayed graph, over
+    # the timed steps.
     prof = read_profile("k_build-generations-paper-1000x100.json")
     inst = prof.get("smsp__inst_executed.sum") if prof else None
-    mhz = (extra.get("sm_mhz") or peaks.get("sm_max_mhz") or 2070.0)
+    mhz = peaks.get("sm_max_mhz") or 2070.0
     peak = 4 * mhz * 1e6 / 1e9                   # G warp-instructions / s
-    dur = extra["k_build_us_timed"] * 1e-6
+    dur = kb_us * 1e-6
     achieved = inst / dur / 1e9 if inst else None
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "G warp-inst/s",
             "frac": achieved / peak if achieved else None,
             "traffic": prof.get("dram_bytes_per_launch") if prof else None,
             "kernel": "k_build (Step 3 builder, one CTA of eight warps on one SM)",
-            "work_per_launch": inst, "work_def": "warp-instructions per launch (ncu)",
-            "peak_source": "4 warp-instructions/cycle (one SM) x median SM clock sampled in this run",
-            "duration_us": extra["k_build_us_timed"],
+            "work_per_launch": inst,
+            "work_def": prof.get("work_def") if prof else None,
+            "peak_source": "4 warp-instructions/cycle (one SM) x the maximum SM clock",
+            "duration_us": kb_us,
             "duration_source": "CUDA events on the launching stream, recorded by event nodes "
                                "around k_build in the replayed graph, mean over the timed steps",
             "kernel_us": kern}
@@ -806,15 +969,17 @@ def read_profile(name: str):
         return None
 
 
-def read_traffic(workload: str):
+def read_traffic(workload: str, kernel: str):
     """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary,
-    if one exists for this workload and kernel build (else null)."""
+    if one exists for this workload and this kernel (else null)."""
     p = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
     try:
         d = json.load(open(p))
-        return d.get("dram_bytes_per_launch")
     except (OSError, ValueError):
         return None
+    if not str(d.get("kernel", "")).startswith(kernel):
+        return None
+    return d.get("dram_bytes_per_launch")
 
 
 def cpu_baseline(wl, budget_s: float):
@@ -827,9 +992,10 @@ def cpu_baseline(wl, budget_s: float):
                           f"core ({dt:.2f} s)"}
     cores = os.cpu_count() or 1
     n, dt = wl.oracle_sample(oracle, budget_s, cores)
+    where = "the largest problem" if isinstance(wl, EvalBatch) else "the population"
     return {"value": n * wl.R / dt, "unit": "tests/s", "cores": cores, "kind": "oracle",
-            "sample": f"first {n} series x all {wl.R} rows of {'the largest problem' if isinstance(wl, EvalBatch) else 'the population'}, one pass, "
-                      f"OpenMP over series on {cores} threads ({dt:.2f} s)"}
+            "sample": f"{n} series x all {wl.R} rows of {where} (the first series, whole "
+                      f"passes repeated), OpenMP over series on {cores} threads ({dt:.2f} s)"}
 
 
 def run_reference(args, ws, rank):
@@ -852,6 +1018,8 @@ def run_reference(args, ws, rank):
         used = 1
     else:
         n, _ = wl.oracle_sample(oracle, 4.0 * per_step, cores)
+        if isinstance(wl, EvalExpression):
+            n = min(n, wl.P)                  # repeated whole passes count once per step
         if isinstance(wl, EvalBatch):
             big = max(wl.items, key=lambda x: x.problem.A.shape[0])
             A, off, cols = big.problem.A, big.offsets[:n + 1], big.cols[:big.offsets[n]]
@@ -889,7 +1057,10 @@ def main(argv=None):
                          "others; 20 for --impl reference)")
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="generations-paper")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="eval-expression")
+    ap.add_argument("--tuning", default=None,
+                    help="eval-expression: a JSON launch shape for ebic_set_eval_tuning instead "
+                         "of the autotuner (e.g. for a profiler run of one shape)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be at least 3")

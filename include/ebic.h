@@ -76,6 +76,15 @@ int32_t ebic_abi_version(void);
  * handles, all threads); for measurement tools.  Library-internal memsets and
  * copies are not counted. */
 uint64_t ebic_kernel_launches(void);
+/* Read-bandwidth probe for measurement tools (no counterpart in the paper):
+ * reads every byte of the device buffer d_buf (`bytes`, a multiple of 16) in
+ * one kernel, once to warm the caches and then `reps` times, each timed with
+ * CUDA events on `stream` (NULL: the legacy default stream; synchronises it).
+ * *out_best_us = the fastest timed pass.  A buffer smaller than the L2 cache
+ * gives the L2 read bandwidth, a larger one the HBM read bandwidth.  The
+ * buffer is only read.  Allocates 4 bytes of device memory for the call. */
+ebic_status ebic_probe_read_bandwidth(const void* d_buf, uint64_t bytes, int32_t reps,
+                                      void* stream, float* out_best_us);
 
 /* ---------------------------------------------------------------------------
  * Matrix.  Step 1 of the "EBIC Algorithm" section: the data is placed on the
@@ -162,11 +171,17 @@ ebic_status ebic_get_eval_tuning(ebic_handle h, ebic_eval_tuning_t* out);
  * ebic_eval_population_dev, which it is) under a short list of launch shapes
  * for the handle's current path, timing each with CUDA events on `stream`, and
  * keeps the fastest for later evaluations.  Synchronises `stream`.  *chosen
- * and *best_us (nullable) receive the shape and its time per launch. */
+ * and *best_us (nullable) receive the shape and its time per launch.
+ * flags: 0 = time launches back to back (the table stays in L2 when it fits,
+ * as in a generation loop); EBIC_TUNE_COLD_L2 = time each launch after the L2
+ * has been emptied (an overwrite of one buffer of twice the L2 size, then a
+ * read of another; both allocated for the call and freed), the case of a
+ * table that other work evicts between passes.  Other bits: EBIC_ERR_ARG. */
+#define EBIC_TUNE_COLD_L2 1
 ebic_status ebic_autotune_eval(ebic_handle h, const int32_t* d_offsets, const int32_t* d_cols,
                                int32_t P, int32_t total_cols, int32_t sigma, int32_t support_mode,
                                uint32_t* d_inc, uint32_t* d_dec, double* d_fitness, void* stream,
-                               ebic_eval_tuning_t* chosen, float* best_us);
+                               int32_t flags, ebic_eval_tuning_t* chosen, float* best_us);
 
 /* ---------------------------------------------------------------------------
  * Population evaluation: Step 4 of the "EBIC Algorithm" section with Eq. (1).

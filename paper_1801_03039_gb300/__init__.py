@@ -23,6 +23,7 @@ __all__ = [
     "EbicError", "build", "lib", "ebic_kernel_launches", "ebic_load_matrix", "ebic_load_matrix_dev", "ebic_free",
     "ebic_matrix_shape", "ebic_build_pair_table", "ebic_pair_table_bytes",
     "ebic_read_pair_words", "ebic_set_path", "ebic_set_eval_tuning", "ebic_get_eval_tuning",
+    "TUNE_COLD_L2", "ebic_probe_read_bandwidth",
     "ebic_autotune_eval", "ebic_eval_population",
     "ebic_eval_population_dev", "ebic_eval_population_dev_noalloc", "ebic_check_device_error", "ebic_default_params",
     "ebic_batch_create", "ebic_batch_eval", "ebic_batch_describe", "ebic_batch_free",
@@ -84,6 +85,7 @@ _SIGS = {
     "ebic_last_error": ([], ctypes.c_char_p),
     "ebic_abi_version": ([], _I32),
     "ebic_kernel_launches": ([], ctypes.c_uint64),
+    "ebic_probe_read_bandwidth": ([_P, ctypes.c_uint64, _I32, _P, _P], _I32),
     "ebic_load_matrix": ([_P, _I32, _I32, _P], _I32),
     "ebic_load_matrix_dev": ([_P, _I32, _I32, _P, _P], _I32),
     "ebic_free": ([_P], None),
@@ -94,7 +96,8 @@ _SIGS = {
     "ebic_set_path": ([_P, _I32], _I32),
     "ebic_set_eval_tuning": ([_P, _P], _I32),
     "ebic_get_eval_tuning": ([_P, _P], _I32),
-    "ebic_autotune_eval": ([_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P, _P, _P], _I32),
+    "ebic_autotune_eval": ([_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P, _I32, _P, _P],
+                           _I32),
     "ebic_eval_population": ([_P, _P, _P, _I32, _I32, _I32, _P, _P, _P], _I32),
     "ebic_eval_population_dev": ([_P, _P, _P, _I32, _I32, _I32, _I32, _P, _P, _P, _P], _I32),
     "ebic_check_device_error": ([_P], _I32),
@@ -209,6 +212,14 @@ def ebic_kernel_launches() -> int:
     return int(lib().ebic_kernel_launches())
 
 
+def ebic_probe_read_bandwidth(d_buf, nbytes: int, reps: int = 20, stream=None) -> float:
+    """Fastest of `reps` timed read passes over a device buffer, in us."""
+    us = ctypes.c_float()
+    _check(lib().ebic_probe_read_bandwidth(_dev(d_buf), int(nbytes), int(reps), _stream(stream),
+                                           ctypes.byref(us)))
+    return us.value
+
+
 def ebic_free(h):
     if h is not None and h.value:
         lib().ebic_free(h)
@@ -263,14 +274,18 @@ def ebic_get_eval_tuning(h) -> dict:
     return {f: getattr(t, f) for f, _ in EvalTuning._fields_}
 
 
+TUNE_COLD_L2 = 1
+
+
 def ebic_autotune_eval(h, d_offsets, d_cols, P: int, total_cols: int, sigma: int,
-                       support_mode: int, d_inc, d_dec, d_fitness, stream=None):
-    """Times launch shapes on this device population; returns (shape dict, us)."""
+                       support_mode: int, d_inc, d_dec, d_fitness, stream=None, flags: int = 0):
+    """Times launch shapes on this device population; returns (shape dict, us).
+    flags=TUNE_COLD_L2 times every launch with the L2 emptied first."""
     t = EvalTuning()
     us = ctypes.c_float()
     _check(lib().ebic_autotune_eval(h, _dev(d_offsets), _dev(d_cols), int(P), int(total_cols),
                                     int(sigma), int(support_mode), _dev(d_inc), _dev(d_dec),
-                                    _dev(d_fitness), _stream(stream), ctypes.byref(t),
+                                    _dev(d_fitness), _stream(stream), int(flags), ctypes.byref(t),
                                     ctypes.byref(us)))
     return {f: getattr(t, f) for f, _ in EvalTuning._fields_}, us.value
 

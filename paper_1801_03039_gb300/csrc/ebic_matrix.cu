@@ -432,13 +432,37 @@ static ebic_status eval_any(ebic_ctx* h, const Pop& pop, EvalArgs a, cudaStream_
   return EBIC_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Read-bandwidth probe: every 16-byte vector of a device buffer is loaded once
+// per pass (grid-stride, 4 vectors in flight per thread) and XOR-folded; the
+// fold is stored only if it equals a value no buffer produces by chance, so
+// the loads cannot be dropped.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(512)
+k_read_probe(const uint4* __restrict__ buf, size_t n4, uint32_t magic, uint32_t* __restrict__ sink) {
+  const size_t stride = (size_t)gridDim.x * blockDim.x;
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t acc = 0;
+  for (; i + 3 * stride < n4; i += 4 * stride) {
+    const uint4 a = __ldcg(buf + i), b = __ldcg(buf + i + stride), c = __ldcg(buf + i + 2 * stride),
+                d = __ldcg(buf + i + 3 * stride);
+    acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^
+           d.z ^ d.w;
+  }
+  for (; i < n4; i += stride) {
+    const uint4 a = __ldcg(buf + i);
+    acc ^= a.x ^ a.y ^ a.z ^ a.w;
+  }
+  if (acc == magic) *sink = acc;
+}
+
 // Autotuner: times candidate launch shapes on the caller's population (each
-// candidate once to warm up, then 3 launches between two events) and keeps
-// the fastest in h->tuning.  The candidates are evaluations, so the outputs
+// candidate once to warm up, then 3 launches each between two events, or 5
+// after emptying the L2 with `cold`) and keeps the fastest in h->tuning.  The candidates are evaluations, so the outputs
 // hold valid results afterwards.
 template <bool CHECK, class Pop>
 static ebic_status autotune_any(ebic_ctx* h, const Pop& pop, const EvalArgs& a, cudaStream_t s,
-                                float* best_us) {
+                                float* best_us, bool cold = false) {
   std::vector<ebic_eval_tuning_t> cands;
   const int32_t path = resolve_path(h);
   const bool dec = a.want_dec != 0 || a.mode == EBIC_SUPPORT_INC_PLUS_DEC;
@@ -467,34 +491,61 @@ static ebic_status autotune_any(ebic_ctx* h, const Pop& pop, const EvalArgs& a, 
       cands.push_back({0, 0, vp, 0, 0, 0, 0, 0});
     }
   }
-  cudaEvent_t e0, e1;
-  EBIC_CUDA_TRY(cudaEventCreate(&e0));
-  EBIC_CUDA_TRY(cudaEventCreate(&e1));
+  // With `cold`, every timed launch follows an overwrite of one buffer of
+  // twice the L2 size and a read of another: the L2 then holds no line of
+  // the workload and no dirty line.
+  void* flush = nullptr;
+  size_t flush_bytes = 0;
+  if (cold) {
+    int l2 = 0;
+    EBIC_CUDA_TRY(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, h->device));
+    flush_bytes = std::max<size_t>((size_t)2 * (size_t)l2, (size_t)64 << 20) / 16 * 16;
+    EBIC_CUDA_TRY(cudaMalloc(&flush, 2 * flush_bytes));
+  }
+  auto clear_l2 = [&]() {
+    cudaMemsetAsync(flush, 0x5a, flush_bytes, s);
+    k_read_probe<<<(unsigned)h->sm_count * 4, 512, 0, s>>>(
+        reinterpret_cast<const uint4*>(static_cast<char*>(flush) + flush_bytes), flush_bytes / 16,
+        0x9e3779b9u, static_cast<uint32_t*>(flush));
+  };
+  const int reps = cold ? 5 : 3;      // timed launches per candidate
+  cudaEvent_t ev[10];
+  for (cudaEvent_t& e : ev) EBIC_CUDA_TRY(cudaEventCreate(&e));
   float best = 1e30f;
   ebic_eval_tuning_t chosen = cands.empty() ? ebic_eval_tuning_t{} : cands[0];
   ebic_status st = EBIC_OK;
   for (const ebic_eval_tuning_t& c : cands) {
     h->tuning = c;
     if ((st = eval_any<CHECK>(h, pop, a, s)) != EBIC_OK) break;
-    cudaEventRecord(e0, s);
-    for (int r = 0; r < 3 && st == EBIC_OK; ++r) st = eval_any<CHECK>(h, pop, a, s);
+    for (int r = 0; r < reps && st == EBIC_OK; ++r) {
+      if (cold) clear_l2();
+      cudaEventRecord(ev[2 * r], s);
+      st = eval_any<CHECK>(h, pop, a, s);
+      cudaEventRecord(ev[2 * r + 1], s);
+    }
     if (st != EBIC_OK) break;
-    cudaEventRecord(e1, s);
-    if (cudaEventSynchronize(e1) != cudaSuccess) {
+    if (cudaEventSynchronize(ev[2 * reps - 1]) != cudaSuccess) {
       st = fail(EBIC_ERR_CUDA, "autotune: event wait failed");
       break;
     }
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, e0, e1);
+    for (int r = 0; r < reps; ++r) {
+      float x = 0.f;
+      cudaEventElapsedTime(&x, ev[2 * r], ev[2 * r + 1]);
+      ms += x;
+    }
     if (ms < best) {
       best = ms;
       chosen = c;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+  for (cudaEvent_t& e : ev) cudaEventDestroy(e);
+  if (flush) {
+    cudaStreamSynchronize(s);
+    cudaFree(flush);
+  }
   h->tuning = chosen;
-  if (best_us) *best_us = best * 1000.f / 3.f;
+  if (best_us) *best_us = best * 1000.f / (float)reps;
   return st;
 }
 
@@ -696,6 +747,43 @@ extern "C" ebic_status ebic_eval_population_dev_noalloc(ebic_handle h, const int
   return EBIC_OK;
 }
 
+
+extern "C" ebic_status ebic_probe_read_bandwidth(const void* d_buf, uint64_t bytes, int32_t reps,
+                                                 void* stream, float* out_best_us) {
+  if (!d_buf || !out_best_us || reps < 1 || bytes < 16 || bytes % 16)
+    return fail(EBIC_ERR_ARG, "probe: need a device buffer of a multiple of 16 bytes and reps >= 1");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int dev = 0, sms = 0;
+  EBIC_CUDA_TRY(cudaGetDevice(&dev));
+  EBIC_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  uint32_t* sink = nullptr;
+  EBIC_CUDA_TRY(cudaMalloc(&sink, sizeof(uint32_t)));
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  const size_t n4 = bytes / 16;
+  const unsigned grid = (unsigned)sms * 4;
+  float best = 1e30f;
+  ebic_status st = EBIC_OK;
+  for (int r = 0; r <= reps && st == EBIC_OK; ++r) {     // pass 0 warms the caches
+    cudaEventRecord(e0, s);
+    k_read_probe<<<grid, 512, 0, s>>>(static_cast<const uint4*>(d_buf), n4, 0x9e3779b9u, sink);
+    cudaEventRecord(e1, s);
+    count_launches(1);
+    if (cudaGetLastError() != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+      st = fail(EBIC_ERR_CUDA, "probe launch failed");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (r > 0 && ms < best) best = ms;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(sink);
+  if (st == EBIC_OK) *out_best_us = best * 1000.f;
+  return st;
+}
 
 // ===========================================================================
 // C ABI
@@ -906,7 +994,7 @@ ebic_status ebic_eval_population_dev(ebic_handle h, const int32_t* d_offsets,
 ebic_status ebic_autotune_eval(ebic_handle h, const int32_t* d_offsets, const int32_t* d_cols,
                                int32_t P, int32_t total_cols, int32_t sigma, int32_t support_mode,
                                uint32_t* d_inc, uint32_t* d_dec, double* d_fitness, void* stream,
-                               ebic_eval_tuning_t* chosen, float* best_us) {
+                               int32_t flags, ebic_eval_tuning_t* chosen, float* best_us) {
   if (!h) return fail(EBIC_ERR_ARG, "null handle");
   if (P <= 0 || P > (1 << 24)) return fail(EBIC_ERR_ARG, "P = %d outside [1, 2^24]", P);
   if (!d_offsets || !d_cols || !d_inc || !d_fitness) return fail(EBIC_ERR_ARG, "null pointer");
@@ -929,7 +1017,8 @@ ebic_status ebic_autotune_eval(ebic_handle h, const int32_t* d_offsets, const in
   }
   if (resolve_path(h) == EBIC_PATH_BITMASK && !h->LT) EBIC_TRY(build_pair_table(h, s));
   CbfPop pop{d_offsets, d_cols, total_cols};
-  EBIC_TRY(autotune_any<true>(h, pop, a, s, best_us));
+  if (flags & ~EBIC_TUNE_COLD_L2) return fail(EBIC_ERR_ARG, "unknown autotune flags %d", flags);
+  EBIC_TRY(autotune_any<true>(h, pop, a, s, best_us, (flags & EBIC_TUNE_COLD_L2) != 0));
   if (chosen) *chosen = h->tuning;
   return EBIC_OK;
 }

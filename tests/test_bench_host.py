@@ -147,3 +147,40 @@ def test_byte_counts_of_the_fitness_pass():
     assert wl.full_table_bytes() == 6 * row + io
     alg, _ = wl.algorithmic_bytes()
     assert io + 157 * 16 <= alg <= wl.full_table_bytes()   # the first step reads every block
+
+
+def _brute_bytes(A, off, cols, unit, first_column):
+    R = A.shape[0]
+    Rp = (R + 127) // 128 * 128
+    total = 0
+    for i in range(len(off) - 1):
+        s = cols[off[i]:off[i + 1]]
+        if len(s) < 2:
+            continue
+        alive = np.zeros(Rp, bool)
+        alive[:] = True                                   # the running AND starts all ones
+        if first_column:
+            total += Rp // unit
+        for t in range(len(s) - 1):
+            total += int(alive.reshape(-1, unit).any(axis=1).sum())
+            rises = np.zeros(Rp, bool)
+            rises[:R] = A[:, s[t]] < A[:, s[t + 1]]
+            alive &= rises
+    return 16 * total
+
+
+@pytest.mark.parametrize("path,unit,first", [("bitmask", 128, False), ("gather", 4, True)])
+def test_support_bytes_matches_a_direct_count(path, unit, first):
+    """The roofline's algorithmic-byte model against a direct count of the
+    alive 128-row blocks (bitmask) or 4-row groups (gather) before every AND
+    step, on ragged shapes with ties, NaN and repeated columns."""
+    rng = np.random.default_rng(3)
+    for R, C in ((1, 3), (130, 5), (700, 9), (2000, 12)):
+        A = rng.integers(-3, 4, (R, C)).astype(np.float32)
+        A[rng.random(A.shape) < 0.02] = np.nan
+        seqs = [rng.integers(0, C, int(rng.integers(1, 7))).tolist() for _ in range(40)]
+        seqs += [list(range(C)), [0]]
+        off = np.zeros(len(seqs) + 1, np.int32)
+        off[1:] = np.cumsum([len(x) for x in seqs])
+        cols = np.array([c for x in seqs for c in x], np.int32)
+        assert bench.support_bytes(A, off, cols, path) == _brute_bytes(A, off, cols, unit, first)

@@ -104,6 +104,26 @@ def test_paper_1000x100_population_600():
              sigma=25, iterations=30)
 
 
+def test_paper_1000x100_thousand_generations():
+    """The benchmark's generation workload over its whole run length: 1,000
+    generations of the 1000 x 100 matrix (P = 600, lengths 3-20, sigma 25),
+    populations and top-rank lists compared at generations 1, 250, 500, 999
+    and 1,000, and the run statistics at the end."""
+    prob = synth.matrix_paper(seed=0)
+    st = run_both(prob.A, gens_to_check={1, 250, 500, 999, 1000}, pop_size=600, len_min=3,
+                  len_max=20, sigma=25, iterations=1000)
+    assert st["generations_done"] == 1000 and st["tabu_hits_total"] > 0
+
+
+def test_paper_1000x100_screened_two_hundred_generations():
+    """Screening with pseudo scores (8 candidates per attempt) on the same
+    workload for 200 generations."""
+    prob = synth.matrix_paper(seed=0)
+    st = run_both(prob.A, gens_to_check={1, 100, 199, 200}, pop_size=600, len_min=3,
+                  len_max=20, sigma=25, iterations=200, oversample=8)
+    assert st["generations_done"] == 200
+
+
 @pytest.mark.parametrize("variant", [
     dict(tournament_k=1), dict(tournament_k=3), dict(tournament_k=4),
     dict(p_crossover=0.0), dict(p_crossover=1.0), dict(fitness_support=1),

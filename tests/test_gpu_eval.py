@@ -256,6 +256,22 @@ def test_long_series_batches(kernel, batch_steps, nv):
         eb.ebic_free(h)
 
 
+def test_autotuner_rejects_unknown_flags():
+    torch = pytest.importorskip("torch")
+    prob = synth.matrix_tiny(seed=0)
+    off, cols = synth.population(0, 10, 20, 2, 6)
+    dev = torch.device("cuda:0")
+    h = eb.ebic_load_matrix(prob.A)
+    try:
+        with pytest.raises(eb.EbicError) as e:
+            eb.ebic_autotune_eval(h, torch.from_numpy(off).to(dev), torch.from_numpy(cols).to(dev),
+                                  10, len(cols), 10, 0, torch.zeros(10, dtype=torch.int32, device=dev),
+                                  None, torch.zeros(10, dtype=torch.float64, device=dev), flags=2)
+        assert e.value.status == 1
+    finally:
+        eb.ebic_free(h)
+
+
 def test_tuning_rejects_bad_batch():
     prob = synth.matrix_tiny(seed=0)
     h = eb.ebic_load_matrix(prob.A)
@@ -270,8 +286,9 @@ def test_tuning_rejects_bad_batch():
         eb.ebic_free(h)
 
 
+@pytest.mark.parametrize("flags", [0, 1])
 @pytest.mark.parametrize("which", ["paper", "expression"])
-def test_autotuner_keeps_results_exact(which):
+def test_autotuner_keeps_results_exact(which, flags):
     torch = pytest.importorskip("torch")
     if which == "paper":
         prob, P, lo, hi, sig = synth.matrix_paper(seed=7), 600, 3, 20, 25
@@ -289,7 +306,7 @@ def test_autotuner_keeps_results_exact(which):
             inc = torch.zeros(P, dtype=torch.int32, device=dev)
             fit = torch.zeros(P, dtype=torch.float64, device=dev)
             shape, us = eb.ebic_autotune_eval(h, d_off, d_cols, P, len(cols), sig, 0, inc, None,
-                                              fit)
+                                              fit, flags=flags)
             assert us > 0 and shape == eb.ebic_get_eval_tuning(h)
             assert_bits_equal(inc.cpu().numpy().view(np.uint32), oinc, f"inc {path}")
             assert_bits_equal(fit.cpu().numpy(), ofit, f"fit {path}")
