@@ -914,7 +914,8 @@ def hbm_roofline(wl, per_step_ms, peaks, alg_bytes, alg_def, kernel, full=None, 
     kernel_s = statistics.mean(per_step_ms) / 1e3
     achieved = alg_bytes / kernel_s / 1e9
     out = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-           "frac": achieved / peaks["hbm_gbs"], "traffic": read_traffic(wl.name, kernel),
+           "frac": achieved / peaks["hbm_gbs"],
+           "traffic": read_traffic(wl.name, kernel, getattr(wl, "tuning", None)),
            "algorithmic_bytes": alg_bytes, "algorithmic_def": alg_def, "kernel": kernel,
            "duration_us": 1e3 * statistics.mean(per_step_ms),
            "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peaks['source']}; burst copy, "
@@ -969,9 +970,10 @@ def read_profile(name: str):
         return None
 
 
-def read_traffic(workload: str, kernel: str):
+def read_traffic(workload: str, kernel: str, tuning=None):
     """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary,
-    if one exists for this workload and this kernel (else null)."""
+    if one exists for this workload, this kernel and (for the staged kernel)
+    this number of staged steps (else null)."""
     p = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
     try:
         d = json.load(open(p))
@@ -979,6 +981,10 @@ def read_traffic(workload: str, kernel: str):
         return None
     if not str(d.get("kernel", "")).startswith(kernel):
         return None
+    by_dense = d.get("dram_bytes_per_launch_by_dense_steps")
+    if by_dense is not None:
+        dense = (tuning or {}).get("dense_steps") or 4
+        return by_dense.get(str(dense))
     return d.get("dram_bytes_per_launch")
 
 
