@@ -228,6 +228,9 @@ ebic_status ebic_check_device_error(ebic_handle h);
  *   - P above EBIC_NOALLOC_MAX_SERIES gives EBIC_ERR_ARG (nothing queued).
  *   - It never builds the pair table: with the table already built (and the
  *     path not forced to gather) it uses it, otherwise the gather path.
+ *   - Its launch shape is fixed (the warp kernel, 8 AND steps per exit test,
+ *     the automatic split of series into parts): the handle's tuning, from
+ *     ebic_set_eval_tuning or ebic_autotune_eval, does not apply to it.
  *   - The first call on each device looks up the array's device address with
  *     that device current; make that first call before any stream capture.
  *   - All calls share the array, which keeps the last call's contents (each

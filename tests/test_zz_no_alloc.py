@@ -8,6 +8,7 @@ import pytest
 
 import paper_1801_03039_gb300 as eb
 from paper_1801_03039_gb300 import synth
+from helpers import assert_bits_equal, oracle_eval
 
 pytestmark = pytest.mark.gpu
 
@@ -51,6 +52,10 @@ def test_matches_the_regular_entry_point_on_two_calls(torch, use_table):
             assert np.array_equal(fit.cpu().numpy().view(np.uint64),
                                   want_fit.cpu().numpy().view(np.uint64)), f"call {call}: fitness"
         assert int(want_inc.max()) >= 1500          # the planted series were counted
+        # and both equal the oracle's counts and Eq. (1) values
+        oinc, _, ofit = oracle_eval(prob.A, off, cols, sigma)
+        assert_bits_equal(inc.cpu().numpy().view(np.uint32), oinc, "inc vs oracle")
+        assert_bits_equal(fit.cpu().numpy(), ofit, "fitness vs oracle")
     finally:
         eb.ebic_free(h)
 
