@@ -151,9 +151,13 @@ ebic_status ebic_set_path(ebic_handle h, int32_t path);
  *   stages (kernel 3): items in flight per group, 2..4 (0 = 2).
  *   groups (kernel 3): at most this many groups of warps per CTA (0 = as many
  *     as fit one CTA per SM).
+ *   dynamic_rounds (kernel 3): groups take items in a fixed stride, except
+ *     for this many last rounds of the even share plus the remainder, which
+ *     they claim one at a time from a counter (1 .. 64; 0 or -1 = none,
+ *     every item in the stride).
  *   vecs_per_lane also sets, for kernel 3, the 16-byte vectors each
- *     consumer thread carries: 1 or 2 (0 = 2 for table entries over 64
- *     vectors). */
+ *     consumer thread carries: 1, 2 or 3 (0 = 2 for table entries over 64
+ *     vectors; with 3 the remaining steps go two per batch). */
 typedef struct {
   int32_t kernel;
   int32_t vecs_per_part_bitmask;
@@ -163,6 +167,7 @@ typedef struct {
   int32_t dense_steps;
   int32_t stages;
   int32_t groups;
+  int32_t dynamic_rounds;
 } ebic_eval_tuning_t;
 /* NULL restores the automatic choice. */
 ebic_status ebic_set_eval_tuning(ebic_handle h, const ebic_eval_tuning_t* tuning);

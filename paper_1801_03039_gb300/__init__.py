@@ -256,15 +256,16 @@ class EvalTuning(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("vecs_per_part_bitmask", ctypes.c_int32),
                 ("vecs_per_part_gather", ctypes.c_int32), ("batch_steps", ctypes.c_int32),
                 ("vecs_per_lane", ctypes.c_int32), ("dense_steps", ctypes.c_int32),
-                ("stages", ctypes.c_int32), ("groups", ctypes.c_int32)]
+                ("stages", ctypes.c_int32), ("groups", ctypes.c_int32),
+                ("dynamic_rounds", ctypes.c_int32)]
 
 
 def ebic_set_eval_tuning(h, kernel: int = 0, vecs_per_part_bitmask: int = 0,
                          vecs_per_part_gather: int = 0, batch_steps: int = 0,
                          vecs_per_lane: int = 0, dense_steps: int = 0, stages: int = 0,
-                         groups: int = 0):
+                         groups: int = 0, dynamic_rounds: int = 0):
     t = EvalTuning(kernel, vecs_per_part_bitmask, vecs_per_part_gather, batch_steps,
-                   vecs_per_lane, dense_steps, stages, groups)
+                   vecs_per_lane, dense_steps, stages, groups, dynamic_rounds)
     _check(lib().ebic_set_eval_tuning(h, ctypes.byref(t)))
 
 

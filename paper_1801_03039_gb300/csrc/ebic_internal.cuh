@@ -71,6 +71,8 @@ struct ebic_ctx {
   ebic_eval_tuning_t tuning{};     // launch shape of evaluations (zeros = automatic)
   cudaStream_t stream = nullptr;  // internal stream for the host-buffer calls
   int* d_err = nullptr;           // device error flag (0 = none)
+  uint32_t* d_claim = nullptr;    // item counter of the staged kernel and its
+                                  // finished-scout count (zero between launches)
   int32_t sm_count = 0;           // streaming multiprocessors of the device
   ebic::DevBuf tickets;           // per-series partial counts and arrivals of split
                                   // series (2 x 64-bit words each, zero between launches)

@@ -306,7 +306,7 @@ int32_t resolve_path(ebic_ctx* h) {
 
 // Geometry of the staged kernel for this handle and tuning; false if it
 // cannot run here (a group does not fit one CTA).  Parts hold at most 256
-// vectors; a consumer thread carries `vecs_per_lane` of them (1 or 2; 0 =
+// vectors; a consumer thread carries `vecs_per_lane` of them (1 to 3; 0 =
 // 2 for parts over 64 vectors).
 static bool staged_geometry(const ebic_ctx* h, const ebic_eval_tuning_t& tu, int32_t P,
                             StagedGeom* out) {
@@ -315,7 +315,8 @@ static bool staged_geometry(const ebic_ctx* h, const ebic_eval_tuning_t& tu, int
   const int32_t parts = (V + 255) / 256;
   g.vpp = (V + parts - 1) / parts;
   g.items_per = parts;
-  g.nvt = tu.vecs_per_lane == 1 ? 1 : (tu.vecs_per_lane == 2 ? 2 : (g.vpp > 64 ? 2 : 1));
+  g.nvt = (tu.vecs_per_lane >= 1 && tu.vecs_per_lane <= 3) ? tu.vecs_per_lane
+                                                           : (g.vpp > 64 ? 2 : 1);
   g.gw = (g.vpp + 32 * g.nvt - 1) / (32 * g.nvt);
   g.dense = tu.dense_steps > 0 ? tu.dense_steps : 4;
   g.ns = tu.stages > 0 ? tu.stages : 2;
@@ -353,11 +354,21 @@ static ebic_status launch_staged(ebic_ctx* h, const Pop& pop, const EvalArgs& a,
   const int64_t grid = std::min<int64_t>((int64_t)h->sm_count * per_sm,
                                          (n_items + g.groups - 1) / g.groups);
   g.n_scouts = (int32_t)(grid * g.groups);
+  // fixed-stride rounds: the even share less the last `dynamic_rounds`
+  // rounds, whose items and the remainder are claimed dynamically; 0 or -1
+  // (the default): every item in the fixed stride (measured as fast as any
+  // dynamic share on the 20,000 x 200 pass, whose claims cost what the
+  // balance gains)
+  const int64_t rounds = n_items / g.n_scouts;
+  const int32_t dyn_rounds = h->tuning.dynamic_rounds;
+  g.static_rounds = dyn_rounds <= 0 ? (int32_t)(rounds + 1)
+                                    : (int32_t)std::max<int64_t>(0, rounds - dyn_rounds);
   if (g.items_per > 1)
     EBIC_TRY(h->tickets.reserve_zeroed((size_t)a.P * 2 * sizeof(unsigned long long), s));
   count_launches(1);
   kern<<<(unsigned)grid, threads, smem, s>>>(h->LT, h->C, h->W, h->R, pop, a, g,
-                                             h->tickets.as<uint32_t>(), h->LN, h->d_err);
+                                             h->tickets.as<uint32_t>(), h->LN, h->d_err,
+                                             h->d_claim);
   EBIC_CUDA_TRY(cudaGetLastError());
   return EBIC_OK;
 }
@@ -372,8 +383,9 @@ static ebic_status eval_any(ebic_ctx* h, const Pop& pop, EvalArgs a, cudaStream_
   if (path == EBIC_PATH_BITMASK && h->tuning.kernel == 3 && !dec && !a.dec) {
     StagedGeom g;
     if (staged_geometry(h, h->tuning, a.P, &g))
-      return g.nvt == 2 ? launch_staged<CHECK, Pop, 2>(h, pop, a, g, s)
-                        : launch_staged<CHECK, Pop, 1>(h, pop, a, g, s);
+      return g.nvt == 3   ? launch_staged<CHECK, Pop, 3>(h, pop, a, g, s)
+             : g.nvt == 2 ? launch_staged<CHECK, Pop, 2>(h, pop, a, g, s)
+                          : launch_staged<CHECK, Pop, 1>(h, pop, a, g, s);
   }
   int32_t vpi = 0, ipc = 1;
   bool lane_kernel = false;
@@ -468,19 +480,19 @@ static ebic_status autotune_any(ebic_ctx* h, const Pop& pop, const EvalArgs& a, 
   const bool dec = a.want_dec != 0 || a.mode == EBIC_SUPPORT_INC_PLUS_DEC;
   if (path == EBIC_PATH_BITMASK) {
     const int32_t V = h->W >> 2;
-    if (V <= 32) cands.push_back({1, 0, 0, 0, 0, 0, 0, 0});
+    if (V <= 32) cands.push_back({1, 0, 0, 0, 0, 0, 0, 0, 0});
     if (!dec && V > 32) {
       for (int32_t nvt : {1, 2})
-        for (int32_t dense : {4, 6}) cands.push_back({3, 0, 0, 0, nvt, dense, 2, 0});
-      cands.push_back({3, 0, 0, 0, 0, 4, 3, 0});
+        for (int32_t dense : {4, 6}) cands.push_back({3, 0, 0, 0, nvt, dense, 2, 0, 0});
+      cands.push_back({3, 0, 0, 0, 0, 4, 3, 0, 0});
     }
     const int32_t parts[] = {32, 64, 128, 256, 0};
     for (int32_t vp : parts) {
       if (vp > 0 && vp / 2 >= V) continue;
-      cands.push_back({2, vp, 0, 8, 1, 0, 0, 0});
+      cands.push_back({2, vp, 0, 8, 1, 0, 0, 0, 0});
       if (!dec) {
-        cands.push_back({2, vp, 0, 4, 1, 0, 0, 0});
-        cands.push_back({2, vp, 0, 4, 2, 0, 0, 0});
+        cands.push_back({2, vp, 0, 4, 1, 0, 0, 0, 0});
+        cands.push_back({2, vp, 0, 4, 2, 0, 0, 0, 0});
       }
     }
   } else {
@@ -488,7 +500,7 @@ static ebic_status autotune_any(ebic_ctx* h, const Pop& pop, const EvalArgs& a, 
     const int32_t parts[] = {32, 64, 128, 256, 512, 1024, 0};
     for (int32_t vp : parts) {
       if (vp > 0 && vp / 2 >= V) continue;
-      cands.push_back({0, 0, vp, 0, 0, 0, 0, 0});
+      cands.push_back({0, 0, vp, 0, 0, 0, 0, 0, 0});
     }
   }
   // With `cold`, every timed launch follows an overwrite of one buffer of
@@ -623,6 +635,7 @@ static void destroy(ebic_ctx* h) {
   if (h->LN) cudaFree(h->LN);
   if (h->LT) cudaFree(h->LT);
   if (h->d_err) cudaFree(h->d_err);
+  if (h->d_claim) cudaFree(h->d_claim);
   h->tickets.release();
   h->st_off.release();
   h->st_cols.release();
@@ -641,6 +654,8 @@ static ebic_status place(ebic_ctx* h, const float* rowmajor_dev, cudaStream_t s)
   EBIC_CUDA_TRY(cudaMalloc(&h->A_c, (size_t)h->C * h->R_pad * sizeof(float)));
   EBIC_CUDA_TRY(cudaMalloc(&h->d_err, sizeof(int)));
   EBIC_CUDA_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int), s));
+  EBIC_CUDA_TRY(cudaMalloc(&h->d_claim, 2 * sizeof(uint32_t)));
+  EBIC_CUDA_TRY(cudaMemsetAsync(h->d_claim, 0, 2 * sizeof(uint32_t), s));
   EBIC_CUDA_TRY(cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device));
   // LN[m] = log(m) with the host C library, m = 0 .. 2R + 1.
   const size_t nln = 2 * (size_t)h->R + 2;
@@ -894,13 +909,15 @@ ebic_status ebic_set_eval_tuning(ebic_handle h, const ebic_eval_tuning_t* t) {
   if (!(t->stages == 0 || (t->stages >= 2 && t->stages <= 4)))
     return fail(EBIC_ERR_ARG, "stages must be 0 or 2 .. 4");
   if (t->groups < 0 || t->groups > 15) return fail(EBIC_ERR_ARG, "groups must be 0 .. 15");
+  if (t->dynamic_rounds < -1 || t->dynamic_rounds > 64)
+    return fail(EBIC_ERR_ARG, "dynamic_rounds must be -1 .. 64");
   if (t->vecs_per_part_bitmask < 0 || t->vecs_per_part_gather < 0)
     return fail(EBIC_ERR_ARG, "negative part size");
   if (!(t->batch_steps == 0 || t->batch_steps == 4 || t->batch_steps == 8))
     return fail(EBIC_ERR_ARG, "batch_steps must be 0, 4 or 8");
   if (!(t->vecs_per_lane == 0 || t->vecs_per_lane == 1 || t->vecs_per_lane == 2 ||
-        t->vecs_per_lane == 4))
-    return fail(EBIC_ERR_ARG, "vecs_per_lane must be 0, 1, 2 or 4");
+        t->vecs_per_lane == 4 || (t->vecs_per_lane == 3 && t->kernel == 3)))
+    return fail(EBIC_ERR_ARG, "vecs_per_lane must be 0, 1, 2 or 4 (3: kernel 3 only)");
   if (t->vecs_per_lane == 4 && t->batch_steps == 8)
     return fail(EBIC_ERR_ARG, "vecs_per_lane 4 allows batch_steps 4 only");
   h->tuning = *t;
@@ -1037,6 +1054,8 @@ ebic_status ebic_check_device_error(ebic_handle h) {
   EBIC_CUDA_TRY(cudaMemcpy(&v, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
   if (v) {
     EBIC_CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
+    // a staged launch that gave up may have left its item counter unreset
+    EBIC_CUDA_TRY(cudaMemset(h->d_claim, 0, 2 * sizeof(uint32_t)));
     return fail(EBIC_ERR_DEVICE, "a kernel flagged invalid input (code %d)", v);
   }
   return EBIC_OK;

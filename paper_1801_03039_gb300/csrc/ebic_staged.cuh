@@ -14,15 +14,19 @@
 //
 // One CTA holds `groups` groups of one scout warp and gw consumer warps.
 //   scout      takes the items (series, part) s, s + S, s + 2S, ... (s its
-//              group's index in the grid, S the number of groups).  While an
-//              item's columns are in flight it reads the next item's offsets;
+//              group's index in the grid, S the number of groups) for the
+//              first `static_rounds` rounds, then claims the remaining items
+//              one at a time from a counter (each claim issued one item
+//              ahead), so that groups whose items were quick take more.
+//              While an item's columns are in flight it reads the next item's
+//              offsets;
 //              it writes the pair indices of the item's first 64 AND steps to
 //              the stage header and issues one bulk copy per staged ("dense")
 //              step: the item's vectors of that step's table row.
 //   consumers  thread j of the group owns vectors part * vpp + j + m * 32 gw
-//              (m < NVT).  It ANDs the staged rows, then walks the remaining
-//              steps with loads of its own vectors, kStagedKB steps per
-//              batch, until their AND is zero.  Each warp adds its count to
+//              (m < NVT, 1 to 3).  It ANDs the staged rows, then walks the
+//              remaining steps with loads of its own vectors, four steps per
+//              batch (two with three vectors), until their AND is zero.  Each warp adds its count to
 //              the stage's ticket word in shared memory; the warp that
 //              arrives last applies Eq. (1) (the log-table value it asks for
 //              is brought in by an asynchronous copy and used one item
@@ -39,7 +43,9 @@
 namespace ebic {
 
 constexpr int kStagedMaxPairs = 64;   // pair indices kept in a stage header
-constexpr int kStagedKB = 4;          // tail steps per batch
+// Tail steps per batch: four, or two when a thread carries three vectors
+// (the batch's loads stay within the register budget).
+template <int NVT> struct StagedKB { static constexpr int value = NVT >= 3 ? 2 : 4; };
 constexpr int kStagedMaxDense = 8;
 
 struct StagedHdr {
@@ -56,7 +62,7 @@ struct StagedHdr {
 struct StagedGeom {
   int32_t groups;       // groups per CTA
   int32_t gw;           // consumer warps per group
-  int32_t nvt;          // vectors per consumer thread (1 or 2)
+  int32_t nvt;          // vectors per consumer thread (1 to 3)
   int32_t vpp;          // vectors per item (part), at most 32 * gw * nvt
   int32_t items_per;    // parts per series
   int32_t dense;        // AND steps staged by bulk copies (1 .. kStagedMaxDense)
@@ -64,6 +70,7 @@ struct StagedGeom {
   int32_t data_bytes;   // dense * vpp * 16, rounded up to 128
   int32_t stage_bytes;  // data_bytes + header, rounded up to 128
   int32_t n_scouts;     // groups in the whole grid
+  int32_t static_rounds;  // items per scout taken in the fixed stride first
 };
 
 // Deferred Eq. (1) write-out of one consumer warp (used by its lane 0): the
@@ -136,7 +143,8 @@ template <bool CHECK, class Pop, int NVT>
 __global__ void __launch_bounds__(1024, 1)
 k_support_staged(const uint32_t* __restrict__ LT, int32_t C, int32_t W, int32_t R, Pop pop,
                  EvalArgs a, StagedGeom g, uint32_t* __restrict__ tickets,
-                 const double* __restrict__ LN, int* __restrict__ err) {
+                 const double* __restrict__ LN, int* __restrict__ err,
+                 uint32_t* __restrict__ claim) {
   extern __shared__ __align__(128) unsigned char smem[];
   if (!pop.active()) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -160,18 +168,45 @@ k_support_staged(const uint32_t* __restrict__ LT, int32_t C, int32_t W, int32_t 
   const uint32_t V = (uint32_t)W >> 2;
   const uint4* LT4 = reinterpret_cast<const uint4*>(LT);
   const uint32_t n_items = (uint32_t)a.P * (uint32_t)g.items_per;
-  const uint32_t S = (uint32_t)g.n_scouts;            // items of scout s: s, s + S, s + 2S, ...
+  const uint32_t S = (uint32_t)g.n_scouts;
+  // Items below n_static go in a fixed stride (scout s: s, s + S, s + 2S,
+  // ...); the rest are claimed one at a time from a counter, so that groups
+  // that finish early take more of them.
+  const uint32_t n_static = min(n_items, S * (uint32_t)g.static_rounds);
 
   if (wg == 0) {
     // ------------------------------------------------------------ scout
-    uint32_t item = blockIdx.x * g.groups + grp;
+    const uint32_t first = blockIdx.x * g.groups + grp;
+    uint32_t ks = 0;                                 // static items taken
+    bool dyn = false;
+    uint32_t raw = 0;                                // lane 0: the claim in flight
+    bool pending = n_static < n_items;               // (warp-uniform)
+    if (lane == 0 && pending) raw = atomicAdd(claim, 1u);
+    // The next item; a dynamic one reads the claim issued earlier and issues
+    // the claim of the one after.  Every claim is read before the scout ends.
+    auto next_item = [&]() -> uint32_t {
+      if (!dyn) {
+        const uint32_t it = first + ks * S;
+        if (it < n_static) {
+          ++ks;
+          return it;
+        }
+        dyn = true;
+        if (!pending) return n_items;
+      }
+      const uint32_t it = n_static + __shfl_sync(kFull, raw, 0);
+      pending = it < n_items;
+      if (lane == 0 && pending) raw = atomicAdd(claim, 1u);
+      return it;
+    };
+    uint32_t item = next_item();
     int64_t begin = 0;
     int32_t L = 0;
     bool ok = false;
     if (item < n_items) ok = pop.range((int32_t)(item / g.items_per), &begin, &L);
     int k = 0;
     bool alive = true;
-    for (; item < n_items; item += S, ++k) {
+    for (; item < n_items; ++k) {
       const int32_t sid = (int32_t)(item / g.items_per);
       const int32_t part = (int32_t)(item % g.items_per);
       // columns of steps 0 .. 63: lane t holds columns t, t + 32 (and lane 31 column 64)
@@ -182,7 +217,7 @@ k_support_staged(const uint32_t* __restrict__ LT, int32_t C, int32_t W, int32_t 
         if (lane == 31 && 64 < L) c2 = (uint32_t)pop.col(begin, 64);
       }
       // the next item's offsets, while those columns are in flight
-      const uint32_t nitem = item + S;
+      const uint32_t nitem = next_item();
       int64_t nbegin = 0;
       int32_t nL = 0;
       bool nok = false;
@@ -232,10 +267,14 @@ k_support_staged(const uint32_t* __restrict__ LT, int32_t C, int32_t W, int32_t 
           mbar_arrive1(&full[s]);
         }
       }
+      item = nitem;
       begin = nbegin;
       L = nL;
       ok = nok;
     }
+    // a scout that gave up still reads its claim in flight, so that the
+    // counter reset below comes after every claim of this launch
+    if (pending && __shfl_sync(kFull, raw, 0) == 0xffffffffu && lane == 0) atomicOr(err, 4);
     // No copy may still be landing when the CTA leaves (which could only
     // happen after a consumer gave up): wait until the latest phase of every
     // stage -- one of the last ns items -- is complete.  Only the scout
@@ -254,6 +293,16 @@ k_support_staged(const uint32_t* __restrict__ LT, int32_t C, int32_t W, int32_t 
       } else if (lane == 0) {
         hd->sid = -1;
         mbar_arrive1(&full[s]);
+      }
+    }
+    // The last scout to finish puts the claim counter back to zero for the
+    // next launch (every scout's claims have returned by now).
+    if (lane == 0 && n_static < n_items) {
+      __threadfence();
+      const uint32_t done = atomicAdd(claim + 1, 1u);
+      if (done == S - 1) {
+        claim[0] = 0u;
+        claim[1] = 0u;
       }
     }
     return;
@@ -294,7 +343,8 @@ k_support_staged(const uint32_t* __restrict__ LT, int32_t C, int32_t W, int32_t 
         for (int t = 0; t < rows; ++t) m[q] = and4(m[q], sd[(size_t)t * vlen + jj]);
     }
     // the remaining steps, all of this thread's live vectors together
-    for (int32_t t = rows; t < nsteps; t += kStagedKB) {
+    constexpr int KB = StagedKB<NVT>::value;
+    for (int32_t t = rows; t < nsteps; t += KB) {
       bool live[NVT], any = false;
 #pragma unroll
       for (int q = 0; q < NVT; ++q) {
@@ -302,9 +352,9 @@ k_support_staged(const uint32_t* __restrict__ LT, int32_t C, int32_t W, int32_t 
         any |= live[q];
       }
       if (!any) break;
-      uint4 x[kStagedKB][NVT];
+      uint4 x[KB][NVT];
 #pragma unroll
-      for (int u = 0; u < kStagedKB; ++u) {
+      for (int u = 0; u < KB; ++u) {
         const int32_t tt = t + u;
         uint32_t pr = 0;
         if (tt < nsteps)
@@ -318,7 +368,7 @@ k_support_staged(const uint32_t* __restrict__ LT, int32_t C, int32_t W, int32_t 
                         : ones;
       }
 #pragma unroll
-      for (int u = 0; u < kStagedKB; ++u)
+      for (int u = 0; u < KB; ++u)
 #pragma unroll
         for (int q = 0; q < NVT; ++q) m[q] = and4(m[q], x[u][q]);
     }

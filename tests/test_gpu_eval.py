@@ -325,7 +325,10 @@ STAGED = [dict(kernel=3), dict(kernel=3, dense_steps=1, stages=2),
           dict(kernel=3, dense_steps=8, stages=4, groups=1),
           dict(kernel=3, dense_steps=3, stages=3, groups=2, vecs_per_lane=1),
           dict(kernel=3, dense_steps=5, stages=2, vecs_per_lane=2),
-          dict(kernel=3, vecs_per_lane=1)]
+          dict(kernel=3, vecs_per_lane=1), dict(kernel=3, vecs_per_lane=3),
+          dict(kernel=3, vecs_per_lane=3, dense_steps=6, stages=3),
+          dict(kernel=3, dynamic_rounds=1), dict(kernel=3, dynamic_rounds=3),
+          dict(kernel=3, dynamic_rounds=64, groups=1)]
 
 
 def _staged_case(name):
@@ -431,7 +434,8 @@ def test_staged_kernel_rejects_bad_tuning():
     h = eb.ebic_load_matrix(synth.matrix_tiny(seed=0).A)
     try:
         for bad in (dict(kernel=3, dense_steps=9), dict(kernel=3, stages=1),
-                    dict(kernel=3, stages=5), dict(kernel=3, groups=16)):
+                    dict(kernel=3, stages=5), dict(kernel=3, groups=16),
+                    dict(kernel=3, dynamic_rounds=-2), dict(kernel=3, dynamic_rounds=65)):
             with pytest.raises(eb.EbicError):
                 eb.ebic_set_eval_tuning(h, **bad)
     finally:
