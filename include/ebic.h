@@ -358,10 +358,13 @@ ebic_status ebic_run_step(ebic_handle h, int32_t generations, ebic_stats_t* stat
  * `stream` has been synchronised.  The run must not go past the generations
  * ebic_run_init sized it for (later generations are not written). */
 ebic_status ebic_run_step_async(ebic_handle h, int32_t generations, void* stream);
-/* One generation (Steps 2-5) as five separate launches with CUDA events between
- * them; kernel_us[5] (nullable) receives the durations of: attempt
- * speculation, the sequential Step 3 builder, tabu insertion, Step 4
- * evaluation, Step 5 ranking.  Synchronous; for measurement. */
+/* One generation (Steps 2-5) as separate launches with CUDA events between
+ * them; kernel_us[8] (nullable) receives the durations of: attempt
+ * speculation (with screening: the whole records stage), the sequential
+ * Step 3 builder, tabu insertion, Step 4 evaluation, Step 5 ranking; then,
+ * with screening, the records stage split into candidate children, their
+ * scores and the pick (zeros without screening).  Synchronous; for
+ * measurement. */
 ebic_status ebic_run_step_profiled(ebic_handle h, float* kernel_us);
 /* In-graph timing of the Step 3 builder, for measurement.  Set before
  * ebic_run_init (it takes effect there; 0, the default, turns it off): the

@@ -393,13 +393,18 @@ def ebic_run_step_async(h, generations: int, stream=None):
     _check(lib().ebic_run_step_async(h, int(generations), _stream(stream)))
 
 
-KERNELS = ("k_spec", "k_build", "k_tabu_insert", "eval", "k_rank")
+KERNELS = ("k_spec", "k_build", "k_tabu_insert", "eval", "k_rank",
+           "screen_candidates", "screen_scores", "screen_pick")
 
 
 def ebic_run_step_profiled(h) -> dict:
-    us = (ctypes.c_float * 5)()
+    us = (ctypes.c_float * 8)()
     _check(lib().ebic_run_step_profiled(h, us))
-    return dict(zip(KERNELS, list(us)))
+    out = dict(zip(KERNELS, list(us)))
+    if not any(out[k] for k in KERNELS[5:]):          # no screening
+        for k in KERNELS[5:]:
+            out.pop(k)
+    return out
 
 
 def ebic_set_kernel_timing(h, slots: int) -> None:

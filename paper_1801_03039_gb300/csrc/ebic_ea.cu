@@ -2142,7 +2142,10 @@ static ebic_status validate(const ebic_ctx* h, const ebic_params_t* p) {
 
 // Attempt records of one Steps 2-5 generation: k_spec, or (screening) the
 // candidates, their scores and the pick.  Returns the launch count in *n.
-static ebic_status launch_records(EaState* st, cudaStream_t s, int* n) {
+// With `mid` (profiling, screening only), events mid[0] and mid[1] are
+// recorded after the candidates and after their scores.
+static ebic_status launch_records(EaState* st, cudaStream_t s, int* n,
+                                  cudaEvent_t* mid = nullptr) {
   const EaDev& d = st->dev;
   const long long jc = (long long)st->J * st->ncombo;
   if (d.V <= 1) {
@@ -2152,6 +2155,7 @@ static ebic_status launch_records(EaState* st, cudaStream_t s, int* n) {
   }
   const long long rows = jc * d.V;
   k_spec<false, true><<<(unsigned)((rows + 127) / 128), 128, 0, s>>>(d);
+  if (mid) cudaEventRecord(mid[0], s);
   int ns = 1;
   if (d.screen == EBIC_SCREEN_SURROGATE) {
     EBIC_TRY(sur_forward_scores(st->sur, d.var_seq, d.var_len, d.S, (int32_t)rows, st->act.ptr,
@@ -2159,6 +2163,7 @@ static ebic_status launch_records(EaState* st, cudaStream_t s, int* n) {
   } else {
     k_pseudo_score<<<(unsigned)((rows + 255) / 256), 256, 0, s>>>(d);
   }
+  if (mid) cudaEventRecord(mid[1], s);
   k_pick<<<(unsigned)((jc + 127) / 128), 128, 0, s>>>(d);
   *n = 2 + ns;
   EBIC_CUDA_TRY(cudaGetLastError());
@@ -2580,8 +2585,8 @@ static ebic_status run_step_async(ebic_ctx* h, int32_t generations, cudaStream_t
 static ebic_status run_step_profiled(ebic_ctx* h, float* us, cudaStream_t s) {
   EaState* st = h->ea;
   if (!st || !st->initialised) return fail(EBIC_ERR_STATE, "ebic_run_init has not run");
-  cudaEvent_t ev[6];
-  for (int i = 0; i < 6; ++i) EBIC_CUDA_TRY(cudaEventCreate(&ev[i]));
+  cudaEvent_t ev[8];
+  for (int i = 0; i < 8; ++i) EBIC_CUDA_TRY(cudaEventCreate(&ev[i]));
   const EaDev& d = st->dev;
   cudaEventRecord(ev[0], s);
   k_build<false><<<1, kBuildThreads, st->smem_build, s>>>(d, st->hmask, st->kB);
@@ -2596,18 +2601,31 @@ static ebic_status run_step_profiled(ebic_ctx* h, float* us, cudaStream_t s) {
   launch_rank(st, s);
   cudaEventRecord(ev[4], s);
   int nrec = 0;
-  ebic_status rs = launch_records(st, s, &nrec);
+  const bool screened = d.V > 1;
+  ebic_status rs = launch_records(st, s, &nrec, screened ? ev + 6 : nullptr);
   cudaEventRecord(ev[5], s);
   count_launches((uint64_t)(3 + nrec));
   cudaError_t e = cudaEventSynchronize(ev[5]);
-  // kernel_us order: records, build, tabu insertion, evaluation, rank
+  // kernel_us order: records, build, tabu insertion, evaluation, rank; then,
+  // when screening, the records stage split into candidates, scores, pick
   const int from[5] = {4, 0, 1, 2, 3};
   for (int i = 0; i < 5 && us; ++i) {
     float ms = 0.f;
     cudaEventElapsedTime(&ms, ev[from[i]], ev[from[i] + 1]);
     us[i] = ms * 1000.f;
   }
-  for (int i = 0; i < 6; ++i) cudaEventDestroy(ev[i]);
+  if (us) {
+    us[5] = us[6] = us[7] = 0.f;
+    if (screened && rs == EBIC_OK) {
+      const cudaEvent_t* seg[4] = {&ev[4], &ev[6], &ev[7], &ev[5]};
+      for (int i = 0; i < 3; ++i) {
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, *seg[i], *seg[i + 1]);
+        us[5 + i] = ms * 1000.f;
+      }
+    }
+  }
+  for (int i = 0; i < 8; ++i) cudaEventDestroy(ev[i]);
   EBIC_TRY(rs);
   EBIC_TRY(es);
   EBIC_CUDA_TRY(e);

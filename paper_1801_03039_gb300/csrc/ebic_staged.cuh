@@ -15,19 +15,20 @@
 // One CTA holds `groups` groups of one scout warp and gw consumer warps.
 //   scout      takes the items (series, part) s, s + S, s + 2S, ... (s its
 //              group's index in the grid, S the number of groups) for the
-//              first `static_rounds` rounds, then claims the remaining items
-//              one at a time from a counter (each claim issued one item
-//              ahead), so that groups whose items were quick take more.
-//              While an item's columns are in flight it reads the next item's
-//              offsets;
-//              it writes the pair indices of the item's first 64 AND steps to
-//              the stage header and issues one bulk copy per staged ("dense")
-//              step: the item's vectors of that step's table row.
+//              first `static_rounds` rounds (by default all of them); any
+//              items left it claims one at a time from a counter (each claim
+//              issued one item ahead), so that groups whose items were quick
+//              take more.  While an item's columns are in flight it reads the
+//              next item's offsets; it writes the pair indices of the item's
+//              first 64 AND steps to the stage header and issues one bulk
+//              copy per staged ("dense") step: the item's vectors of that
+//              step's table row.
 //   consumers  thread j of the group owns vectors part * vpp + j + m * 32 gw
 //              (m < NVT, 1 to 3).  It ANDs the staged rows, then walks the
 //              remaining steps with loads of its own vectors, four steps per
-//              batch (two with three vectors), until their AND is zero.  Each warp adds its count to
-//              the stage's ticket word in shared memory; the warp that
+//              batch (two with three vectors), until their AND is zero.  Each
+//              warp adds its count to the stage's ticket word in shared
+//              memory; the warp that
 //              arrives last applies Eq. (1) (the log-table value it asks for
 //              is brought in by an asynchronous copy and used one item
 //              later, so no warp waits for it) and every warp then releases

@@ -287,3 +287,26 @@ def test_population_and_list_sizes(P, T):
     per thread (P up to 512, 1,024 and 2,048)."""
     prob = synth.matrix_tiny(seed=5)
     run_both(prob.A, iterations=5, pop_size=P, toprank_size=T, len_max=6)
+
+
+def test_profiled_step_splits_the_screened_records_stage():
+    """ebic_run_step_profiled: with screening, the records stage is also given
+    as candidates + scores + pick, which add up to it; without, those keys are
+    absent."""
+    prob = synth.matrix_tiny(seed=0)
+    h = eb.ebic_load_matrix(prob.A)
+    try:
+        p = _device_params({**BASE, "iterations": 6})
+        eb.ebic_run_init(h, p)
+        eb.ebic_run_step(h, 2)
+        plain = eb.ebic_run_step_profiled(h)
+        assert set(plain) == set(eb.KERNELS[:5]) and plain["k_build"] > 0
+        eb.ebic_run_screen(h, None, 8, eb.SCREEN_PSEUDO)
+        eb.ebic_run_init(h, p)
+        eb.ebic_run_step(h, 2)
+        scr = eb.ebic_run_step_profiled(h)
+        parts = scr["screen_candidates"] + scr["screen_scores"] + scr["screen_pick"]
+        assert min(scr["screen_candidates"], scr["screen_scores"], scr["screen_pick"]) > 0
+        assert abs(parts - scr["k_spec"]) <= 1e-3 * scr["k_spec"] + 0.01
+    finally:
+        eb.ebic_free(h)
