@@ -511,6 +511,12 @@ ebic_status ebic_surrogate_train(ebic_surrogate s, const uint16_t* d_seq, const 
                                  int32_t steps, int32_t batch, float lr, float* out_loss);
 /* The target standardisation of the last training call. */
 ebic_status ebic_surrogate_target_norm(ebic_surrogate s, float* mean, float* sd);
+/* Which kernel scores series (ebic_surrogate_predict and screening): 0 (the
+ * default) = tiles of 128 series on the tcgen05 tensor cores, fp32
+ * accumulators in tensor memory; 1 = tiles of 64 series on mma.sync.  Both
+ * round the features and hidden activations to bf16 at the same points; they
+ * differ only in the order of fp32 additions. */
+ebic_status ebic_surrogate_forward_kernel(ebic_surrogate s, int32_t kind);
 /* Predicted standardised targets of n series (device pointers; d_out[n] fp32),
  * queued on `stream` (NULL: the surrogate's own stream, then synchronised). */
 ebic_status ebic_surrogate_predict(ebic_surrogate s, const uint16_t* d_seq, const int32_t* d_len,

@@ -36,6 +36,7 @@ __all__ = [
     "ebic_surrogate_create", "ebic_surrogate_free", "ebic_surrogate_params", "ebic_surrogate_grads",
     "ebic_surrogate_colstats", "ebic_surrogate_step", "ebic_surrogate_log", "ebic_surrogate_train",
     "ebic_surrogate_target_norm", "ebic_surrogate_predict", "ebic_run_screen",
+    "ebic_surrogate_forward_kernel", "FORWARD_TCGEN05", "FORWARD_MMA_SYNC",
     "SCREEN_OFF", "SCREEN_SURROGATE", "SCREEN_PSEUDO",
     "ebic_extract_rows", "ebic_extract_rows_approx", "ebic_recovery_relevance", "ROWS_RISING", "ROWS_RISING_OR_FALLING",
 ]
@@ -127,6 +128,7 @@ _SIGS = {
                               _P], _I32),
     "ebic_surrogate_target_norm": ([_P, _P, _P], _I32),
     "ebic_surrogate_predict": ([_P, _P, _P, _I32, ctypes.c_int64, _P, _P], _I32),
+    "ebic_surrogate_forward_kernel": ([_P, _I32], _I32),
     "ebic_run_screen": ([_P, _P, _I32, _I32], _I32),
     "ebic_extract_rows": ([_P, _P, _P, _I32, _I32, _P, _P, _P], _I32),
     "ebic_extract_rows_approx": ([_P, _P, _P, _I32, _I32, _I32, _P, _P, _P], _I32),
@@ -551,6 +553,14 @@ def ebic_surrogate_target_norm(s):
     m, d = ctypes.c_float(0), ctypes.c_float(0)
     _check(lib().ebic_surrogate_target_norm(s, ctypes.byref(m), ctypes.byref(d)))
     return m.value, d.value
+
+
+FORWARD_TCGEN05, FORWARD_MMA_SYNC = 0, 1
+
+
+def ebic_surrogate_forward_kernel(s, kind: int):
+    """Scoring kernel: FORWARD_TCGEN05 (default) or FORWARD_MMA_SYNC."""
+    _check(lib().ebic_surrogate_forward_kernel(s, int(kind)))
 
 
 def ebic_surrogate_predict(s, d_seq, d_len, stride: int, n: int, d_out, stream=None):

@@ -21,6 +21,7 @@
 
 #include "ebic_async.cuh"
 #include "ebic_internal.cuh"
+#include "ebic_tcmlp.cuh"
 
 namespace ebic {
 
@@ -669,6 +670,9 @@ struct ebic_surrogate_ctx {
   long long o_emb = 0, o_w1 = 0, o_b1 = 0, o_w2 = 0, o_b2 = 0, o_w3 = 0, o_b3 = 0;
   DevBuf par, grad, mom, vel, w1b, w2b, cmean, csd;
   DevBuf wpack;                // W1^T | W2^T in the fused forward's layout (bf16)
+  DevBuf wpack_tc;             // W1^T | W2^T in the tcgen05 forward's layout (bf16)
+  int32_t fwd_kind = 0;        // scoring kernel: 0 tcgen05, 1 mma.sync
+  int32_t sm_count = 0;
   DevBuf ferr;                 // set by the fused forward on a copy timeout
   // training activations (capacity rows)
   int32_t cap = 0;
@@ -766,10 +770,25 @@ ebic_status sur_forward_scores(ebic_surrogate_ctx* s, const uint16_t* seq, const
     if (launches) *launches = 0;
     return EBIC_OK;
   }
+  const float* P = s->par.as<float>();
+  if (s->fwd_kind == 0) {
+    static_assert(tc::kF == kF && tc::kH == kH && tc::kEmb == kEmb, "layer widths");
+    EBIC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_forward_tc,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)tc::kSmem));
+    const int ntiles = (n + tc::kTT - 1) / tc::kTT;
+    const int grid = std::min(ntiles, std::max(s->sm_count, 1));
+    k_mlp_forward_tc<<<grid, tc::kThreads, tc::kSmem, st>>>(
+        seq, len, stride, n, s->C, P + s->o_emb, s->cmean.as<float>(), s->csd.as<float>(),
+        s->len_scale, s->wpack_tc.as<bf16>(), P + s->o_b1, P + s->o_b2, P + s->o_w3,
+        P + s->o_b3, y, s->ferr.as<int>());
+    if (launches) *launches = 1;
+    EBIC_CUDA_TRY(cudaGetLastError());
+    return EBIC_OK;
+  }
   // opt in to the large shared-memory carve-out (per device; cheap to repeat)
   EBIC_CUDA_TRY(cudaFuncSetAttribute(k_mlp_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                      (int)kFwdSmem));
-  const float* P = s->par.as<float>();
   const int ntiles = (n + kFT - 1) / kFT;
   const int grid = std::min(ntiles, 152);
   k_mlp_forward<<<grid, kFwdThreads, kFwdSmem, st>>>(
@@ -779,6 +798,16 @@ ebic_status sur_forward_scores(ebic_surrogate_ctx* s, const uint16_t* seq, const
   if (launches) *launches = 1;
   EBIC_CUDA_TRY(cudaGetLastError());
   return EBIC_OK;
+}
+
+// Both packed copies of W1^T | W2^T the scoring kernels read (2 launches).
+static void pack_forward(ebic_surrogate_ctx* s, cudaStream_t st) {
+  const float* P = s->par.as<float>();
+  constexpr int npack = kH * (kF + 8) + kH * (kH + 8);
+  k_pack_fwd<<<(npack + 255) / 256, 256, 0, st>>>(P + s->o_w1, P + s->o_w2, s->wpack.as<bf16>());
+  constexpr int ntc = kH * kF + kH * kH;
+  k_pack_fwd_tc<<<(ntc + 255) / 256, 256, 0, st>>>(P + s->o_w1, P + s->o_w2,
+                                                   s->wpack_tc.as<bf16>());
 }
 
 // One training step on batch rows idx (device; nullptr: rows 0 .. B - 1);
@@ -848,9 +877,8 @@ static ebic_status sur_step(ebic_surrogate_ctx* s, const uint16_t* seq, const in
           P + g.o, G + g.o, s->mom.as<float>() + g.o, s->vel.as<float>() + g.o, g.n, lr, b1, b2,
           1e-8f, c1, c2, g.copy);
     }
-    constexpr int npack = kH * (kF + 8) + kH * (kH + 8);
-    k_pack_fwd<<<(npack + 255) / 256, 256, 0, st>>>(P + s->o_w1, P + s->o_w2, s->wpack.as<bf16>());
-    count_launches(6);
+    pack_forward(s, st);
+    count_launches(7);
   }
   EBIC_CUDA_TRY(cudaGetLastError());
   return EBIC_OK;
@@ -862,9 +890,8 @@ static ebic_status refresh_copies(ebic_surrogate_ctx* s, cudaStream_t st) {
                                                    (long long)kF * kH);
   k_to_bf16<<<(kH * kH + 255) / 256, 256, 0, st>>>(P + s->o_w2, s->w2b.as<bf16>(),
                                                    (long long)kH * kH);
-  constexpr int npack = kH * (kF + 8) + kH * (kH + 8);
-  k_pack_fwd<<<(npack + 255) / 256, 256, 0, st>>>(P + s->o_w1, P + s->o_w2, s->wpack.as<bf16>());
-  count_launches(3);
+  pack_forward(s, st);
+  count_launches(4);
   EBIC_CUDA_TRY(cudaGetLastError());
   return EBIC_OK;
 }
@@ -896,7 +923,8 @@ static void init_weights(ebic_surrogate_ctx* s, std::vector<float>& p) {
 
 static void sur_release(ebic_surrogate_ctx* s) {
   if (s->stream) cudaStreamSynchronize(s->stream);
-  for (DevBuf* b : {&s->par, &s->grad, &s->mom, &s->vel, &s->w1b, &s->w2b, &s->wpack, &s->ferr,
+  for (DevBuf* b : {&s->par, &s->grad, &s->mom, &s->vel, &s->w1b, &s->w2b, &s->wpack,
+                    &s->wpack_tc, &s->ferr,
                     &s->cmean, &s->csd,
                     &s->act, &s->dh1, &s->dh2, &s->dx, &s->y, &s->dy, &s->idx, &s->loss,
                     &s->tgt, &s->tmp, &s->log_seq, &s->log_len, &s->log_fit})
@@ -929,6 +957,8 @@ static ebic_status sur_create(ebic_ctx* h, int32_t len_scale, uint64_t seed,
   EBIC_TRY(s->w1b.reserve((size_t)kF * kH * sizeof(bf16)));
   EBIC_TRY(s->w2b.reserve((size_t)kH * kH * sizeof(bf16)));
   EBIC_TRY(s->wpack.reserve((size_t)(kH * (kF + 8) + kH * (kH + 8)) * sizeof(bf16)));
+  EBIC_TRY(s->wpack_tc.reserve(tc::kW1 + tc::kW2));
+  EBIC_CUDA_TRY(cudaDeviceGetAttribute(&s->sm_count, cudaDevAttrMultiProcessorCount, s->device));
   EBIC_TRY(s->ferr.reserve_zeroed(sizeof(int), s->stream));
   EBIC_TRY(s->cmean.reserve((size_t)s->C * sizeof(float)));
   EBIC_TRY(s->csd.reserve((size_t)s->C * sizeof(float)));
@@ -1148,6 +1178,13 @@ ebic_status ebic_surrogate_target_norm(ebic_surrogate s, float* mean, float* sd)
   if (!s) return fail(EBIC_ERR_ARG, "null surrogate");
   if (mean) *mean = s->t_mean;
   if (sd) *sd = s->t_sd;
+  return EBIC_OK;
+}
+
+ebic_status ebic_surrogate_forward_kernel(ebic_surrogate s, int32_t kind) {
+  if (!s) return fail(EBIC_ERR_ARG, "null surrogate");
+  if (kind != 0 && kind != 1) return fail(EBIC_ERR_ARG, "forward kernel must be 0 or 1");
+  s->fwd_kind = kind;
   return EBIC_OK;
 }
 

@@ -98,11 +98,13 @@ def test_column_statistics(paper_problem):
         eb.ebic_free(h)
 
 
-def test_forward_matches_oracle(paper_problem):
+@pytest.mark.parametrize("kind", [eb.FORWARD_TCGEN05, eb.FORWARD_MMA_SYNC])
+def test_forward_matches_oracle(paper_problem, kind):
     prob, h = paper_problem
     C = prob.A.shape[1]
     s = eb.ebic_surrogate_create(h, 20, 1)
     try:
+        eb.ebic_surrogate_forward_kernel(s, kind)
         p, flat = _oracle_params(C, 7)
         eb.ebic_surrogate_params(s, flat)
         back = eb.ebic_surrogate_params(s)
@@ -128,6 +130,39 @@ def test_forward_matches_oracle(paper_problem):
         out2 = torch.empty_like(out)
         eb.ebic_surrogate_predict(s, d_rev, d_rlen, 20, len(seqs), out2)
         assert np.all(np.abs(out2.cpu().numpy() - y) <= 2 * bound)
+    finally:
+        eb.ebic_surrogate_free(s)
+
+
+def test_forward_kernels_agree(paper_problem):
+    """The tcgen05 scoring kernel (128-series tiles, accumulators in tensor
+    memory) and the mma.sync one (64-series tiles) round at the same points;
+    on 5,000 series of ragged tiles (39 full tiles of 128 + 8) they differ by
+    no more than the fp32 order of the additions allows."""
+    prob, h = paper_problem
+    C = prob.A.shape[1]
+    s = eb.ebic_surrogate_create(h, 20, 2)
+    try:
+        p, flat = _oracle_params(C, 11)
+        eb.ebic_surrogate_params(s, flat)
+        rng = np.random.default_rng(3)
+        seqs = _series(rng, 5000, C, 1, 20)
+        d_seq, d_len = _device_series(seqs, 20)
+        outs = {}
+        for kind in (eb.FORWARD_TCGEN05, eb.FORWARD_MMA_SYNC):
+            eb.ebic_surrogate_forward_kernel(s, kind)
+            out = torch.full((len(seqs),), float("nan"), dtype=torch.float32, device="cuda")
+            for _ in range(2):                      # twice: the result does not depend on history
+                eb.ebic_surrogate_predict(s, d_seq, d_len, 20, len(seqs), out)
+            outs[kind] = out.cpu().numpy().astype(np.float64)
+        a, b = outs[eb.FORWARD_TCGEN05], outs[eb.FORWARD_MMA_SYNC]
+        assert np.isfinite(a).all() and np.isfinite(b).all()
+        cm, cs = mlp.column_stats(prob.A)
+        X = mlp.features(seqs, p["Emb"], cm, cs, 20)
+        bound = 10 * _forward_sigma(X, p) + 1e-5
+        assert np.all(np.abs(a - b) <= 2 * bound), float(np.abs(a - b).max())
+        with pytest.raises(eb.EbicError):
+            eb.ebic_surrogate_forward_kernel(s, 2)
     finally:
         eb.ebic_surrogate_free(s)
 
