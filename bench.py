@@ -528,6 +528,51 @@ class GenerationsScreened(GenerationsPaper):
                 "source": f"plain run seed {self.HOLDOUT_SEED}, populations of every 10th "
                           "generation (not in the training log)"}
 
+    FWD_ROWS = 1 << 17
+    FWD_FLOPS = 2 * (80 * 256 + 256 * 256 + 256)      # multiply-adds of the three layers
+
+    def forward_throughput(self, torch, eb) -> dict:
+        """The surrogate's scoring kernels alone on a large batch of random
+        series of one length (131,072 rows, two 65,536-row launches a call):
+        CUDA events around 10 back-to-back ebic_surrogate_predict calls on one
+        stream, for the tcgen05 kernel and the mma.sync one.  TFLOP/s counts
+        the three layers' multiply-adds (172,544 flops a series); the feature
+        gather (embedding sums) is work on top that the count leaves out."""
+        peaks = load_peaks()
+        peak = peaks.get("bf16_tflops")
+        n, C = self.FWD_ROWS, self.prob.A.shape[1]
+        rng = np.random.default_rng(7)
+        st = torch.cuda.current_stream()
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+        rows = {}
+        for L in (3, 12, 20):
+            arr = np.zeros((n, self.LMAX), np.int16)
+            arr[:, :L] = np.argsort(rng.random((n, C)), axis=1)[:, :L]
+            d_seq = torch.from_numpy(arr).cuda()
+            d_len = torch.full((n,), L, dtype=torch.int32, device="cuda")
+            row = {}
+            for kind, name in ((eb.FORWARD_TCGEN05, "tcgen05"), (eb.FORWARD_MMA_SYNC, "mma_sync")):
+                eb.ebic_surrogate_forward_kernel(self.sur, kind)
+                for _ in range(3):
+                    eb.ebic_surrogate_predict(self.sur, d_seq, d_len, self.LMAX, n, out, st)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                a.record(st)
+                for _ in range(10):
+                    eb.ebic_surrogate_predict(self.sur, d_seq, d_len, self.LMAX, n, out, st)
+                b.record(st)
+                torch.cuda.synchronize()
+                us = a.elapsed_time(b) * 1e3 / 10
+                tf = n * self.FWD_FLOPS / us / 1e6
+                row[name] = {"us": round(us, 1), "tflops": round(tf, 1),
+                             "frac_of_bf16_peak": round(tf / peak, 3) if peak else None}
+            rows[f"L{L}"] = row
+        eb.ebic_surrogate_forward_kernel(self.sur, eb.FORWARD_TCGEN05)
+        return {"rows": n, "per_length": rows, "peak_tflops": peak,
+                "peak_source": f"bf16 burst, of {peaks['source']}",
+                "flops_per_series": self.FWD_FLOPS}
+
     COMPARE_SEEDS = 3
 
     def compare(self) -> dict:
@@ -854,6 +899,7 @@ def run_ours(args, ws, rank, local):
         extra["kernel_us"] = {k: round(v, 2) for k, v in wl.profile_gpu(eb).items()}
         if isinstance(wl, GenerationsScreened):
             extra["surrogate"] = wl.compare()
+            extra["surrogate"]["forward"] = wl.forward_throughput(torch, eb)
     barrier(ws)
     slowest = aggregate_max(total_s, ws, device=torch.device("cuda", local))
     e2e = wl.e2e_gpu(torch, eb, max(3, args.steps))

@@ -1,13 +1,14 @@
 // The surrogate's scoring pass on the fifth-generation tensor cores
 // (tcgen05.mma with fp32 accumulators in tensor memory).
 //
-// Tiles of 128 series.  Per tile the CTA's 256 threads build the features x
-// (two threads a series; embedding sums in fp32, in column order, rounded to
-// bf16, as every other path does) in shared memory; one thread issues the layer-1 MMAs (M = 128, N = 256, K = 80
-// in five K = 16 steps) into tensor-memory columns [0, 256); the epilogue
+// Tiles of 128 series.  Per tile the CTA's eight warps build the features x
+// (sixteen series a warp, two embedding dimensions a lane; sums in fp32, in
+// column order, rounded to bf16, as every other path does) in shared memory;
+// one thread issues the layer-1 MMAs (M = 128, N = 256, K = 80 in five
+// K = 16 steps) into tensor-memory columns [0, 256); the epilogue
 // reads them back (tcgen05.ld), adds b1, applies ReLU and rounds to bf16 into
-// a half-width h1 buffer; layer 2 runs as two K-halves of 128 (eight K = 16
-// steps each) into columns [256, 512), the second half accumulating; the last
+// a quarter-width h1 buffer; layer 2 runs as four K-quarters of 64 (four
+// K = 16 steps each) into columns [256, 512), accumulating; the last
 // epilogue adds b2, applies ReLU, rounds to bf16 and takes the dot product
 // with w3 per row.  W1^T (256 x 80) and W2^T (256 x 256) stay in shared memory
 // for the whole kernel, brought in by one bulk copy.
@@ -33,9 +34,15 @@ constexpr int kTT = 128;                          // series per tile (TMEM lanes
 constexpr int kF = 80, kH = 256, kEmb = 64;       // as the surrogate's layers
 constexpr size_t kW1 = (size_t)kH * kF * 2;       // W1^T bytes
 constexpr size_t kW2 = (size_t)kH * kH * 2;       // W2^T bytes
+constexpr int kQ = 64;                            // h1 columns per layer-2 K-quarter
 constexpr size_t kX = (size_t)kTT * kF * 2;       // x tile bytes
-constexpr size_t kHh = (size_t)kTT * (kH / 2) * 2;  // half of an h1 tile
-constexpr size_t kSmem = kW1 + kW2 + kX + kHh + 3 * (size_t)kH * 4 + (size_t)kTT * 2 * 4;
+constexpr size_t kHq = (size_t)kTT * kQ * 2;      // a quarter of an h1 tile
+// x and the current h1 quarter share one buffer (x is dead once the layer-1
+// MMAs have completed); the total stays below 196 KB, which leaves the SM a
+// 60 KB L1 for the embedding rows the feature gather rereads
+constexpr size_t kXH = kX > kHq ? kX : kHq;
+constexpr size_t kSmem = kW1 + kW2 + kXH + 3 * (size_t)kH * 4 + (size_t)kTT * 2 * 4;
+static_assert(kSmem + 1024 + 128 <= 196 * 1024, "shared memory above the 196 KB carve-out");
 constexpr int kThreads = 256;
 constexpr uint32_t kTmemCols = 512;
 
@@ -100,6 +107,13 @@ __device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Embedding rows are reread by every tile: ask L1 to keep them.
+__device__ __forceinline__ float2 ld_keep(const float2* p) {
+  float2 v;
+  asm("ld.global.nc.L1::evict_last.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+
 }  // namespace tc
 
 // W1^T and W2^T in the tcgen05 forward's shared-memory layout (bf16 core
@@ -134,8 +148,8 @@ k_mlp_forward_tc(const uint16_t* __restrict__ seq, const int32_t* __restrict__ l
   bf* sW1 = reinterpret_cast<bf*>(tsm);                        // [256 x 80] core matrices
   bf* sW2 = sW1 + kH * kF;                                     // [256 x 256]
   bf* sX = sW2 + kH * kH;                                      // [128 x 80]
-  bf* sH = sX + kTT * kF;                                      // [128 x 128]
-  float* b1s = reinterpret_cast<float*>(sH + kTT * (kH / 2));
+  bf* sH = sX;                                                 // [128 x 64], aliases x
+  float* b1s = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(sX) + kXH);
   float* b2s = b1s + kH;
   float* w3s = b2s + kH;
   float* yp = w3s + kH;                                        // [128][2]
@@ -195,72 +209,71 @@ k_mlp_forward_tc(const uint16_t* __restrict__ seq, const int32_t* __restrict__ l
   int tile = blockIdx.x;
   for (; tile < ntiles && ok; tile += gridDim.x) {
     const int r0 = tile * kTT;
-    // ---- features: thread t builds dimensions [32 h, 32 h + 32) (h = t & 1)
-    // of row t / 2: its embedding loads go out two columns (16 float4) at a
-    // time, and every sum runs in column order, as in the other paths ----
+    // ---- features: warp w builds rows [16 w, 16 w + 16); lane l holds
+    // dimensions 2 l and 2 l + 1 of all sixteen, so every embedding load is
+    // one 256-byte row for the whole warp; sums run in column order, as in
+    // the other paths ----
     {
-      const int r = tid >> 1, hf = tid & 1, grow = r0 + r;
+      const int rb = warp * 16, k = lane & 15, grow = r0 + rb + k;
       const int L = grow < n ? min(max(len[grow], 0), stride) : 0;
       const uint16_t* sp = seq + (size_t)(grow < n ? grow : 0) * stride;
-      const float4* e4 = reinterpret_cast<const float4*>(emb) + 8 * hf;   // 16 float4 a column
-      float acc[32];
+      const int Lmax = __reduce_max_sync(0xffffffffu, L);
+      const float2* e2 = reinterpret_cast<const float2*>(emb) + lane;   // 32 float2 a column
+      float2 acc[16];
 #pragma unroll
-      for (int d = 0; d < 32; ++d) acc[d] = 0.f;
+      for (int j = 0; j < 16; ++j) acc[j] = make_float2(0.f, 0.f);
       float m = 0.f, dsum = 0.f;
-      // the next pair's column ids are loaded one iteration ahead
-      int n0 = L > 0 ? (int)sp[0] : C, n1 = L > 1 ? (int)sp[1] : C;
-      for (int i = 0; i < L; i += 2) {
-        const int c0 = n0, c1 = n1;
-        n0 = i + 2 < L ? (int)sp[i + 2] : C;
-        n1 = i + 3 < L ? (int)sp[i + 3] : C;
-        float4 v0[8], v1[8];
-        const bool ok0 = c0 < C, ok1 = c1 < C;
+      // two columns a step (32 loads in flight a lane); the next step's
+      // column ids are read one step ahead
+      int cn0 = L > 0 ? (int)__ldg(sp) : C, cn1 = L > 1 ? (int)__ldg(sp + 1) : C;
+      for (int i = 0; i < Lmax; i += 2) {
+        const int c0 = cn0, c1 = cn1;
+        cn0 = i + 2 < L ? (int)__ldg(sp + i + 2) : C;
+        cn1 = i + 3 < L ? (int)__ldg(sp + i + 3) : C;
+        int cc0[16], cc1[16];
+        float2 v0[16], v1[16];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          v0[j] = ok0 ? __ldg(e4 + (size_t)c0 * 16 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
-          v1[j] = ok1 ? __ldg(e4 + (size_t)c1 * 16 + j) : make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int j = 0; j < 16; ++j) {
+          cc0[j] = __shfl_sync(0xffffffffu, c0, j);
+          cc1[j] = __shfl_sync(0xffffffffu, c1, j);
+          v0[j] = cc0[j] < C ? ld_keep(e2 + (size_t)cc0[j] * 32) : make_float2(0.f, 0.f);
+          v1[j] = cc1[j] < C ? ld_keep(e2 + (size_t)cc1[j] * 32) : make_float2(0.f, 0.f);
         }
-        float m0 = 0.f, d0 = 0.f, m1 = 0.f, d1 = 0.f;
-        if (hf == 0) {
-          if (ok0) { m0 = cmean[c0]; d0 = csd[c0]; }
-          if (ok1) { m1 = cmean[c1]; d1 = csd[c1]; }
-        }
-        if (ok0) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            acc[4 * j] += v0[j].x; acc[4 * j + 1] += v0[j].y;
-            acc[4 * j + 2] += v0[j].z; acc[4 * j + 3] += v0[j].w;
+        if (lane < 16) {
+          if (c0 < C) {
+            m += cmean[c0];
+            dsum += csd[c0];
           }
-          m += m0;
-          dsum += d0;
-        }
-        if (ok1) {
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            acc[4 * j] += v1[j].x; acc[4 * j + 1] += v1[j].y;
-            acc[4 * j + 2] += v1[j].z; acc[4 * j + 3] += v1[j].w;
+          if (c1 < C) {
+            m += cmean[c1];
+            dsum += csd[c1];
           }
-          m += m1;
-          dsum += d1;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          if (cc0[j] < C) {
+            acc[j].x += v0[j].x;
+            acc[j].y += v0[j].y;
+          }
+          if (cc1[j] < C) {
+            acc[j].x += v1[j].x;
+            acc[j].y += v1[j].y;
+          }
         }
       }
 #pragma unroll
-      for (int g8 = 0; g8 < 4; ++g8) {
-        __align__(16) bf o[8];
-#pragma unroll
-        for (int i = 0; i < 8; ++i) o[i] = __float2bfloat16_rn(acc[8 * g8 + i]);
-        *reinterpret_cast<uint4*>(sX + cm(r, 32 * hf + 8 * g8, kF)) =
-            *reinterpret_cast<const uint4*>(o);
-      }
-      if (hf == 0) {
+      for (int j = 0; j < 16; ++j)
+        *reinterpret_cast<__nv_bfloat162*>(sX + cm(rb + j, 2 * lane, kF)) =
+            __floats2bfloat162_rn(acc[j].x, acc[j].y);
+      if (lane < 16) {
         __align__(16) bf o[16];
 #pragma unroll
         for (int i = 0; i < 16; ++i) o[i] = __float2bfloat16_rn(0.f);
         o[0] = __float2bfloat16_rn(L ? m / (float)L : 0.f);
         o[1] = __float2bfloat16_rn(L ? dsum / (float)L : 0.f);
         o[2] = __float2bfloat16_rn((float)L / len_scale);
-        *reinterpret_cast<uint4*>(sX + cm(r, 64, kF)) = *reinterpret_cast<const uint4*>(o);
-        *reinterpret_cast<uint4*>(sX + cm(r, 72, kF)) = *reinterpret_cast<const uint4*>(o + 8);
+        *reinterpret_cast<uint4*>(sX + cm(rb + k, 64, kF)) = *reinterpret_cast<const uint4*>(o);
+        *reinterpret_cast<uint4*>(sX + cm(rb + k, 72, kF)) = *reinterpret_cast<const uint4*>(o + 8);
       }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -275,31 +288,30 @@ k_mlp_forward_tc(const uint16_t* __restrict__ seq, const int32_t* __restrict__ l
       commit(&mbar);
     }
     if (!(ok = wait_mma())) break;
-    // ---- h1 by halves of 128 columns, each followed by its layer-2 MMAs ----
-    for (int h = 0; h < 2 && ok; ++h) {
+    // ---- h1 by quarters of 64 columns, each followed by its layer-2 MMAs
+    // (the first quarter overwrites x, which the completed layer-1 MMAs no
+    // longer read) ----
+    for (int h = 0; h < kH / kQ && ok; ++h) {
+      const int c0 = 32 * cg;                                   // column within the quarter
+      float v[32];
+      ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(kQ * h + c0), v);
 #pragma unroll
-      for (int t = 0; t < 2; ++t) {
-        const int c0 = 64 * cg + 32 * t;                        // column within the half
-        float v[32];
-        ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(128 * h + c0), v);
+      for (int g8 = 0; g8 < 4; ++g8) {
+        __align__(16) bf o[8];
 #pragma unroll
-        for (int g8 = 0; g8 < 4; ++g8) {
-          __align__(16) bf o[8];
-#pragma unroll
-          for (int i = 0; i < 8; ++i)
-            o[i] = __float2bfloat16_rn(fmaxf(v[8 * g8 + i] + b1s[128 * h + c0 + 8 * g8 + i], 0.f));
-          *reinterpret_cast<uint4*>(sH + cm(row, c0 + 8 * g8, kH / 2)) =
-              *reinterpret_cast<const uint4*>(o);
-        }
+        for (int i = 0; i < 8; ++i)
+          o[i] = __float2bfloat16_rn(fmaxf(v[8 * g8 + i] + b1s[kQ * h + c0 + 8 * g8 + i], 0.f));
+        *reinterpret_cast<uint4*>(sH + cm(row, c0 + 8 * g8, kQ)) =
+            *reinterpret_cast<const uint4*>(o);
       }
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       fence_before();
       __syncthreads();
       fence_after();
       if (tid == 0) {
-        for (int k0 = 0; k0 < kH / 2; k0 += 16)
-          mma(tmem + (uint32_t)kH, sdesc(aH + (k0 / 8) * 128, 128, (kH / 2 / 8) * 128),
-              sdesc(aW2 + ((128 * h + k0) / 8) * 128, 128, (kH / 8) * 128), id, h > 0 || k0 > 0);
+        for (int k0 = 0; k0 < kQ; k0 += 16)
+          mma(tmem + (uint32_t)kH, sdesc(aH + (k0 / 8) * 128, 128, (kQ / 8) * 128),
+              sdesc(aW2 + ((kQ * h + k0) / 8) * 128, 128, (kH / 8) * 128), id, h > 0 || k0 > 0);
         commit(&mbar);
       }
       ok = wait_mma();
