@@ -517,6 +517,15 @@ ebic_status ebic_surrogate_target_norm(ebic_surrogate s, float* mean, float* sd)
  * round the features and hidden activations to bf16 at the same points; they
  * differ only in the order of fp32 additions. */
 ebic_status ebic_surrogate_forward_kernel(ebic_surrogate s, int32_t kind);
+/* Which kernels run the six GEMMs of a training step: 0 (the default) = the
+ * tcgen05 tensor cores with fp32 accumulators in tensor memory (operands that
+ * are K-major in memory arrive by tensor copies or one bulk copy, the weight
+ * gradients' MN-major operands are transposed in 8 x 8 blocks on the way into
+ * shared memory); 1 = mma.sync tiles of 64 x 64.  Both round at the same
+ * points (bf16 operands and stored activations, fp32 sums; split-K slices
+ * summed in split order); they differ only in the order of fp32 additions.
+ * EBIC_ERR_ARG for any other kind. */
+ebic_status ebic_surrogate_train_kernel(ebic_surrogate s, int32_t kind);
 /* Predicted standardised targets of n series (device pointers; d_out[n] fp32),
  * queued on `stream` (NULL: the surrogate's own stream, then synchronised). */
 ebic_status ebic_surrogate_predict(ebic_surrogate s, const uint16_t* d_seq, const int32_t* d_len,

@@ -37,6 +37,7 @@ __all__ = [
     "ebic_surrogate_colstats", "ebic_surrogate_step", "ebic_surrogate_log", "ebic_surrogate_train",
     "ebic_surrogate_target_norm", "ebic_surrogate_predict", "ebic_run_screen",
     "ebic_surrogate_forward_kernel", "FORWARD_TCGEN05", "FORWARD_MMA_SYNC",
+    "ebic_surrogate_train_kernel",
     "SCREEN_OFF", "SCREEN_SURROGATE", "SCREEN_PSEUDO",
     "ebic_extract_rows", "ebic_extract_rows_approx", "ebic_recovery_relevance", "ROWS_RISING", "ROWS_RISING_OR_FALLING",
 ]
@@ -129,6 +130,7 @@ _SIGS = {
     "ebic_surrogate_target_norm": ([_P, _P, _P], _I32),
     "ebic_surrogate_predict": ([_P, _P, _P, _I32, ctypes.c_int64, _P, _P], _I32),
     "ebic_surrogate_forward_kernel": ([_P, _I32], _I32),
+    "ebic_surrogate_train_kernel": ([_P, _I32], _I32),
     "ebic_run_screen": ([_P, _P, _I32, _I32], _I32),
     "ebic_extract_rows": ([_P, _P, _P, _I32, _I32, _P, _P, _P], _I32),
     "ebic_extract_rows_approx": ([_P, _P, _P, _I32, _I32, _I32, _P, _P, _P], _I32),
@@ -561,6 +563,11 @@ FORWARD_TCGEN05, FORWARD_MMA_SYNC = 0, 1
 def ebic_surrogate_forward_kernel(s, kind: int):
     """Scoring kernel: FORWARD_TCGEN05 (default) or FORWARD_MMA_SYNC."""
     _check(lib().ebic_surrogate_forward_kernel(s, int(kind)))
+
+
+def ebic_surrogate_train_kernel(s, kind: int):
+    """Training GEMMs: FORWARD_TCGEN05 (default) or FORWARD_MMA_SYNC."""
+    _check(lib().ebic_surrogate_train_kernel(s, int(kind)))
 
 
 def ebic_surrogate_predict(s, d_seq, d_len, stride: int, n: int, d_out, stream=None):

@@ -17,11 +17,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <vector>
 
 #include "ebic_async.cuh"
 #include "ebic_internal.cuh"
 #include "ebic_tcmlp.cuh"
+#include "ebic_tcgemm.cuh"
 
 namespace ebic {
 
@@ -251,26 +253,34 @@ __global__ void __launch_bounds__(256) k_dh2(const float* __restrict__ dy,
   dh2[i] = __float2bfloat16_rn(v);
 }
 
-// out[j] = sum_b scale[b] * X[b][j] for j < cols (scale = nullptr: 1);
-// one block per 32 columns, X bf16 (or fp32 via Xf)
+// Column sums out[j] = sum_b scale[b] * X[b][j] for j < cols (scale =
+// nullptr: 1), in two fixed-order levels so that the result does not depend
+// on scheduling: CTA (32-column tile, segment of kColSeg rows) has its eight
+// warps take every eighth row of the segment, each in row order, adds the
+// warps in order and writes part[segment][j]; k_sum_splits then adds the
+// segments in order.  X bf16 (or fp32 via Xf).
+constexpr int kColSeg = 128;
 __global__ void __launch_bounds__(256)
-k_colsum(const bf16* __restrict__ Xb, const float* __restrict__ Xf, int n, int cols,
-         const float* __restrict__ scale, float* __restrict__ out) {
+k_colsum_part(const bf16* __restrict__ Xb, const float* __restrict__ Xf, int n, int cols,
+              const float* __restrict__ scale, float* __restrict__ part) {
   const int c = blockIdx.x * 32 + (threadIdx.x & 31);
   const int r0 = threadIdx.x >> 5;
+  const int b_lo = blockIdx.y * kColSeg, b_hi = min(n, b_lo + kColSeg);
   float s = 0.f;
-  if (c < cols)
-    for (int b = r0; b < n; b += 8) {
+  if (c < cols) {
+#pragma unroll 4
+    for (int b = b_lo + r0; b < b_hi; b += 8) {
       const float v = Xb ? __bfloat162float(Xb[(size_t)b * cols + c]) : Xf[(size_t)b * cols + c];
       s += scale ? scale[b] * v : v;
     }
+  }
   __shared__ float red[8][33];
   red[r0][threadIdx.x & 31] = s;
   __syncthreads();
   if (r0 == 0 && c < cols) {
     float t = 0.f;
     for (int q = 0; q < 8; ++q) t += red[q][threadIdx.x & 31];
-    out[c] = t;
+    part[(size_t)blockIdx.y * cols + c] = t;
   }
 }
 
@@ -672,11 +682,12 @@ struct ebic_surrogate_ctx {
   DevBuf wpack;                // W1^T | W2^T in the fused forward's layout (bf16)
   DevBuf wpack_tc;             // W1^T | W2^T in the tcgen05 forward's layout (bf16)
   int32_t fwd_kind = 0;        // scoring kernel: 0 tcgen05, 1 mma.sync
+  int32_t gemm_kind = 0;       // training GEMMs: 0 tcgen05, 1 mma.sync
   int32_t sm_count = 0;
   DevBuf ferr;                 // set by the fused forward on a copy timeout
   // training activations (capacity rows)
   int32_t cap = 0;
-  DevBuf act, dh1, dh2, dx, y, dy, idx, loss, tgt, tmp, sq, split, epart;
+  DevBuf act, dh1, dh2, dx, y, dy, idx, loss, tgt, tmp, sq, split, epart, csplit;
   // training log: series [log_n][kLogStride], lengths, exact fitness
   long long log_n = 0, log_cap = 0;
   DevBuf log_seq, log_len, log_fit;
@@ -732,6 +743,7 @@ static ebic_status sur_reserve(ebic_surrogate_ctx* s, int32_t rows) {
   EBIC_TRY(s->sq.reserve(r * sizeof(float)));
   const int ks = std::max(1, std::min(32, rows / 256));
   EBIC_TRY(s->split.reserve((size_t)ks * kH * kH * sizeof(float)));
+  EBIC_TRY(s->csplit.reserve((size_t)((rows + kColSeg - 1) / kColSeg) * kH * sizeof(float)));
   const int seg = s->emb_seg_len(rows);
   EBIC_TRY(s->epart.reserve((size_t)((rows + seg - 1) / seg) * s->C * kEmb * sizeof(float)));
   s->cap = rows;
@@ -747,19 +759,107 @@ static void gemm(int M, int N, int K, const bf16* A, int lda, const bf16* B, int
                                                   Cb, ldc);
 }
 
+// out[0 .. cols) = the column sums of k_colsum_part (2 launches).
+static void colsum(ebic_surrogate_ctx* s, const bf16* Xb, const float* Xf, int n, int cols,
+                   const float* scale, float* out, cudaStream_t st) {
+  const int nseg = (n + kColSeg - 1) / kColSeg;
+  k_colsum_part<<<dim3((unsigned)((cols + 31) / 32), (unsigned)nseg), 256, 0, st>>>(
+      Xb, Xf, n, cols, scale, s->csplit.as<float>());
+  k_sum_splits<<<(unsigned)((cols + 255) / 256), 256, 0, st>>>(s->csplit.as<float>(), nseg,
+                                                               (long long)cols, out);
+}
+
+// ---- the tcgen05 training GEMMs (ebic_tcgemm.cuh) ----
+
+typedef CUresult (*TmapEncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// Tensor map of a K-major bf16 matrix (rows x cols, row pitch ld elements)
+// in boxes of 8 columns x box_rows rows; rows past the end read as zeros.
+static ebic_status tmap_kmajor(CUtensorMap* m, const bf16* p, int rows, int cols, int ld,
+                               int box_rows) {
+  static TmapEncodeFn encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    EBIC_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                   cudaEnableDefault, &q));
+    if (q != cudaDriverEntryPointSuccess || !fn)
+      return fail(EBIC_ERR_CUDA, "the driver offers no tensor-map encoder");
+    encode = reinterpret_cast<TmapEncodeFn>(fn);
+  }
+  const cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t pitch[1] = {(cuuint64_t)ld * sizeof(bf16)};
+  const cuuint32_t box[2] = {8u, (cuuint32_t)box_rows};
+  const cuuint32_t step[2] = {1u, 1u};
+  const CUresult r = encode(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(p), dim,
+                            pitch, box, step, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(EBIC_ERR_CUDA, "tensor-map encoding failed");
+  return EBIC_OK;
+}
+
+// D[M x N] = A[M x K] . op(B), A K-major (pitch lda); B either K-major as
+// N x K (Bk, pitch ldb) or the packed W^T at Bpacked.  One launch.
+template <int BSRC, int EPI>
+static ebic_status gemm_tc_full(ebic_surrogate_ctx* s, int M, int N, int K, const bf16* A,
+                                int lda, const bf16* Bk, int ldb, const bf16* Bpacked,
+                                const float* bias, const bf16* mask, int ldm, float* Cf,
+                                bf16* Cb, int ldc, cudaStream_t st) {
+  CUtensorMap ta, tb;
+  std::memset(&tb, 0, sizeof(tb));
+  EBIC_TRY(tmap_kmajor(&ta, A, M, K, lda, tcg::kTM));
+  if (BSRC == tcg::B_TMA) EBIC_TRY(tmap_kmajor(&tb, Bk, N, K, ldb, N));
+  const int smem = std::max(tcg::kMinSmem, (tcg::kTM + N) * K * (int)sizeof(bf16)) +
+                   tcg::kAlignSlack;
+  EBIC_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_full<BSRC, EPI>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+  k_gemm_tc_full<BSRC, EPI><<<(unsigned)((M + tcg::kTM - 1) / tcg::kTM), tcg::kThreads, smem,
+                              st>>>(ta, tb, Bpacked, M, N, K, bias, mask, ldm, Cf, Cb, ldc,
+                                    s->ferr.as<int>());
+  return EBIC_OK;
+}
+
+// Split-K slices of op(A) op(B) with both operands MN-major.  One launch.
+static ebic_status gemm_tc_split(ebic_surrogate_ctx* s, int M, int N, int K, const bf16* A,
+                                 int lda, const bf16* B, int ldb, float* Cf, int ldc, int ksplit,
+                                 cudaStream_t st) {
+  const int smem = std::max(tcg::kMinSmem, (tcg::kTM + N) * tcg::kKC * (int)sizeof(bf16)) +
+                   tcg::kAlignSlack;
+  EBIC_CUDA_TRY(cudaFuncSetAttribute(k_gemm_tc_split, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     smem));
+  const dim3 grid((unsigned)((M + tcg::kTM - 1) / tcg::kTM), 1u, (unsigned)ksplit);
+  k_gemm_tc_split<<<grid, tcg::kThreads, smem, st>>>(M, N, K, A, lda, B, ldb, Cf, ldc,
+                                                     s->ferr.as<int>());
+  return EBIC_OK;
+}
+
 // Features and both hidden layers of n series (rows idx[b], or 0 .. n - 1):
 // 3 launches.
-static void sur_hidden(ebic_surrogate_ctx* s, const uint16_t* seq, const int32_t* len,
-                       int32_t stride, const int32_t* idx, int32_t n, const ActView& a,
-                       cudaStream_t st) {
+static ebic_status sur_hidden(ebic_surrogate_ctx* s, const uint16_t* seq, const int32_t* len,
+                              int32_t stride, const int32_t* idx, int32_t n, const ActView& a,
+                              cudaStream_t st) {
   const float* P = s->par.as<float>();
   k_features<<<(unsigned)((n + 7) / 8), 256, 0, st>>>(seq, len, stride, idx, n, s->C,
                                                       P + s->o_emb, s->cmean.as<float>(),
                                                       s->csd.as<float>(), s->len_scale, a.x);
+  if (s->gemm_kind == 0) {
+    const bf16* wt = s->wpack_tc.as<bf16>();          // W1^T | W2^T, packed row-major
+    EBIC_TRY((gemm_tc_full<tcg::B_PACKED, tcg::EPI_BIAS_RELU_BF16>(
+        s, n, kH, kF, a.x, kF, nullptr, 0, wt, P + s->o_b1, nullptr, 0, nullptr, a.h1, kH, st)));
+    EBIC_TRY((gemm_tc_full<tcg::B_PACKED, tcg::EPI_BIAS_RELU_BF16>(
+        s, n, kH, kH, a.h1, kH, nullptr, 0, wt + kH * kF, P + s->o_b2, nullptr, 0, nullptr, a.h2,
+        kH, st)));
+    return EBIC_OK;
+  }
   gemm<false, false, EPI_BIAS_RELU_BF16>(n, kH, kF, a.x, kF, s->w1b.as<bf16>(), kH, P + s->o_b1,
                                          nullptr, 0, nullptr, a.h1, kH, 1, st);
   gemm<false, false, EPI_BIAS_RELU_BF16>(n, kH, kH, a.h1, kH, s->w2b.as<bf16>(), kH, P + s->o_b2,
                                          nullptr, 0, nullptr, a.h2, kH, 1, st);
+  return EBIC_OK;
 }
 
 ebic_status sur_forward_scores(ebic_surrogate_ctx* s, const uint16_t* seq, const int32_t* len,
@@ -817,16 +917,16 @@ static ebic_status sur_step(ebic_surrogate_ctx* s, const uint16_t* seq, const in
                             float lr, bool update, cudaStream_t st) {
   EBIC_TRY(sur_reserve(s, B));
   const ActView a = act_view(s->act.ptr, B);
-  sur_hidden(s, seq, len, stride, idx, B, a, st);
+  EBIC_TRY(sur_hidden(s, seq, len, stride, idx, B, a, st));
   float* P = s->par.as<float>();
   float* G = s->grad.as<float>();
   const unsigned wb = (unsigned)((B + 7) / 8);
   k_out<<<wb, 256, 0, st>>>(a.h2, P + s->o_w3, P + s->o_b3, B, s->y.as<float>(), t, idx,
                             s->dy.as<float>(), s->sq.as<float>());
-  k_colsum<<<1, 256, 0, st>>>(nullptr, s->sq.as<float>(), B, 1, nullptr, s->loss.as<float>());
+  colsum(s, nullptr, s->sq.as<float>(), B, 1, nullptr, s->loss.as<float>(), st);
   // output layer
-  k_colsum<<<(kH + 31) / 32, 256, 0, st>>>(a.h2, nullptr, B, kH, s->dy.as<float>(), G + s->o_w3);
-  k_colsum<<<1, 256, 0, st>>>(nullptr, s->dy.as<float>(), B, 1, nullptr, G + s->o_b3);
+  colsum(s, a.h2, nullptr, B, kH, s->dy.as<float>(), G + s->o_w3, st);
+  colsum(s, nullptr, s->dy.as<float>(), B, 1, nullptr, G + s->o_b3, st);
   const long long nb = (long long)B * kH;
   k_dh2<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(s->dy.as<float>(), P + s->o_w3, a.h2, B,
                                                       s->dh2.as<bf16>());
@@ -834,21 +934,37 @@ static ebic_status sur_step(ebic_surrogate_ctx* s, const uint16_t* seq, const in
   // dh1 = (dh2 W2^T) [h1 > 0]
   const int ks = std::max(1, std::min(32, B / 256));
   float* split = s->split.as<float>();
-  gemm<true, false, EPI_F32_SPLIT>(kH, kH, B, a.h1, kH, s->dh2.as<bf16>(), kH, nullptr, nullptr,
-                                   0, split, nullptr, kH, ks, st);
+  const bool tcg5 = s->gemm_kind == 0;
+  if (tcg5)
+    EBIC_TRY(gemm_tc_split(s, kH, kH, B, a.h1, kH, s->dh2.as<bf16>(), kH, split, kH, ks, st));
+  else
+    gemm<true, false, EPI_F32_SPLIT>(kH, kH, B, a.h1, kH, s->dh2.as<bf16>(), kH, nullptr, nullptr,
+                                     0, split, nullptr, kH, ks, st);
   k_sum_splits<<<(kH * kH + 255) / 256, 256, 0, st>>>(split, ks, (long long)kH * kH, G + s->o_w2);
-  k_colsum<<<(kH + 31) / 32, 256, 0, st>>>(s->dh2.as<bf16>(), nullptr, B, kH, nullptr,
-                                           G + s->o_b2);
-  gemm<false, true, EPI_MASK_BF16>(B, kH, kH, s->dh2.as<bf16>(), kH, s->w2b.as<bf16>(), kH,
-                                   nullptr, a.h1, kH, nullptr, s->dh1.as<bf16>(), kH, 1, st);
+  colsum(s, s->dh2.as<bf16>(), nullptr, B, kH, nullptr, G + s->o_b2, st);
+  if (tcg5)
+    EBIC_TRY((gemm_tc_full<tcg::B_TMA, tcg::EPI_MASK_BF16>(
+        s, B, kH, kH, s->dh2.as<bf16>(), kH, s->w2b.as<bf16>(), kH, nullptr, nullptr, a.h1, kH,
+        nullptr, s->dh1.as<bf16>(), kH, st)));
+  else
+    gemm<false, true, EPI_MASK_BF16>(B, kH, kH, s->dh2.as<bf16>(), kH, s->w2b.as<bf16>(), kH,
+                                     nullptr, a.h1, kH, nullptr, s->dh1.as<bf16>(), kH, 1, st);
   // layer 1: dW1 = x^T dh1, db1, dx = dh1 W1^T, then the embedding rows
-  gemm<true, false, EPI_F32_SPLIT>(kF, kH, B, a.x, kF, s->dh1.as<bf16>(), kH, nullptr, nullptr, 0,
-                                   split, nullptr, kH, ks, st);
+  if (tcg5)
+    EBIC_TRY(gemm_tc_split(s, kF, kH, B, a.x, kF, s->dh1.as<bf16>(), kH, split, kH, ks, st));
+  else
+    gemm<true, false, EPI_F32_SPLIT>(kF, kH, B, a.x, kF, s->dh1.as<bf16>(), kH, nullptr, nullptr,
+                                     0, split, nullptr, kH, ks, st);
   k_sum_splits<<<(kF * kH + 255) / 256, 256, 0, st>>>(split, ks, (long long)kF * kH, G + s->o_w1);
-  k_colsum<<<(kH + 31) / 32, 256, 0, st>>>(s->dh1.as<bf16>(), nullptr, B, kH, nullptr,
-                                           G + s->o_b1);
-  gemm<false, true, EPI_F32>(B, kF, kH, s->dh1.as<bf16>(), kH, s->w1b.as<bf16>(), kH, nullptr,
-                             nullptr, 0, s->dx.as<float>(), nullptr, kF, 1, st);
+  colsum(s, s->dh1.as<bf16>(), nullptr, B, kH, nullptr, G + s->o_b1, st);
+  if (tcg5)
+    EBIC_TRY((gemm_tc_full<tcg::B_TMA, tcg::EPI_F32>(s, B, kF, kH, s->dh1.as<bf16>(), kH,
+                                                     s->w1b.as<bf16>(), kH, nullptr, nullptr,
+                                                     nullptr, 0, s->dx.as<float>(), nullptr, kF,
+                                                     st)));
+  else
+    gemm<false, true, EPI_F32>(B, kF, kH, s->dh1.as<bf16>(), kH, s->w1b.as<bf16>(), kH, nullptr,
+                               nullptr, 0, s->dx.as<float>(), nullptr, kF, 1, st);
   {
     const int seg = s->emb_seg_len(B);
     const dim3 eg((unsigned)((s->C + 63) / 64), (unsigned)((B + seg - 1) / seg));
@@ -858,7 +974,7 @@ static ebic_status sur_step(ebic_surrogate_ctx* s, const uint16_t* seq, const in
     k_sum_splits<<<(unsigned)((ne + 255) / 256), 256, 0, st>>>(s->epart.as<float>(), (int)eg.y, ne,
                                                               G + s->o_emb);
   }
-  count_launches(17);
+  count_launches(23);   // 3 + 20 above
   if (update) {
     s->steps_done += 1;
     const float b1 = 0.9f, b2 = 0.999f;
@@ -927,7 +1043,8 @@ static void sur_release(ebic_surrogate_ctx* s) {
                     &s->wpack_tc, &s->ferr,
                     &s->cmean, &s->csd,
                     &s->act, &s->dh1, &s->dh2, &s->dx, &s->y, &s->dy, &s->idx, &s->loss,
-                    &s->tgt, &s->tmp, &s->log_seq, &s->log_len, &s->log_fit})
+                    &s->tgt, &s->tmp, &s->sq, &s->split, &s->epart, &s->csplit, &s->log_seq,
+                    &s->log_len, &s->log_fit})
     b->release();
   if (s->stream) cudaStreamDestroy(s->stream);
   s->stream = nullptr;
@@ -1185,6 +1302,13 @@ ebic_status ebic_surrogate_forward_kernel(ebic_surrogate s, int32_t kind) {
   if (!s) return fail(EBIC_ERR_ARG, "null surrogate");
   if (kind != 0 && kind != 1) return fail(EBIC_ERR_ARG, "forward kernel must be 0 or 1");
   s->fwd_kind = kind;
+  return EBIC_OK;
+}
+
+ebic_status ebic_surrogate_train_kernel(ebic_surrogate s, int32_t kind) {
+  if (!s) return fail(EBIC_ERR_ARG, "null surrogate");
+  if (kind != 0 && kind != 1) return fail(EBIC_ERR_ARG, "training kernel must be 0 or 1");
+  s->gemm_kind = kind;
   return EBIC_OK;
 }
 

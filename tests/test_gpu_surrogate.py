@@ -167,11 +167,19 @@ def test_forward_kernels_agree(paper_problem):
         eb.ebic_surrogate_free(s)
 
 
-def test_gradients_match_oracle(paper_problem):
+TRAIN_KINDS = [eb.FORWARD_TCGEN05, eb.FORWARD_MMA_SYNC]
+
+
+@pytest.mark.parametrize("kind", TRAIN_KINDS)
+def test_gradients_match_oracle(paper_problem, kind):
+    """Loss and every parameter gradient of one minibatch of 300 series (a
+    ragged last tile of 44 rows, split-K over a ragged range) against the
+    oracle, with the tcgen05 training GEMMs and with the mma.sync ones."""
     prob, h = paper_problem
     C = prob.A.shape[1]
     s = eb.ebic_surrogate_create(h, 20, 2)
     try:
+        eb.ebic_surrogate_train_kernel(s, kind)
         p, flat = _oracle_params(C, 9)
         eb.ebic_surrogate_params(s, flat)
         rng = np.random.default_rng(2)
@@ -198,13 +206,15 @@ def test_gradients_match_oracle(paper_problem):
         eb.ebic_surrogate_free(s)
 
 
-def test_adam_step(paper_problem):
+@pytest.mark.parametrize("kind", TRAIN_KINDS)
+def test_adam_step(paper_problem, kind):
     """First Adam step: every parameter moves by at most lr, and where the
     oracle's gradient is large it moves by exactly -lr sign(g)."""
     prob, h = paper_problem
     C = prob.A.shape[1]
     s = eb.ebic_surrogate_create(h, 20, 3)
     try:
+        eb.ebic_surrogate_train_kernel(s, kind)
         p, flat = _oracle_params(C, 11)
         eb.ebic_surrogate_params(s, flat)
         rng = np.random.default_rng(3)
@@ -351,7 +361,8 @@ def test_trained_surrogate_picks_fitter_children(paper_problem):
         eb.ebic_surrogate_free(s)
 
 
-def test_training_is_deterministic(paper_problem):
+@pytest.mark.parametrize("kind", TRAIN_KINDS)
+def test_training_is_deterministic(paper_problem, kind):
     """Two surrogates created with the same seed and trained on the same log
     end with bit-identical parameters (no atomics in the reverse pass), and a
     large minibatch exercises the split-K weight gradients."""
@@ -361,6 +372,7 @@ def test_training_is_deterministic(paper_problem):
     for _ in range(2):
         s = eb.ebic_surrogate_create(h, 20, 77)
         try:
+            eb.ebic_surrogate_train_kernel(s, kind)
             eb.ebic_surrogate_log(s, h)
             loss = eb.ebic_surrogate_train(s, 40, 2048, 1e-3)
             out.append((eb.ebic_surrogate_params(s), loss))
@@ -368,3 +380,45 @@ def test_training_is_deterministic(paper_problem):
             eb.ebic_surrogate_free(s)
     assert_bits_equal(out[0][0], out[1][0], "trained parameters")
     assert out[0][1] == out[1][1]
+
+
+def test_train_kernels_agree(paper_problem):
+    """The tcgen05 training GEMMs and the mma.sync ones give the same loss and
+    gradients up to the fp32 order of additions (and the bf16 roundings that
+    order can flip) on a minibatch of 1,000 series: eight row tiles, the last
+    of 104 rows, and three split-K ranges of 384, 384 and 232 rows."""
+    prob, h = paper_problem
+    C = prob.A.shape[1]
+    p, flat = _oracle_params(C, 13)
+    rng = np.random.default_rng(5)
+    B = 1000
+    seqs = _series(rng, B, C, 1, 20)
+    cm, cs = mlp.column_stats(prob.A)
+    y0, _ = mlp.forward(mlp.features(seqs, p["Emb"], cm, cs, 20), p)
+    t = y0 - 1.0 - np.abs(rng.standard_normal(B))
+    d_seq, d_len = _device_series(seqs, 20)
+    d_t = torch.from_numpy(t.astype(np.float32)).cuda()
+    res = {}
+    for kind in TRAIN_KINDS:
+        s = eb.ebic_surrogate_create(h, 20, 4)
+        try:
+            eb.ebic_surrogate_train_kernel(s, kind)
+            eb.ebic_surrogate_params(s, flat)
+            loss = eb.ebic_surrogate_step(s, d_seq, d_len, 20, d_t, B, update=False)
+            res[kind] = (loss, eb.ebic_surrogate_split(
+                eb.ebic_surrogate_grads(s).astype(np.float64), C))
+        finally:
+            eb.ebic_surrogate_free(s)
+    (la, ga), (lb, gb) = res[TRAIN_KINDS[0]], res[TRAIN_KINDS[1]]
+    assert abs(la - lb) <= 1e-3 * abs(lb)
+    for name in ["Emb", "W1", "b1", "W2", "b2", "w3", "b3"]:
+        a, b = ga[name].reshape(-1), gb[name].reshape(-1)
+        assert np.isfinite(a).all()
+        rel = np.linalg.norm(a - b) / np.linalg.norm(b)
+        assert rel <= 2 ** -6, (name, rel)
+    with pytest.raises(eb.EbicError):
+        s = eb.ebic_surrogate_create(h, 20, 4)
+        try:
+            eb.ebic_surrogate_train_kernel(s, 2)
+        finally:
+            eb.ebic_surrogate_free(s)
