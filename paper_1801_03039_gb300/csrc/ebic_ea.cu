@@ -508,49 +508,55 @@ __global__ void __launch_bounds__(128) k_pick(EaDev d) {
   if (jc >= (long long)d.J * d.ncombo) return;
   const int j = (int)(jc / d.ncombo), c = (int)(jc % d.ncombo);
   const float* sc = d.var_score + jc * d.V;
+  float scv[16];                                    // the scores, read once (V <= 16)
+  for (int v = 0; v < d.V; ++v) {
+    const float x = sc[v];
+    scv[v] = x != x ? -INFINITY : x;
+  }
+  // each visited candidate is read once into t (eight loads in flight per
+  // round); its hash, tabu probe and write-out work on that copy
+  uint16_t t[kMaxLen];
   uint32_t seen = 0u;
-  int first = -1, chosen = -1;
+  int first = -1, chosen = -1, L = 0;
   unsigned long long chosen_h = 0ull, first_h = 0ull;
   for (int r = 0; r < d.V && chosen < 0; ++r) {
     int bv = -1;
     float bs = 0.f;
     for (int v = 0; v < d.V; ++v) {
       if ((seen >> v) & 1u) continue;
-      float x = sc[v];
-      if (x != x) x = -INFINITY;
-      if (bv < 0 || x > bs) {
+      if (bv < 0 || scv[v] > bs) {
         bv = v;
-        bs = x;
+        bs = scv[v];
       }
     }
     seen |= 1u << bv;
     const long long row = jc * d.V + bv;
-    const int L = d.var_len[row];
-    const uint16_t* x = d.var_seq + (size_t)row * d.S;
-    const unsigned long long h = seq_hash(x, L);
+    L = d.var_len[row];
+    copy_cols(t, d.var_seq + (size_t)row * d.S, L);
+    const unsigned long long h = seq_hash(t, L);
     if (first < 0) {
       first = bv;
       first_h = h;
     }
-    if (!tabu_contains(d, h, x, L)) {
+    if (!tabu_contains(d, h, t, L)) {
       chosen = bv;
       chosen_h = h;
     }
   }
   const bool hit = chosen < 0;
-  if (hit) {
+  if (hit) {                                        // every candidate is in the list
     chosen = first;
     chosen_h = first_h;
+    const long long row = jc * d.V + chosen;
+    L = d.var_len[row];
+    copy_cols(t, d.var_seq + (size_t)row * d.S, L);
   }
-  const long long row = jc * d.V + chosen;
-  const int L = d.var_len[row];
-  const uint16_t* x = d.var_seq + (size_t)row * d.S;
   const RecLayout l = rec_layout(d.k, d.S, false, bit_words(d.WC));
   char* rec = d.rec + (size_t)j * d.rec_bytes;
   uint16_t* out = reinterpret_cast<uint16_t*>(rec + l.ccols) + (size_t)c * d.S;
-  for (int i = 0; i < L; ++i) out[i] = x[i];
+  for (int i = 0; i < L; ++i) out[i] = t[i];
   reinterpret_cast<int32_t*>(rec + l.cL)[c] = L;
-  if (l.nw) write_bits(reinterpret_cast<uint32_t*>(rec + l.cbit) + (size_t)c * l.nw, l.nw, x, L);
+  if (l.nw) write_bits(reinterpret_cast<uint32_t*>(rec + l.cbit) + (size_t)c * l.nw, l.nw, t, L);
   reinterpret_cast<unsigned long long*>(rec + l.chash)[c] = chosen_h;
   reinterpret_cast<int32_t*>(rec + l.ctabu)[c] = hit ? 1 : 0;
 }
