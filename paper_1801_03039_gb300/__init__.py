@@ -170,8 +170,11 @@ def _check(status: int):
 
 
 def _host(a, dtype):
+    """A contiguous array of `dtype` and its address (a plain int, which the
+    c_void_p argument types take as is and which is cheaper to get than a
+    ctypes pointer object)."""
     a = np.ascontiguousarray(a, dtype=dtype)
-    return a, a.ctypes.data_as(ctypes.c_void_p)
+    return a, a.ctypes.data
 
 
 def _dev(x):
@@ -248,7 +251,7 @@ def ebic_pair_table_bytes(h):
 
 def ebic_read_pair_words(h, p, q, w0, n):
     out = np.zeros(n, np.uint32)
-    _check(lib().ebic_read_pair_words(h, p, q, w0, n, out.ctypes.data_as(ctypes.c_void_p)))
+    _check(lib().ebic_read_pair_words(h, p, q, w0, n, out.ctypes.data))
     return out
 
 
@@ -301,12 +304,12 @@ def ebic_eval_population(h, offsets, cols, sigma: int, support_mode: int = SUPPO
     off, po = _host(offsets, np.int32)
     cl, pc = _host(cols, np.int32)
     P = off.shape[0] - 1
-    inc = np.zeros(P, np.uint32)
-    dec = np.zeros(P, np.uint32) if want_dec else None
-    fit = np.zeros(P, np.float64)
+    inc = np.empty(P, np.uint32)
+    dec = np.empty(P, np.uint32) if want_dec else None
+    fit = np.empty(P, np.float64)
     _check(lib().ebic_eval_population(
-        h, po, pc, P, int(sigma), int(support_mode), inc.ctypes.data_as(_P),
-        dec.ctypes.data_as(_P) if dec is not None else None, fit.ctypes.data_as(_P)))
+        h, po, pc, P, int(sigma), int(support_mode), inc.ctypes.data,
+        dec.ctypes.data if dec is not None else None, fit.ctypes.data))
     return inc, dec, fit
 
 
@@ -432,8 +435,8 @@ def ebic_get_toprank(h, capacity: int, len_max: int):
     fit = np.zeros(max(1, capacity), np.float64)
     inc = np.zeros(max(1, capacity), np.uint32)
     n = ctypes.c_int32(capacity)
-    _check(lib().ebic_get_toprank(h, off.ctypes.data_as(_P), cols.ctypes.data_as(_P),
-                                  fit.ctypes.data_as(_P), inc.ctypes.data_as(_P),
+    _check(lib().ebic_get_toprank(h, off.ctypes.data, cols.ctypes.data,
+                                  fit.ctypes.data, inc.ctypes.data,
                                   ctypes.byref(n)))
     k = n.value
     return _records(off, cols, k), fit[:k].copy(), inc[:k].copy()
@@ -446,9 +449,9 @@ def ebic_get_population(h, capacity: int, len_max: int):
     dec = np.zeros(max(1, capacity), np.uint32)
     fit = np.zeros(max(1, capacity), np.float64)
     n = ctypes.c_int32(capacity)
-    _check(lib().ebic_get_population(h, off.ctypes.data_as(_P), cols.ctypes.data_as(_P),
-                                     inc.ctypes.data_as(_P), dec.ctypes.data_as(_P),
-                                     fit.ctypes.data_as(_P), ctypes.byref(n)))
+    _check(lib().ebic_get_population(h, off.ctypes.data, cols.ctypes.data,
+                                     inc.ctypes.data, dec.ctypes.data,
+                                     fit.ctypes.data, ctypes.byref(n)))
     k = n.value
     return dict(seqs=_records(off, cols, k), inc=inc[:k].copy(), dec=dec[:k].copy(),
                 f=fit[:k].copy())
@@ -462,8 +465,8 @@ def ebic_run_generations(h, params: Params, capacity: int | None = None):
     fit = np.zeros(max(1, cap), np.float64)
     n = ctypes.c_int32(cap)
     st = Stats()
-    _check(lib().ebic_run_generations(h, ctypes.byref(params), off.ctypes.data_as(_P),
-                                      cols.ctypes.data_as(_P), fit.ctypes.data_as(_P),
+    _check(lib().ebic_run_generations(h, ctypes.byref(params), off.ctypes.data,
+                                      cols.ctypes.data, fit.ctypes.data,
                                       ctypes.byref(n), ctypes.byref(st)))
     k = n.value
     return _records(off, cols, k), fit[:k].copy(), st.as_dict()
@@ -490,7 +493,7 @@ def ebic_surrogate_params(s, values=None) -> np.ndarray:
     _check(lib().ebic_surrogate_params(s, None, ctypes.byref(n), 0))
     if values is None:
         out = np.zeros(n.value, np.float32)
-        _check(lib().ebic_surrogate_params(s, out.ctypes.data_as(_P), ctypes.byref(n), 0))
+        _check(lib().ebic_surrogate_params(s, out.ctypes.data, ctypes.byref(n), 0))
         return out
     v, p = _host(values, np.float32)
     if v.size != n.value:
@@ -515,14 +518,14 @@ def ebic_surrogate_grads(s) -> np.ndarray:
     n = ctypes.c_int64(0)
     _check(lib().ebic_surrogate_params(s, None, ctypes.byref(n), 0))
     out = np.zeros(n.value, np.float32)
-    _check(lib().ebic_surrogate_grads(s, out.ctypes.data_as(_P), n.value))
+    _check(lib().ebic_surrogate_grads(s, out.ctypes.data, n.value))
     return out
 
 
 def ebic_surrogate_colstats(s, C: int):
     m = np.zeros(C, np.float32)
     d = np.zeros(C, np.float32)
-    _check(lib().ebic_surrogate_colstats(s, m.ctypes.data_as(_P), d.ctypes.data_as(_P)))
+    _check(lib().ebic_surrogate_colstats(s, m.ctypes.data, d.ctypes.data))
     return m, d
 
 
@@ -588,11 +591,11 @@ def _extract(call, offsets, cols):
     P = len(off) - 1
     roff = np.zeros(P + 1, np.int64)
     cap = ctypes.c_int64(0)
-    st = call(po, pc, P, roff.ctypes.data_as(_P), None, ctypes.byref(cap))
+    st = call(po, pc, P, roff.ctypes.data, None, ctypes.byref(cap))
     if st != 0 and cap.value == 0 and P > 0:
         _check(st)
     rows = np.zeros(max(1, cap.value), np.int32)
-    _check(call(po, pc, P, roff.ctypes.data_as(_P), rows.ctypes.data_as(_P), ctypes.byref(cap)))
+    _check(call(po, pc, P, roff.ctypes.data, rows.ctypes.data, ctypes.byref(cap)))
     return [rows[roff[i]:roff[i + 1]].copy() for i in range(P)]
 
 
@@ -626,7 +629,7 @@ def ebic_recovery_relevance(expected, found, want_jaccard: bool = False):
     fc, fcv = _csr([f[1] for f in found])
     rec, rel = ctypes.c_double(0), ctypes.c_double(0)
     J = np.zeros(max(1, E * F), np.float64)
-    p = lambda a: a.ctypes.data_as(_P)
+    p = lambda a: a.ctypes.data
     _check(lib().ebic_recovery_relevance(E, p(er), p(ev), p(ec), p(ecv), F, p(fr), p(fv), p(fc),
                                          p(fcv), ctypes.byref(rec), ctypes.byref(rel),
                                          p(J) if want_jaccard else None))

@@ -934,47 +934,73 @@ ebic_status ebic_eval_population(ebic_handle h, const int32_t* offsets, const in
   if (support_mode != EBIC_SUPPORT_INC && support_mode != EBIC_SUPPORT_INC_PLUS_DEC)
     return fail(EBIC_ERR_ARG, "bad support mode %d", support_mode);
   if (offsets[0] != 0) return fail(EBIC_ERR_ARG, "offsets[0] must be 0");
+  // the lengths, in one pass without early exit; the offending series only
+  // when there is one
+  bool bad_len = false;
   for (int32_t i = 0; i < P; ++i) {
-    int32_t L = offsets[i + 1] - offsets[i];
-    if (L < 1 || L > EBIC_MAX_EVAL_LEN)
-      return fail(EBIC_ERR_ARG, "series %d has length %d outside [1, %d]", i, L,
-                  EBIC_MAX_EVAL_LEN);
+    const int32_t L = offsets[i + 1] - offsets[i];
+    bad_len |= (L < 1) | (L > EBIC_MAX_EVAL_LEN);
   }
+  if (bad_len)
+    for (int32_t i = 0; i < P; ++i) {
+      const int32_t L = offsets[i + 1] - offsets[i];
+      if (L < 1 || L > EBIC_MAX_EVAL_LEN)
+        return fail(EBIC_ERR_ARG, "series %d has length %d outside [1, %d]", i, L,
+                    EBIC_MAX_EVAL_LEN);
+    }
   const int32_t total = offsets[P];
-  for (int32_t k = 0; k < total; ++k)
-    if (cols[k] < 0 || cols[k] >= h->C)
-      return fail(EBIC_ERR_ARG, "column index %d at position %d outside [0, %d)", cols[k], k,
-                  h->C);
   DeviceGuard g(h->device);
   cudaStream_t s = h->stream;
+  // device staging: the CBF, then [fitness | inc | dec] in one buffer so that
+  // one copy brings every result back into the pinned host stage
+  const size_t nres = (size_t)P * (sizeof(double) + 2 * sizeof(uint32_t));
   EBIC_TRY(h->st_off.reserve((size_t)(P + 1) * sizeof(int32_t)));
   EBIC_TRY(h->st_cols.reserve((size_t)std::max(total, 1) * sizeof(int32_t)));
-  EBIC_TRY(h->st_inc.reserve((size_t)P * sizeof(uint32_t)));
-  EBIC_TRY(h->st_dec.reserve((size_t)P * sizeof(uint32_t)));
-  EBIC_TRY(h->st_fit.reserve((size_t)P * sizeof(double)));
+  EBIC_TRY(h->st_fit.reserve(nres));
+  EBIC_TRY(h->h_stage.reserve(nres));
   EBIC_CUDA_TRY(cudaMemcpyAsync(h->st_off.ptr, offsets, (size_t)(P + 1) * sizeof(int32_t),
                                 cudaMemcpyHostToDevice, s));
   EBIC_CUDA_TRY(cudaMemcpyAsync(h->st_cols.ptr, cols, (size_t)total * sizeof(int32_t),
                                 cudaMemcpyHostToDevice, s));
+  double* d_fit = h->st_fit.as<double>();
+  uint32_t* d_inc = reinterpret_cast<uint32_t*>(d_fit + P);
+  uint32_t* d_dec = d_inc + P;
+  const bool with_dec = out_dec != nullptr;
   EvalArgs a{};
   a.P = P;
   a.sigma = sigma;
   a.mode = support_mode;
-  a.want_dec = out_dec != nullptr;
-  a.inc = h->st_inc.as<uint32_t>();
-  a.dec = (out_dec || support_mode == EBIC_SUPPORT_INC_PLUS_DEC) ? h->st_dec.as<uint32_t>()
-                                                                 : nullptr;
-  a.fit = h->st_fit.as<double>();
+  a.want_dec = with_dec;
+  a.inc = d_inc;
+  a.dec = (with_dec || support_mode == EBIC_SUPPORT_INC_PLUS_DEC) ? d_dec : nullptr;
+  a.fit = d_fit;
   a.lnf = nullptr;
   EBIC_TRY(eval_cbf(h, h->st_off.as<int32_t>(), h->st_cols.as<int32_t>(), total, a, s));
-  EBIC_CUDA_TRY(cudaMemcpyAsync(out_inc, a.inc, (size_t)P * sizeof(uint32_t),
-                                cudaMemcpyDeviceToHost, s));
-  if (out_dec)
-    EBIC_CUDA_TRY(cudaMemcpyAsync(out_dec, a.dec, (size_t)P * sizeof(uint32_t),
-                                  cudaMemcpyDeviceToHost, s));
-  EBIC_CUDA_TRY(cudaMemcpyAsync(out_fitness, a.fit, (size_t)P * sizeof(double),
-                                cudaMemcpyDeviceToHost, s));
+  const size_t back = (size_t)P * (sizeof(double) + (with_dec ? 2 : 1) * sizeof(uint32_t));
+  EBIC_CUDA_TRY(cudaMemcpyAsync(h->h_stage.ptr, d_fit, back, cudaMemcpyDeviceToHost, s));
+  // the column indices are checked while the device works (the kernels
+  // bound-check every index themselves, so a bad one only raises the device
+  // flag, which is cleared again below); nothing reaches the caller's
+  // buffers unless every index is valid
+  int32_t lo = 0, hi = 0;
+  for (int32_t k = 0; k < total; ++k) {
+    lo = std::min(lo, cols[k]);
+    hi = std::max(hi, cols[k]);
+  }
   EBIC_CUDA_TRY(cudaStreamSynchronize(s));
+  if (lo < 0 || hi >= h->C) {
+    EBIC_CUDA_TRY(cudaMemset(h->d_err, 0, sizeof(int)));
+    for (int32_t k = 0; k < total; ++k)
+      if (cols[k] < 0 || cols[k] >= h->C)
+        return fail(EBIC_ERR_ARG, "column index %d at position %d outside [0, %d)", cols[k], k,
+                    h->C);
+  }
+  const unsigned char* hs = h->h_stage.as<unsigned char>();
+  std::memcpy(out_fitness, hs, (size_t)P * sizeof(double));
+  std::memcpy(out_inc, hs + (size_t)P * sizeof(double), (size_t)P * sizeof(uint32_t));
+  if (with_dec)
+    std::memcpy(out_dec, hs + (size_t)P * (sizeof(double) + sizeof(uint32_t)),
+                (size_t)P * sizeof(uint32_t));
   return EBIC_OK;
 }
 

@@ -1,6 +1,8 @@
 """Parity of the CUDA evaluation path (K1 placement, K2 pair table, K3 support
 + Eq. (1)) with the oracle, through the C ABI.  Counts and fitness must be
 bit-identical: integers exactly, binary64 fitness bit for bit."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -171,10 +173,30 @@ def test_host_variant_rejects_invalid_cbf():
     A = np.random.default_rng(0).standard_normal((50, 4)).astype(np.float32)
     h = eb.ebic_load_matrix(A)
     for off, cols in [([0, 2], [0, 4]), ([0, 2], [-1, 1]), ([1, 3], [0, 1, 2]),
-                      ([0, 0], []), ([0, 2, 1], [0, 1])]:
+                      ([0, 0], []), ([0, 2, 1], [0, 1]), ([0, 2, 5], [0, 1, 2, 3, 9])]:
         with pytest.raises(eb.EbicError) as e:
             eb.ebic_eval_population(h, np.array(off), np.array(cols), 3)
         assert e.value.status == 1
+    # column indices are checked while the device runs: a bad one leaves the
+    # caller's buffers untouched and no device error behind
+    off = np.array([0, 2, 4], np.int32)
+    cols = np.array([0, 1, 2, 7], np.int32)
+    inc = np.full(2, 7, np.uint32)
+    dec = np.full(2, 7, np.uint32)
+    fit = np.full(2, 7.0)
+    P_ = ctypes.c_void_p
+    st = eb.lib().ebic_eval_population(h, off.ctypes.data_as(P_), cols.ctypes.data_as(P_), 2, 3, 0,
+                                       inc.ctypes.data_as(P_), dec.ctypes.data_as(P_),
+                                       fit.ctypes.data_as(P_))
+    assert st == 1
+    assert (inc == 7).all() and (dec == 7).all() and (fit == 7.0).all()
+    eb.ebic_check_device_error(h)
+    cols[3] = 3
+    oinc, odec, ofit = oracle_eval(A, off, cols, 3)
+    ginc, gdec, gfit = eb.ebic_eval_population(h, off, cols, 3)
+    assert_bits_equal(ginc, oinc, "inc")
+    assert_bits_equal(gdec, odec, "dec")
+    assert_bits_equal(gfit, ofit, "fitness")
     eb.ebic_free(h)
 
 
