@@ -350,9 +350,15 @@ __global__ void k_sum_splits(const float* __restrict__ part, int splits, long lo
 __global__ void __launch_bounds__(256)
 k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
        float* __restrict__ v, long long n, float lr, float b1, float b2, float eps, float c1,
-       float c2, bf16* __restrict__ copy) {
+       float c2, bf16* __restrict__ copy, const float2* __restrict__ ctab,
+       const int32_t* __restrict__ ctr) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
+  if (ctab) {                                       // replayed step: its corrections
+    const float2 c = ctab[*ctr];
+    c1 = c.x;
+    c2 = c.y;
+  }
   const float gi = g[i];
   const float mi = b1 * m[i] + (1.f - b1) * gi;
   const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
@@ -362,6 +368,9 @@ k_adam(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m
   p[i] = pi;
   if (copy) copy[i] = __float2bfloat16_rn(pi);
 }
+
+// The replay index of a captured training step, advanced at its end.
+__global__ void k_step_advance(int32_t* ctr) { *ctr += 1; }
 
 __global__ void k_to_bf16(const float* __restrict__ src, bf16* __restrict__ dst, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -421,9 +430,11 @@ __global__ void __launch_bounds__(256) k_sum_log1p(const double* __restrict__ f,
 }
 
 // minibatch indices: idx[b] = floor(u * n), u from Philox-4x32-10 keyed by (seed, step)
-__global__ void k_sample(uint64_t seed, uint32_t step, long long n, int B, int32_t* idx) {
+__global__ void k_sample(uint64_t seed, uint32_t step, long long n, int B, int32_t* idx,
+                         const int32_t* __restrict__ ctr) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= B) return;
+  if (ctr) step += (uint32_t)*ctr;                  // replayed step: base + replay index
   uint32_t x0 = (uint32_t)b, x1 = step, x2 = 0x5EEDu, x3 = 0u;
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
 #pragma unroll
@@ -688,6 +699,7 @@ struct ebic_surrogate_ctx {
   // training activations (capacity rows)
   int32_t cap = 0;
   DevBuf act, dh1, dh2, dx, y, dy, idx, loss, tgt, tmp, sq, split, epart, csplit;
+  DevBuf ctab, ctr;            // replayed training: Adam corrections per step, replay index
   // training log: series [log_n][kLogStride], lengths, exact fitness
   long long log_n = 0, log_cap = 0;
   DevBuf log_seq, log_len, log_fit;
@@ -912,9 +924,13 @@ static void pack_forward(ebic_surrogate_ctx* s, cudaStream_t st) {
 
 // One training step on batch rows idx (device; nullptr: rows 0 .. B - 1);
 // gradients are left in s->grad.
+// One Adam step (update) or the loss and gradients only.  With ctab/ctr the
+// step is being captured for replay: Adam's bias corrections come from
+// ctab[*ctr] and the caller counts the steps.
 static ebic_status sur_step(ebic_surrogate_ctx* s, const uint16_t* seq, const int32_t* len,
                             int32_t stride, const float* t, const int32_t* idx, int32_t B,
-                            float lr, bool update, cudaStream_t st) {
+                            float lr, bool update, cudaStream_t st,
+                            const float2* ctab = nullptr, const int32_t* ctr = nullptr) {
   EBIC_TRY(sur_reserve(s, B));
   const ActView a = act_view(s->act.ptr, B);
   EBIC_TRY(sur_hidden(s, seq, len, stride, idx, B, a, st));
@@ -976,7 +992,7 @@ static ebic_status sur_step(ebic_surrogate_ctx* s, const uint16_t* seq, const in
   }
   count_launches(23);   // 3 + 20 above
   if (update) {
-    s->steps_done += 1;
+    if (!ctab) s->steps_done += 1;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = (float)(1.0 - std::pow(0.9, (double)s->steps_done));
     const float c2 = (float)(1.0 - std::pow(0.999, (double)s->steps_done));
@@ -991,7 +1007,7 @@ static ebic_status sur_step(ebic_surrogate_ctx* s, const uint16_t* seq, const in
     for (const Seg& g : segs) {
       k_adam<<<(unsigned)((g.n + 255) / 256), 256, 0, st>>>(
           P + g.o, G + g.o, s->mom.as<float>() + g.o, s->vel.as<float>() + g.o, g.n, lr, b1, b2,
-          1e-8f, c1, c2, g.copy);
+          1e-8f, c1, c2, g.copy, ctab, ctr);
     }
     pack_forward(s, st);
     count_launches(7);
@@ -1043,7 +1059,7 @@ static void sur_release(ebic_surrogate_ctx* s) {
                     &s->wpack_tc, &s->ferr,
                     &s->cmean, &s->csd,
                     &s->act, &s->dh1, &s->dh2, &s->dx, &s->y, &s->dy, &s->idx, &s->loss,
-                    &s->tgt, &s->tmp, &s->sq, &s->split, &s->epart, &s->csplit, &s->log_seq,
+                    &s->tgt, &s->tmp, &s->sq, &s->split, &s->epart, &s->csplit, &s->ctab, &s->ctr, &s->log_seq,
                     &s->log_len, &s->log_fit})
     b->release();
   if (s->stream) cudaStreamDestroy(s->stream);
@@ -1116,12 +1132,52 @@ static ebic_status sur_train(ebic_surrogate_ctx* s, const uint16_t* seq, const i
                                                          s->tgt.as<float>());
   count_launches(2);
   EBIC_TRY(sur_reserve(s, batch));
-  for (int32_t i = 0; i < steps; ++i) {
+  if (steps > 0) {
+    // One step (minibatch draw, forward, reverse pass, Adam, weight packing)
+    // is captured once and replayed `steps` times.  What changes from step
+    // to step comes from the device: the replay index (advanced by the last
+    // kernel of the step) picks the Philox step number of the draw and
+    // Adam's bias corrections from a table computed here exactly as the
+    // eager step computes them.
+    const long long base = s->steps_done;
+    std::vector<float2> tab((size_t)steps);
+    for (int32_t i = 0; i < steps; ++i) {
+      const double t = (double)(base + i + 1);
+      tab[(size_t)i] = make_float2((float)(1.0 - std::pow(0.9, t)), (float)(1.0 - std::pow(0.999, t)));
+    }
+    EBIC_TRY(s->ctab.reserve(tab.size() * sizeof(float2)));
+    EBIC_TRY(s->ctr.reserve(sizeof(int32_t)));
+    EBIC_CUDA_TRY(cudaMemcpyAsync(s->ctab.ptr, tab.data(), tab.size() * sizeof(float2),
+                                  cudaMemcpyHostToDevice, st));
+    EBIC_CUDA_TRY(cudaMemsetAsync(s->ctr.ptr, 0, sizeof(int32_t), st));
+    EBIC_CUDA_TRY(cudaStreamSynchronize(st));        // the table outlives this scope's vector
+    const uint64_t c0 = ebic_kernel_launches();
+    cudaGraph_t graph = nullptr;
+    EBIC_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeRelaxed));
     k_sample<<<(unsigned)((batch + 255) / 256), 256, 0, st>>>(
-        s->seed, (uint32_t)(s->steps_done + 1), n, batch, s->idx.as<int32_t>());
+        s->seed, (uint32_t)(base + 1), n, batch, s->idx.as<int32_t>(), s->ctr.as<int32_t>());
     count_launches(1);
-    EBIC_TRY(sur_step(s, seq, len, stride, s->tgt.as<float>(), s->idx.as<int32_t>(), batch, lr,
-                      true, st));
+    ebic_status rs = sur_step(s, seq, len, stride, s->tgt.as<float>(), s->idx.as<int32_t>(), batch,
+                              lr, true, st, s->ctab.as<float2>(), s->ctr.as<int32_t>());
+    k_step_advance<<<1, 1, 0, st>>>(s->ctr.as<int32_t>());
+    count_launches(1);
+    const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+    if (rs != EBIC_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return rs;
+    }
+    if (ce != cudaSuccess) return fail(EBIC_ERR_CUDA, "training step capture: %s", cudaGetErrorString(ce));
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ie != cudaSuccess) return fail(EBIC_ERR_CUDA, "training step graph: %s", cudaGetErrorString(ie));
+    const uint64_t per_step = ebic_kernel_launches() - c0;
+    cudaError_t le = cudaSuccess;
+    for (int32_t i = 0; i < steps && le == cudaSuccess; ++i) le = cudaGraphLaunch(exec, st);
+    cudaGraphExecDestroy(exec);
+    if (le != cudaSuccess) return fail(EBIC_ERR_CUDA, "training step replay: %s", cudaGetErrorString(le));
+    count_launches(per_step * (uint64_t)(steps - 1));
+    s->steps_done += steps;
   }
   float loss = 0.f;
   if (out_loss && steps > 0)
