@@ -422,3 +422,24 @@ def test_train_kernels_agree(paper_problem):
             eb.ebic_surrogate_train_kernel(s, 2)
         finally:
             eb.ebic_surrogate_free(s)
+
+
+def test_replayed_training_does_not_depend_on_the_call_split(paper_problem):
+    """Training replays one captured Adam step; the step's minibatch draw and
+    bias corrections come from a device replay index and a table built per
+    call from the steps done so far.  Three steps in one call and the same
+    three steps in three calls end with bit-identical parameters."""
+    prob, h = paper_problem
+    _plain_run(h, 60, iters=10)
+    out = []
+    for split in ([3], [1, 1, 1], [2, 1]):
+        s = eb.ebic_surrogate_create(h, 20, 5)
+        try:
+            eb.ebic_surrogate_log(s, h)
+            losses = [eb.ebic_surrogate_train(s, k, 512, 1e-3) for k in split]
+            out.append((eb.ebic_surrogate_params(s), losses[-1]))
+        finally:
+            eb.ebic_surrogate_free(s)
+    for params, loss in out[1:]:
+        assert_bits_equal(params, out[0][0], "trained parameters")
+        assert loss == out[0][1]
