@@ -509,7 +509,9 @@ ebic_status ebic_surrogate_log(ebic_surrogate s, ebic_handle h, int64_t* out_tot
  * over the n pairs; `steps` Adam steps on minibatches of `batch` rows drawn
  * uniformly with replacement (Philox-4x32-10 keyed by the creation seed and
  * the step number).  d_seq/d_len/d_fitness NULL: train on the log.  *out_loss
- * = minibatch loss of the last step.  Synchronous. */
+ * = minibatch loss of the last step.  Synchronous.  The call captures one
+ * step as a CUDA graph and replays it `steps` times; the result equals that
+ * of the same steps in any split across calls. */
 ebic_status ebic_surrogate_train(ebic_surrogate s, const uint16_t* d_seq, const int32_t* d_len,
                                  int32_t stride, const double* d_fitness, int64_t n,
                                  int32_t steps, int32_t batch, float lr, float* out_loss);
