@@ -1574,7 +1574,9 @@ __global__ void __launch_bounds__(kBuildThreads, 1) k_build(EaDev d, int hmask, 
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_tabu_insert(EaDev d) {
   if (*(volatile int32_t*)&d.ctl->stop) return;
-  const int g = d.ctl->gen;
+  // the generation k_build just built: Step 5 of that generation may run
+  // beside this kernel and advance ctl->gen, so it comes from spec_gen
+  const int g = d.ctl->spec_gen - 1;
   const int slot = d.ctl->n_elite + (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (slot >= d.P) return;
   const long long e = (long long)g * d.P + slot;
@@ -2186,12 +2188,15 @@ static void launch_rank(const EaState* st, cudaStream_t s) {
 }
 
 // One generation g as captured for replay.  Step 3 first; then tabu
-// insertion beside the evaluation; then Step 5 of g beside the attempt
-// records of g + 1 (they need g's fitness and tabu list, not its top-rank
-// list, which only the next Step 2 reads):
+// insertion beside the evaluation; Step 5 of g as soon as the evaluation is
+// done, beside the attempt records of g + 1 (which need g's fitness and tabu
+// list, not its top-rank list, which only the next Step 2 reads; tabu
+// insertion and the records take the generation from spec_gen, not from
+// the counter Step 5 advances):
 //
-//   k_build(g) -+- eval(g) ----------+- records(g + 1) -+- (next replay)
-//               +- k_tabu_insert(g) -+- k_rank(g) ------+
+//   k_build(g) -+- eval(g) -+- k_rank(g) ---------------+- (next replay)
+//               |           +---------+                 |
+//               +- k_tabu_insert(g) --+- records(g + 1) -+
 //
 // The records of generation 1 are built at the end of ebic_run_init.
 static ebic_status launch_generation(ebic_ctx* h, EaState* st, cudaStream_t s) {
@@ -2205,14 +2210,14 @@ static ebic_status launch_generation(ebic_ctx* h, EaState* st, cudaStream_t s) {
   k_tabu_insert<<<(unsigned)((st->p.pop_size + 255) / 256), 256, 0, s2>>>(d);
   EBIC_CUDA_TRY(cudaGetLastError());
   EBIC_TRY(eval_archive(h, st->apop, st->eargs, s));
-  EBIC_CUDA_TRY(cudaEventRecord(st->fork_ev[1], s2));
-  EBIC_CUDA_TRY(cudaStreamWaitEvent(s, st->fork_ev[1], 0));
-  EBIC_CUDA_TRY(cudaEventRecord(st->fork_ev[2], s));
-  EBIC_CUDA_TRY(cudaStreamWaitEvent(s2, st->fork_ev[2], 0));
-  launch_rank(st, s2);
+  // Step 5 right after the evaluation (it needs the fitness, not the tabu
+  // list); the next attempt records after both
+  EBIC_CUDA_TRY(cudaEventRecord(st->fork_ev[1], s));
+  EBIC_CUDA_TRY(cudaStreamWaitEvent(s2, st->fork_ev[1], 0));
+  launch_rank(st, s);
   EBIC_CUDA_TRY(cudaGetLastError());
   int nrec = 0;
-  EBIC_TRY(launch_records(st, s, &nrec));
+  EBIC_TRY(launch_records(st, s2, &nrec));
   st->launches_per_gen = nrec + 4;
   EBIC_CUDA_TRY(cudaEventRecord(st->fork_ev[3], s2));
   EBIC_CUDA_TRY(cudaStreamWaitEvent(s, st->fork_ev[3], 0));
