@@ -1900,10 +1900,18 @@ __global__ void __launch_bounds__(kRankWarpThreads) k_rank_warp(EaDev d, int Pp)
   uint32_t* lbits = pbits + (size_t)P * NW;
   int32_t* thr = reinterpret_cast<int32_t*>(lbits + (size_t)cap * NW);
 
+  // Every individual's fitness, length and column bitset, by population
+  // index, read before the sort (the bitsets' column loads go out eight at
+  // a time); the visit reaches them through the sorted index.
   for (int i = tid; i < Ns; i += kRankWarpThreads) {
     if (i < P) {
-      skey[i] = ~(unsigned long long)__double_as_longlong(d.fit[base + i]);
+      const double f = d.fit[base + i];
+      skey[i] = ~(unsigned long long)__double_as_longlong(f);
       sidx[i] = i;
+      pf[i] = f;
+      const int L = d.len[base + i];
+      pL[i] = L;
+      write_bits(pbits + (size_t)i * NW, NW, d.seq + (size_t)(base + i) * d.S, L);
     } else {
       skey[i] = ~0ull;
       sidx[i] = 0x7fffffff;
@@ -1915,11 +1923,7 @@ __global__ void __launch_bounds__(kRankWarpThreads) k_rank_warp(EaDev d, int Pp)
     const int32_t r = d.list_ref[t];
     const int L = d.len[r];
     lm[t] = RankRec{d.list_f[t], r, L};
-    uint32_t* b = lbits + (size_t)t * NW;     // this thread's entry
-#pragma unroll
-    for (int w = 0; w < NW; ++w) b[w] = 0u;
-    const uint16_t* sq = d.seq + (size_t)r * d.S;
-    for (int c = 0; c < L; ++c) b[sq[c] >> 5] |= 1u << (sq[c] & 31);
+    write_bits(lbits + (size_t)t * NW, NW, d.seq + (size_t)r * d.S, L);
   }
   __syncthreads();
   switch (Ns / kRankWarpThreads) {     // Ns is a power of two >= 512
@@ -1928,29 +1932,18 @@ __global__ void __launch_bounds__(kRankWarpThreads) k_rank_warp(EaDev d, int Pp)
     case 4: sort_pairs<4>(skey, sidx, tid); break;
     default: sort_pairs<8>(skey, sidx, tid); break;
   }
-  // individuals in visiting order: fitness, length, bitset
-  for (int oi = tid; oi < P; oi += kRankWarpThreads) {
-    const long long xe = base + sidx[oi];
-    pf[oi] = d.fit[xe];
-    const int L = d.len[xe];
-    pL[oi] = L;
-    uint32_t* b = pbits + (size_t)oi * NW;    // this thread's entry
-#pragma unroll
-    for (int w = 0; w < NW; ++w) b[w] = 0u;
-    const uint16_t* sq = d.seq + (size_t)xe * d.S;
-    for (int c = 0; c < L; ++c) b[sq[c] >> 5] |= 1u << (sq[c] & 31);
-  }
-  __syncthreads();
+
 
   if (tid < 32) {
     const unsigned FULL = 0xffffffffu;
     for (int oi = 0; oi < P; ++oi) {
-      const double xf = pf[oi];
-      const int xL = pL[oi];
+      const int xi = sidx[oi];                  // population index of the oi-th visited
+      const double xf = pf[xi];
+      const int xL = pL[xi];
       uint32_t xb[NW];
 #pragma unroll
       for (int v = 0; v < NW / 4; ++v) {
-        const uint4 w = reinterpret_cast<const uint4*>(pbits + (size_t)oi * NW)[v];
+        const uint4 w = reinterpret_cast<const uint4*>(pbits + (size_t)xi * NW)[v];
         xb[4 * v] = w.x;
         xb[4 * v + 1] = w.y;
         xb[4 * v + 2] = w.z;
@@ -2020,7 +2013,7 @@ __global__ void __launch_bounds__(kRankWarpThreads) k_rank_warp(EaDev d, int Pp)
         }
         __syncwarp();
       }
-      if (lane == 0) lm[ge] = RankRec{xf, (int32_t)(base + sidx[oi]), xL};
+      if (lane == 0) lm[ge] = RankRec{xf, (int32_t)(base + xi), xL};
 #pragma unroll
       for (int w = 0; w < NW; ++w)
         if (lane == w) lbits[(size_t)ge * NW + w] = xb[w];
