@@ -1580,7 +1580,10 @@ __global__ void __launch_bounds__(256) k_tabu_insert(EaDev d) {
   const int slot = d.ctl->n_elite + (int)(blockIdx.x * blockDim.x + threadIdx.x);
   if (slot >= d.P) return;
   const long long e = (long long)g * d.P + slot;
-  const unsigned long long key = seq_hash(d.seq + (size_t)e * d.S, d.len[e]);
+  uint16_t x[kMaxLen];                              // the series, eight loads in flight
+  const int L = d.len[e];
+  copy_cols(x, d.seq + (size_t)e * d.S, L);
+  const unsigned long long key = seq_hash(x, L);
   unsigned long long i = key & d.tmask;
   for (unsigned long long n = 0; n <= d.tmask; ++n) {
     if (atomicCAS(&d.tkey[i], 0ull, key) == 0ull) {
