@@ -799,7 +799,7 @@ static ebic_status tmap_kmajor(CUtensorMap* m, const bf16* p, int rows, int cols
     EBIC_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
                                                    cudaEnableDefault, &q));
     if (q != cudaDriverEntryPointSuccess || !fn)
-      return fail(EBIC_ERR_CUDA, "the driver offers no tensor-map encoder");
+      return fail(EBIC_ERR_CUDA, "the CUDA driver API has no tensor-map encoder entry point");
     encode = reinterpret_cast<TmapEncodeFn>(fn);
   }
   const cuuint64_t dim[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
