@@ -57,6 +57,15 @@ struct EaState;     // generation-loop state (ebic_ea.cu)
 }  // namespace ebic
 
 // The opaque handle.
+// The last launch shape of the staged kernel on a handle and its occupancy,
+// so that repeated evaluations skip the occupancy query.
+struct StagedMemo {
+  const void* fn = nullptr;
+  int threads = 0;
+  size_t smem = 0;
+  int per_sm = 0;
+};
+
 struct ebic_ctx {
   int device = 0;
   int32_t R = 0;          // rows
@@ -74,6 +83,7 @@ struct ebic_ctx {
   uint32_t* d_claim = nullptr;    // item counter of the staged kernel and its
                                   // finished-scout count (zero between launches)
   int32_t sm_count = 0;           // streaming multiprocessors of the device
+  StagedMemo staged_memo;
   ebic::DevBuf tickets;           // per-series partial counts and arrivals of split
                                   // series (2 x 64-bit words each, zero between launches)
   ebic::DevBuf st_off, st_cols, st_inc, st_dec, st_fit;   // staging for host calls

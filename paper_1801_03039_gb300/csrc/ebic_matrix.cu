@@ -308,6 +308,8 @@ int32_t resolve_path(ebic_ctx* h) {
 // cannot run here (a group does not fit one CTA).  Parts hold at most 256
 // vectors; a consumer thread carries `vecs_per_lane` of them (1 to 3; 0 =
 // 2 for parts over 64 vectors).
+constexpr int kStagedMaxSmem = 227 * 1024;   // the per-CTA opt-in limit of sm_100 / sm_103
+
 static bool staged_geometry(const ebic_ctx* h, const ebic_eval_tuning_t& tu, int32_t P,
                             StagedGeom* out) {
   StagedGeom g{};
@@ -326,7 +328,7 @@ static bool staged_geometry(const ebic_ctx* h, const ebic_eval_tuning_t& tu, int
   for (int32_t n = 1; n <= 15; ++n) {
     StagedGeom t = g;
     t.groups = n;
-    if (n * (g.gw + 1) * 32 > 1024 || staged_smem_bytes(t) > 227 * 1024) break;
+    if (n * (g.gw + 1) * 32 > 1024 || staged_smem_bytes(t) > (size_t)kStagedMaxSmem) break;
     groups = n;
   }
   if (tu.groups > 0) groups = std::min(groups, tu.groups);
@@ -345,10 +347,20 @@ static ebic_status launch_staged(ebic_ctx* h, const Pop& pop, const EvalArgs& a,
   const size_t smem = staged_smem_bytes(g);
   const int threads = g.groups * (g.gw + 1) * 32;
   auto kern = k_support_staged<CHECK, Pop, NVT>;
-  EBIC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)smem));
-  int per_sm = 0;
-  EBIC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, smem));
+  // The shared-memory opt-in is set to the device maximum (every handle sets
+  // the same value, so handles with different shapes never undercut each
+  // other) and the occupancy is queried once per shape and handle.
+  StagedMemo& memo = h->staged_memo;
+  const void* fn = reinterpret_cast<const void*>(kern);
+  if (memo.fn != fn || memo.threads != threads || memo.smem != smem) {
+    EBIC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kStagedMaxSmem));
+    EBIC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&memo.per_sm, kern, threads, smem));
+    memo.fn = fn;
+    memo.threads = threads;
+    memo.smem = smem;
+  }
+  const int per_sm = memo.per_sm;
   if (per_sm < 1) return fail(EBIC_ERR_CUDA, "staged kernel: no CTA fits an SM");
   const int64_t n_items = (int64_t)a.P * g.items_per;
   const int64_t grid = std::min<int64_t>((int64_t)h->sm_count * per_sm,
