@@ -232,10 +232,12 @@ k_mlp_forward_tc(const uint16_t* __restrict__ seq, const int32_t* __restrict__ l
         cn1 = i + 3 < L ? (int)__ldg(sp + i + 3) : C;
         int cc0[16], cc1[16];
         float2 v0[16], v1[16];
+        const uint32_t pair = (uint32_t)c0 | ((uint32_t)c1 << 16);   // both ids < 65,536
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-          cc0[j] = __shfl_sync(0xffffffffu, c0, j);
-          cc1[j] = __shfl_sync(0xffffffffu, c1, j);
+          const uint32_t pj = __shfl_sync(0xffffffffu, pair, j);
+          cc0[j] = (int)(pj & 0xFFFFu);
+          cc1[j] = (int)(pj >> 16);
           v0[j] = cc0[j] < C ? ld_keep(e2 + (size_t)cc0[j] * 32) : make_float2(0.f, 0.f);
           v1[j] = cc1[j] < C ? ld_keep(e2 + (size_t)cc1[j] * 32) : make_float2(0.f, 0.f);
         }
