@@ -475,8 +475,8 @@ typedef struct ebic_surrogate_ctx* ebic_surrogate;
 /* A surrogate for the handle's matrix (column count and column statistics are
  * taken from it; the handle must outlive the surrogate).  Weights are
  * initialised from `seed` (embeddings N(0, 0.01), W1 / W2 He-scaled normal,
- * w3 N(0, 1/256), biases 0).  Matrices of more than 65,535 columns:
- * EBIC_ERR_ARG (series hold 16-bit column ids). */
+ * w3 N(0, 1/256), biases 0).  Column ids fit 16 bits (ebic_load_matrix
+ * accepts at most 65,535 columns); the scoring kernel relies on it. */
 ebic_status ebic_surrogate_create(ebic_handle h, int32_t len_scale, uint64_t seed,
                                   ebic_surrogate* out);
 /* Releases the surrogate (NULL: nothing to do, EBIC_OK).  EBIC_ERR_STATE (and

@@ -1069,8 +1069,8 @@ static void sur_release(ebic_surrogate_ctx* s) {
 static ebic_status sur_create(ebic_ctx* h, int32_t len_scale, uint64_t seed,
                               ebic_surrogate_ctx* s) {
   s->device = h->device;
-  // series hold 16-bit column ids, and the scoring kernel shuffles two of
-  // them (or the end marker C) in one 32-bit word
+  // the scoring kernel shuffles two column ids (or the end marker C) in one
+  // 32-bit word; the loader already keeps C at or below 65,535
   if (h->C > 65535) return fail(EBIC_ERR_ARG, "the surrogate supports at most 65,535 columns");
   s->C = h->C;
   s->h = h;

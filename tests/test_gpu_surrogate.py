@@ -443,3 +443,26 @@ def test_replayed_training_does_not_depend_on_the_call_split(paper_problem):
     for params, loss in out[1:]:
         assert_bits_equal(params, out[0][0], "trained parameters")
         assert loss == out[0][1]
+
+
+def test_surrogate_at_the_column_limit():
+    """Series hold 16-bit column ids: a matrix of 65,535 columns gets a
+    surrogate that scores a series of its last columns; 65,536 columns are
+    refused by the loader already (EBIC_ERR_ARG)."""
+    C = 65535
+    A = np.random.default_rng(C).standard_normal((4, C)).astype(np.float32)
+    h = eb.ebic_load_matrix(A)
+    try:
+        s = eb.ebic_surrogate_create(h, 8, 0)
+        try:
+            d_seq, d_len = _device_series([np.array([C - 3, C - 2, C - 1])], 8)
+            out = torch.full((1,), float("nan"), dtype=torch.float32, device="cuda")
+            eb.ebic_surrogate_predict(s, d_seq, d_len, 8, 1, out)
+            assert np.isfinite(out.cpu().numpy()).all()
+        finally:
+            eb.ebic_surrogate_free(s)
+    finally:
+        eb.ebic_free(h)
+    with pytest.raises(eb.EbicError) as e:
+        eb.ebic_load_matrix(np.zeros((4, C + 1), np.float32))
+    assert e.value.status == 1
