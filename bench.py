@@ -950,7 +950,8 @@ def run_ours(args, ws, rank, local):
 
 def kernel_name(tuning) -> str:
     k = (tuning or {}).get("kernel", 0)
-    return {3: "k_support_staged", 1: "k_support_bitmask_lane"}.get(k, "k_support_bitmask_warp")
+    return {4: "k_support_phased", 3: "k_support_staged",
+            1: "k_support_bitmask_lane"}.get(k, "k_support_bitmask_warp")
 
 
 def hbm_roofline(wl, per_step_ms, peaks, alg_bytes, alg_def, kernel, full=None, warm_us=None,
@@ -1018,18 +1019,21 @@ def read_profile(name: str):
 
 def read_traffic(workload: str, kernel: str, tuning=None):
     """Per-launch DRAM bytes of the dominant kernel from the committed ncu summary,
-    if one exists for this workload, this kernel and (for the staged kernel)
-    this number of staged steps (else null)."""
+    if one exists for this workload, this kernel and (for the staged and the
+    phased kernel) this number of staged steps (else null).  The summary holds
+    one entry, or a list of entries under "kernels", one per kernel."""
     p = os.path.join(ROOT, "profiles", f"traffic_{workload}.json")
     try:
-        d = json.load(open(p))
+        top = json.load(open(p))
     except (OSError, ValueError):
         return None
-    if not str(d.get("kernel", "")).startswith(kernel):
+    entries = top.get("kernels", [top])
+    d = next((e for e in entries if str(e.get("kernel", "")).startswith(kernel)), None)
+    if d is None:
         return None
     by_dense = d.get("dram_bytes_per_launch_by_dense_steps")
     if by_dense is not None:
-        dense = (tuning or {}).get("dense_steps") or 4
+        dense = (tuning or {}).get("dense_steps") or (5 if kernel == "k_support_phased" else 4)
         return by_dense.get(str(dense))
     return d.get("dram_bytes_per_launch")
 

@@ -138,17 +138,28 @@ ebic_status ebic_set_path(ebic_handle h, int32_t path);
  *     128-row block still needs) and the group's other warps AND them and
  *     walk the remaining steps with per-vector loads and early exit; rising
  *     counts only (support mode EBIC_SUPPORT_INC, no falling counts), else
- *     the warp kernel runs.  0 = lane kernel up to 2,048 rows, else warp
- *     kernel.
+ *     the warp kernel runs.  4 = phased: a persistent kernel in which each
+ *     CTA owns a fixed set of series and takes them in chunks of up to 32;
+ *     each of its first warps owns a shared-memory slot, copies the first
+ *     dense_steps table rows of one series at a time into it (cp.async),
+ *     ANDs them and issues the next series' copies before loading the next
+ *     steps of the 128-row blocks still alive; blocks alive after that are
+ *     finished by the whole CTA at the end of the chunk; rising counts
+ *     only, and only where two slots fit (else kernel 3's rules apply).  0 = lane kernel up
+ *     to 2,048 rows, else warp kernel.
  *   vecs_per_part_bitmask / vecs_per_part_gather: 16-byte vectors of a table
  *     entry / of a column that one warp walks before the rest of the series
- *     goes to another warp (rounded to a multiple of 32).
+ *     goes to another warp (rounded to a multiple of 32).  For kernel 3,
+ *     vecs_per_part_bitmask caps the vectors of one item (at most 256, the
+ *     default cap; a series is cut into equal parts under the cap).
  *   batch_steps: AND steps fetched between two early-exit tests (4 or 8).
  *   vecs_per_lane: 16-byte vectors each lane of the warp kernel carries
  *     (1, 2 or 4; 4 only with batch_steps 4).  Series that need the falling
  *     count use batch_steps 4 and one vector per lane.
- *   dense_steps (kernel 3): AND steps staged by bulk copies, 1..8 (0 = 4).
- *   stages (kernel 3): items in flight per group, 2..4 (0 = 2).
+ *   dense_steps (kernels 3, 4): AND steps copied whole into shared memory,
+ *     1..8 (0 = 4 for kernel 3, 5 for kernel 4).
+ *   stages (kernel 3): items in flight per group, 2..4 (0 = 2); for kernel
+ *     4 a cap on the slots, one per warp (0 = as many as fit, at most 32).
  *   groups (kernel 3): at most this many groups of warps per CTA (0 = as many
  *     as fit one CTA per SM).
  *   dynamic_rounds (kernel 3): groups take items in a fixed stride, except

@@ -84,6 +84,7 @@ struct ebic_ctx {
                                   // finished-scout count (zero between launches)
   int32_t sm_count = 0;           // streaming multiprocessors of the device
   StagedMemo staged_memo;
+  StagedMemo phased_memo;
   ebic::DevBuf tickets;           // per-series partial counts and arrivals of split
                                   // series (2 x 64-bit words each, zero between launches)
   ebic::DevBuf st_off, st_cols, st_inc, st_dec, st_fit;   // staging for host calls

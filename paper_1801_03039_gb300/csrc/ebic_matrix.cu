@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "ebic_internal.cuh"
+#include "ebic_phased.cuh"
 #include "ebic_staged.cuh"
 #include "ebic_support.cuh"
 
@@ -314,7 +315,10 @@ static bool staged_geometry(const ebic_ctx* h, const ebic_eval_tuning_t& tu, int
                             StagedGeom* out) {
   StagedGeom g{};
   const int32_t V = h->W >> 2;
-  const int32_t parts = (V + 255) / 256;
+  // an item holds at most 256 vectors (or the tuning's part size), the
+  // parts of a series as even as possible
+  const int32_t cap = tu.vecs_per_part_bitmask > 0 ? std::min(tu.vecs_per_part_bitmask, 256) : 256;
+  const int32_t parts = (V + cap - 1) / cap;
   g.vpp = (V + parts - 1) / parts;
   g.items_per = parts;
   g.nvt = (tu.vecs_per_lane >= 1 && tu.vecs_per_lane <= 3) ? tu.vecs_per_lane
@@ -385,6 +389,60 @@ static ebic_status launch_staged(ebic_ctx* h, const Pop& pop, const EvalArgs& a,
   return EBIC_OK;
 }
 
+// Longest series a population view can hold.
+static int32_t pop_max_len(const CbfPop&) { return EBIC_MAX_EVAL_LEN; }
+static int32_t pop_max_len(const FixedPop& p) { return p.stride; }
+static int32_t pop_max_len(const ArchivePop& p) { return p.stride; }
+
+// Geometry of the phased kernel (kernel 4): the slots take the shared memory
+// the fixed regions leave, at most one per warp; false when fewer than two
+// slots fit or the view can hold series longer than a chunk.
+template <class Pop>
+static bool phased_geometry(const ebic_ctx* h, const ebic_eval_tuning_t& tu, const Pop& pop,
+                            PhasedGeom* out) {
+  const int32_t V = h->W >> 2;
+  if (V < 1 || V > 65535 || pop_max_len(pop) > kPhasedCols) return false;
+  PhasedGeom g{};
+  g.dense = tu.dense_steps > 0 ? tu.dense_steps : 5;
+  g.slot_bytes = (int32_t)(((int64_t)g.dense * V * 16 + 127) / 128 * 128);
+  g.ns = 0;
+  const size_t fixed = phased_layout(g).total;           // with no ring
+  if (fixed >= (size_t)kStagedMaxSmem) return false;
+  const int64_t per_slot = g.slot_bytes + (int64_t)kPhasedStage * 20;   // slot + staging
+  const int64_t fit = ((int64_t)kStagedMaxSmem - (int64_t)fixed) / per_slot;
+  g.ns = (int32_t)std::min<int64_t>(fit, kPhasedMaxSlots);
+  if (tu.stages > 0) g.ns = std::min(g.ns, tu.stages);
+  if (g.ns < 2) return false;
+  *out = g;
+  return true;
+}
+
+// Queues the phased kernel: one CTA per SM, at most one per series.
+template <bool CHECK, class Pop>
+static ebic_status launch_phased(ebic_ctx* h, const Pop& pop, const EvalArgs& a,
+                                 const PhasedGeom& g, cudaStream_t s) {
+  const size_t smem = phased_layout(g).total;
+  auto kern = k_support_phased<CHECK, Pop>;
+  StagedMemo& memo = h->phased_memo;
+  const void* fn = reinterpret_cast<const void*>(kern);
+  if (memo.fn != fn || memo.smem != smem) {
+    EBIC_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       kStagedMaxSmem));
+    EBIC_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&memo.per_sm, kern,
+                                                                kPhasedThreads, smem));
+    memo.fn = fn;
+    memo.threads = kPhasedThreads;
+    memo.smem = smem;
+  }
+  if (memo.per_sm < 1) return fail(EBIC_ERR_CUDA, "phased kernel: no CTA fits an SM");
+  const int64_t grid = std::min<int64_t>(h->sm_count, a.P);
+  count_launches(1);
+  kern<<<(unsigned)grid, kPhasedThreads, smem, s>>>(h->LT, h->C, h->W, h->R, pop, a, g, h->LN,
+                                                    h->d_err);
+  EBIC_CUDA_TRY(cudaGetLastError());
+  return EBIC_OK;
+}
+
 template <bool CHECK, class Pop>
 static ebic_status eval_any(ebic_ctx* h, const Pop& pop, EvalArgs a, cudaStream_t s) {
   if (a.P <= 0) return EBIC_OK;
@@ -392,7 +450,11 @@ static ebic_status eval_any(ebic_ctx* h, const Pop& pop, EvalArgs a, cudaStream_
   if (dec && !a.dec) return fail(EBIC_ERR_ARG, "internal: dec output required");
   const int32_t path = resolve_path(h);
   if (path == EBIC_PATH_BITMASK && !h->LT) EBIC_TRY(build_pair_table(h, s));
-  if (path == EBIC_PATH_BITMASK && h->tuning.kernel == 3 && !dec && !a.dec) {
+  if (path == EBIC_PATH_BITMASK && h->tuning.kernel == 4 && !dec && !a.dec) {
+    PhasedGeom g;
+    if (phased_geometry(h, h->tuning, pop, &g)) return launch_phased<CHECK, Pop>(h, pop, a, g, s);
+  }
+  if (path == EBIC_PATH_BITMASK && h->tuning.kernel >= 3 && !dec && !a.dec) {
     StagedGeom g;
     if (staged_geometry(h, h->tuning, a.P, &g))
       return g.nvt == 3   ? launch_staged<CHECK, Pop, 3>(h, pop, a, g, s)
@@ -497,6 +559,7 @@ static ebic_status autotune_any(ebic_ctx* h, const Pop& pop, const EvalArgs& a, 
       for (int32_t nvt : {1, 2})
         for (int32_t dense : {4, 6}) cands.push_back({3, 0, 0, 0, nvt, dense, 2, 0, 0});
       cands.push_back({3, 0, 0, 0, 0, 4, 3, 0, 0});
+      for (int32_t dense : {5, 6}) cands.push_back({4, 0, 0, 0, 0, dense, 0, 0, 0});
     }
     const int32_t parts[] = {32, 64, 128, 256, 0};
     for (int32_t vp : parts) {
@@ -915,7 +978,7 @@ ebic_status ebic_set_eval_tuning(ebic_handle h, const ebic_eval_tuning_t* t) {
   if (!h) return fail(EBIC_ERR_ARG, "null handle");
   ebic_eval_tuning_t z{};
   if (!t) t = &z;
-  if (t->kernel < 0 || t->kernel > 3) return fail(EBIC_ERR_ARG, "kernel must be 0, 1, 2 or 3");
+  if (t->kernel < 0 || t->kernel > 4) return fail(EBIC_ERR_ARG, "kernel must be 0 .. 4");
   if (t->dense_steps < 0 || t->dense_steps > kStagedMaxDense)
     return fail(EBIC_ERR_ARG, "dense_steps must be 0 .. %d", kStagedMaxDense);
   if (!(t->stages == 0 || (t->stages >= 2 && t->stages <= 4)))

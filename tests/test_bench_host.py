@@ -184,3 +184,26 @@ def test_support_bytes_matches_a_direct_count(path, unit, first):
         off[1:] = np.cumsum([len(x) for x in seqs])
         cols = np.array([c for x in seqs for c in x], np.int32)
         assert bench.support_bytes(A, off, cols, path) == _brute_bytes(A, off, cols, unit, first)
+
+
+def test_traffic_lookup_per_kernel_and_staged_steps(tmp_path, monkeypatch):
+    """The DRAM traffic of the timed kernel comes from the committed ncu
+    summary of that kernel and number of staged steps, else null."""
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    (prof / "traffic_w.json").write_text(json.dumps({"kernels": [
+        {"kernel": "k_support_staged<checked, CbfPop, NVT>",
+         "dram_bytes_per_launch_by_dense_steps": {"4": 11, "6": 12}},
+        {"kernel": "k_support_phased<checked, CbfPop>",
+         "dram_bytes_per_launch_by_dense_steps": {"5": 21}}]}))
+    (prof / "traffic_one.json").write_text(json.dumps({"kernel": "k_support_bitmask_warp<x>",
+                                                       "dram_bytes_per_launch": 7}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.read_traffic("w", "k_support_staged", {"dense_steps": 6}) == 12
+    assert bench.read_traffic("w", "k_support_staged", {"dense_steps": 0}) == 11
+    assert bench.read_traffic("w", "k_support_phased", {"dense_steps": 0}) == 21
+    assert bench.read_traffic("w", "k_support_phased", {"dense_steps": 6}) is None
+    assert bench.read_traffic("w", "k_support_bitmask_warp", {}) is None
+    assert bench.read_traffic("one", "k_support_bitmask_warp", {}) == 7
+    assert bench.read_traffic("missing", "k_support_staged", {}) is None
+    assert bench.kernel_name({"kernel": 4}) == "k_support_phased"

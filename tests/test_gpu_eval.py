@@ -233,7 +233,8 @@ def test_device_variant_flags_invalid_series(path):
                                   dict(kernel=2, batch_steps=8, vecs_per_lane=2),
                                   dict(kernel=2, batch_steps=4, vecs_per_lane=4,
                                        vecs_per_part_bitmask=64),
-                                  dict(kernel=3), dict(kernel=3, dense_steps=2, stages=2)])
+                                  dict(kernel=3), dict(kernel=3, dense_steps=2, stages=2),
+                                  dict(kernel=4), dict(kernel=4, dense_steps=2, stages=2)])
 def test_launch_shapes_do_not_change_results(shape, tune):
     # lane-per-vector kernel, warp kernel, and forced splits of each series
     R, C = shape
@@ -350,7 +351,9 @@ STAGED = [dict(kernel=3), dict(kernel=3, dense_steps=1, stages=2),
           dict(kernel=3, vecs_per_lane=1), dict(kernel=3, vecs_per_lane=3),
           dict(kernel=3, vecs_per_lane=3, dense_steps=6, stages=3),
           dict(kernel=3, dynamic_rounds=1), dict(kernel=3, dynamic_rounds=3),
-          dict(kernel=3, dynamic_rounds=64, groups=1)]
+          dict(kernel=3, dynamic_rounds=64, groups=1),
+          dict(kernel=3, vecs_per_part_bitmask=64), dict(kernel=3, vecs_per_part_bitmask=20,
+                                                        vecs_per_lane=1, stages=4)]
 
 
 def _staged_case(name):
@@ -405,7 +408,7 @@ def test_staged_kernel_exact(case, tune):
         eb.ebic_free(h)
 
 
-@pytest.mark.parametrize("tune", STAGED[:2])
+@pytest.mark.parametrize("tune", STAGED[:2] + [dict(kernel=3, vecs_per_part_bitmask=80)])
 def test_staged_kernel_expression_full(tune):
     """The expression-shaped workload at full size, 20,000 x 200, P = 4,096."""
     prob = synth.matrix_expression(seed=0)
@@ -452,12 +455,103 @@ def test_staged_kernel_flags_invalid_series():
     eb.ebic_free(h)
 
 
+# ---------------------------------------------------------------------------
+# The phased kernel (launch shape kernel 4): per-CTA chunks of series, their
+# dense steps streamed through a ring of shared-memory slots, the live
+# vectors' remaining steps walked by the whole CTA.  Rising counts.
+# ---------------------------------------------------------------------------
+PHASED = [dict(kernel=4), dict(kernel=4, dense_steps=1), dict(kernel=4, dense_steps=3, stages=2),
+          dict(kernel=4, dense_steps=4), dict(kernel=4, dense_steps=6, stages=3),
+          dict(kernel=4, dense_steps=8)]
+
+
+def _rising_case():
+    """Rows that rise along every column (a sorted matrix): every 128-row
+    block of a series in increasing column order stays alive through all its
+    steps, so the live-vector and survivor lists of a chunk overflow and the
+    walking threads finish those vectors themselves."""
+    rng = np.random.default_rng(11)
+    A = np.sort(rng.standard_normal((20000, 40)).astype(np.float32), axis=1)
+    seqs = [sorted(rng.choice(40, size=int(rng.integers(2, 31)), replace=False).tolist())
+            for _ in range(2000)]
+    seqs += [rng.permutation(40)[:int(rng.integers(2, 20))].tolist() for _ in range(200)]
+    off, cols = oracle.to_cbf(seqs)
+    return A, off, cols, 100
+
+
+@pytest.mark.parametrize("tune", PHASED)
+@pytest.mark.parametrize("case", ["tiny", "ragged_4097x30", "windows_3000x60_L30_45",
+                                  "long_300x1100", "parts_60000x12", "ties_nan", "rising"])
+def test_phased_kernel_exact(case, tune):
+    A, off, cols, sigma = _rising_case() if case == "rising" else _staged_case(case)
+    oinc, _, ofit = oracle_eval(A, off, cols, sigma)
+    h = eb.ebic_load_matrix(A)
+    try:
+        eb.ebic_set_path(h, eb.PATH_BITMASK)
+        eb.ebic_set_eval_tuning(h, **tune)
+        for rep in range(2):
+            inc, _, fit = eb.ebic_eval_population(h, off, cols, sigma, want_dec=False)
+            eb.ebic_check_device_error(h)
+            assert_bits_equal(inc, oinc, f"inc {case} {tune} launch {rep}")
+            assert_bits_equal(fit, ofit, f"fit {case} {tune} launch {rep}")
+    finally:
+        eb.ebic_free(h)
+
+
+@pytest.mark.parametrize("tune", PHASED[:1] + PHASED[3:5])
+def test_phased_kernel_expression_full(tune):
+    """The expression-shaped workload at full size, 20,000 x 200, P = 4,096."""
+    prob = synth.matrix_expression(seed=0)
+    off, cols = synth.population(2, 4096, 200, 3, 30, plants=prob.plants)
+    oinc, _, ofit = oracle_eval(prob.A, off, cols, 50)
+    h = eb.ebic_load_matrix(prob.A)
+    try:
+        eb.ebic_set_path(h, eb.PATH_BITMASK)
+        eb.ebic_set_eval_tuning(h, **tune)
+        for _ in range(2):
+            inc, _, fit = eb.ebic_eval_population(h, off, cols, 50, want_dec=False)
+            assert_bits_equal(inc, oinc, "inc")
+            assert_bits_equal(fit, ofit, "fit")
+        eb.ebic_check_device_error(h)
+    finally:
+        eb.ebic_free(h)
+
+
+def test_phased_kernel_flags_invalid_series():
+    torch = pytest.importorskip("torch")
+    A = np.random.default_rng(1).standard_normal((5000, 6)).astype(np.float32)
+    h = eb.ebic_load_matrix(A)
+    eb.ebic_set_path(h, eb.PATH_BITMASK)
+    eb.ebic_set_eval_tuning(h, kernel=4)
+    dev = torch.device("cuda:0")
+    off = torch.tensor([0, 2, 4, 6, 99], dtype=torch.int32, device=dev)
+    cols = torch.tensor([0, 1, 2, 6, 3, 4], dtype=torch.int32, device=dev)
+    inc = torch.full((4,), 7, dtype=torch.int32, device=dev)
+    fit = torch.full((4,), 7.0, dtype=torch.float64, device=dev)
+    eb.ebic_eval_population_dev(h, off, cols, 4, 6, 3, 0, inc, None, fit)
+    with pytest.raises(eb.EbicError) as e:
+        eb.ebic_check_device_error(h)
+    assert e.value.status == 7
+    got = inc.cpu().numpy()
+    oinc, _, ofit = oracle_eval(A, np.array([0, 2, 4]), np.array([0, 1, 3, 4]), 3)
+    assert got[1] == 0 and got[3] == 0 and fit.cpu().numpy()[1] == 0.0
+    assert got[0] == oinc[0] and got[2] == oinc[1]
+    off2, cols2 = synth.population(3, 200, 6, 2, 5)
+    oinc2, _, ofit2 = oracle_eval(A, off2, cols2, 3)
+    inc2, _, fit2 = eb.ebic_eval_population(h, off2, cols2, 3, want_dec=False)
+    assert_bits_equal(inc2, oinc2, "inc")
+    assert_bits_equal(fit2, ofit2, "fit")
+    eb.ebic_check_device_error(h)
+    eb.ebic_free(h)
+
+
 def test_staged_kernel_rejects_bad_tuning():
     h = eb.ebic_load_matrix(synth.matrix_tiny(seed=0).A)
     try:
         for bad in (dict(kernel=3, dense_steps=9), dict(kernel=3, stages=1),
                     dict(kernel=3, stages=5), dict(kernel=3, groups=16),
-                    dict(kernel=3, dynamic_rounds=-2), dict(kernel=3, dynamic_rounds=65)):
+                    dict(kernel=3, dynamic_rounds=-2), dict(kernel=3, dynamic_rounds=65),
+                    dict(kernel=5), dict(kernel=4, dense_steps=9)):
             with pytest.raises(eb.EbicError):
                 eb.ebic_set_eval_tuning(h, **bad)
     finally:
