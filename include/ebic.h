@@ -362,7 +362,10 @@ void ebic_default_params(ebic_params_t* p);
 
 /* Step 1.  Allocates the run state on the device (population archive, tabu
  * hash table sized for (iterations + 1) * P series, penalty table) and runs
- * Step 1.  Replaces any earlier run of the handle. */
+ * Step 1.  Replaces any earlier run of the handle.  The run evaluates with
+ * the handle's launch shape when one was set with a nonzero kernel
+ * (ebic_set_eval_tuning, ebic_autotune_eval), else with the shape the
+ * autotuner picks on the initial population. */
 ebic_status ebic_run_init(ebic_handle h, const ebic_params_t* p);
 /* Steps 2-5, `generations` times (fewer if the tabu rule stops the run, or if
  * the archive is full: EBIC_ERR_STATE).  Synchronous. */

@@ -2432,10 +2432,18 @@ static ebic_status run_init(ebic_ctx* h, const ebic_params_t* p) {
   EBIC_CUDA_TRY(cudaGetLastError());
   Ctl c{};
   EBIC_TRY(read_ctl(st, s, &c));
+  // The evaluation of the initial population, with the launch shape set by
+  // hand (a nonzero kernel), else with the one the autotuner picks on it
+  // (its candidates are evaluations of that population).  Either way any
+  // scratch the shape needs is allocated here, before the capture below.
   const ebic_eval_tuning_t user_tuning = h->tuning;
   if (!c.stop) {
-    float us = 0.f;
-    EBIC_TRY(autotune_archive(h, st->apop, a, s, &us));
+    if (user_tuning.kernel != 0) {
+      EBIC_TRY(eval_archive(h, st->apop, a, s));
+    } else {
+      float us = 0.f;
+      EBIC_TRY(autotune_archive(h, st->apop, a, s, &us));
+    }
   }
   launch_rank(st, s);
   count_launches(1);

@@ -31,14 +31,17 @@ def _device_params(kw):
     return p
 
 
-def run_both(A, gens_to_check=None, **kw):
+def run_both(A, gens_to_check=None, tuning=None, **kw):
     """Runs the oracle and the device loop with the same parameters and compares
     them generation by generation.  oversample > 1 screens offspring with
-    pseudo scores on both sides."""
+    pseudo scores on both sides; `tuning` fixes the evaluation's launch shape."""
     kw = {**BASE, **kw}
     ref = oracle.run(A, trace=True, **kw)
     h = eb.ebic_load_matrix(A)
     try:
+        if tuning:
+            eb.ebic_set_path(h, eb.PATH_BITMASK)
+            eb.ebic_set_eval_tuning(h, **tuning)
         p = _device_params(kw)
         V = kw.get("oversample", 1)
         if V > 1:
@@ -219,6 +222,16 @@ def test_expression_shape_three_generations():
     prob = synth.matrix_expression(seed=0)
     run_both(prob.A, gens_to_check={0, 3}, pop_size=4096, len_min=3, len_max=30, sigma=50,
              iterations=3)
+
+
+@pytest.mark.parametrize("tuning", [dict(kernel=2), dict(kernel=3, dense_steps=6),
+                                    dict(kernel=4), dict(kernel=4, dense_steps=3)])
+def test_expression_shape_each_launch_shape(tuning):
+    """The EA's own population view (the archive) through each bitmask launch
+    shape, set by hand so that the run keeps it."""
+    prob = synth.matrix_expression(seed=1)
+    run_both(prob.A, gens_to_check={0, 2, 5}, tuning=tuning, pop_size=600, len_min=3,
+             len_max=30, sigma=50, iterations=5)
 
 
 # ---------------------------------------------------------------------------
