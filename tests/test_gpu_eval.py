@@ -173,10 +173,25 @@ def test_host_variant_rejects_invalid_cbf():
     A = np.random.default_rng(0).standard_normal((50, 4)).astype(np.float32)
     h = eb.ebic_load_matrix(A)
     for off, cols in [([0, 2], [0, 4]), ([0, 2], [-1, 1]), ([1, 3], [0, 1, 2]),
-                      ([0, 0], []), ([0, 2, 1], [0, 1]), ([0, 2, 5], [0, 1, 2, 3, 9])]:
+                      ([0, 0], []), ([0, 2, 1], [0, 1]), ([0, 2, 5], [0, 1, 2, 3, 9]),
+                      ([0, 3, 2, 5], [0, 1, 2, 3, 1]), ([0, 1, 1, 3], [0, 1, 2]),
+                      ([0, 2000], list(range(4)) * 500)]:
         with pytest.raises(eb.EbicError) as e:
             eb.ebic_eval_population(h, np.array(off), np.array(cols), 3)
         assert e.value.status == 1
+        eb.ebic_check_device_error(h)       # no device error left behind
+    # a length check that runs beside the device work also leaves the
+    # caller's buffers untouched
+    off = np.array([0, 2, 2, 4], np.int32)
+    cols = np.array([0, 1, 2, 3], np.int32)
+    inc = np.full(3, 7, np.uint32)
+    fit = np.full(3, 7.0)
+    P_ = ctypes.c_void_p
+    st = eb.lib().ebic_eval_population(h, off.ctypes.data_as(P_), cols.ctypes.data_as(P_), 3, 3, 0,
+                                       inc.ctypes.data_as(P_), None, fit.ctypes.data_as(P_))
+    assert st == 1 and b"series 1" in eb.lib().ebic_last_error()
+    assert (inc == 7).all() and (fit == 7.0).all()
+    eb.ebic_check_device_error(h)
     # column indices are checked while the device runs: a bad one leaves the
     # caller's buffers untouched and no device error behind
     off = np.array([0, 2, 4], np.int32)
