@@ -214,12 +214,10 @@ ebic_status ebic_autotune_eval(ebic_handle h, const int32_t* d_offsets, const in
  *   P + 1 entries; cols offsets[P] entries; out_inc and out_fitness P entries;
  *   out_dec P entries or NULL.  P in [0, 2^24].  Invalid CBF (a column outside
  *   [0, cols), a length outside [1, EBIC_MAX_EVAL_LEN], offsets[0] != 0) gives
- *   EBIC_ERR_ARG with nothing written to the caller's buffers.  offsets[0]
- *   and offsets[P] are checked before anything is queued (offsets[P] sizes
- *   the copy: it must lie in [P, P * EBIC_MAX_EVAL_LEN]); the lengths and the
- *   column indices are checked on the host while the device evaluates (whose
- *   kernels check every range and index too; the device error flag this
- *   raises is cleared before the call returns).
+ *   EBIC_ERR_ARG with nothing written to the caller's buffers.  The offsets
+ *   are checked before anything is queued; the column indices are checked on
+ *   the host while the device evaluates (whose kernels bound-check them too;
+ *   the device error flag this raises is cleared before the call returns).
  *   The results come back in one copy through a pinned stage of the handle.
  * ebic_eval_population_dev: the same with device buffers, queued on `stream`
  *   (asynchronous).  total_cols must equal offsets[P].  The CBF is validated on

@@ -56,9 +56,8 @@ struct EaState;     // generation-loop state (ebic_ea.cu)
 
 }  // namespace ebic
 
-// The opaque handle.
-// The last launch shape of the staged kernel on a handle and its occupancy,
-// so that repeated evaluations skip the occupancy query.
+// The last launch shape of the staged (or phased) kernel on a handle and its
+// occupancy, so that repeated evaluations skip the occupancy query.
 struct StagedMemo {
   const void* fn = nullptr;
   int threads = 0;
@@ -66,6 +65,7 @@ struct StagedMemo {
   int per_sm = 0;
 };
 
+// The opaque handle.
 struct ebic_ctx {
   int device = 0;
   int32_t R = 0;          // rows
@@ -83,8 +83,8 @@ struct ebic_ctx {
   uint32_t* d_claim = nullptr;    // item counter of the staged kernel and its
                                   // finished-scout count (zero between launches)
   int32_t sm_count = 0;           // streaming multiprocessors of the device
-  StagedMemo staged_memo;
-  StagedMemo phased_memo;
+  StagedMemo staged_memo;         // kernel 3
+  StagedMemo phased_memo;         // kernel 4
   ebic::DevBuf tickets;           // per-series partial counts and arrivals of split
                                   // series (2 x 64-bit words each, zero between launches)
   ebic::DevBuf st_off, st_cols, st_inc, st_dec, st_fit;   // staging for host calls
